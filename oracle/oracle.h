@@ -1,0 +1,133 @@
+/*
+ * oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow CPU restatement of the share-domain masked iris-code
+ * uniqueness check of "Large-Scale MPC: Scaling Private Iris Code Uniqueness
+ * Checks to Millions of Users" (arXiv 2405.04463). Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may call it; the CUDA library
+ * never links it and shares no code with it.
+ *
+ * Conventions (0-based parties P0,P1,P2; the paper counts from 1):
+ *   - additive components x_0,x_1,x_2 with x = x_0+x_1+x_2 (mod 2^k);
+ *   - party i holds the replicated pair (x_i, x_{i-1}) (App. C);
+ *   - seed_j is shared by parties j and j+1, so party i holds seed_i and
+ *     seed_{i-1} (App. D, 3OT and BitInject);
+ *   - boolean sharings are the same with XOR in place of +.
+ *
+ * Randomness: every random value the protocol draws comes from
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by a 64-bit seed,
+ * with the counter layout of the PRF table below. The CUDA library implements
+ * the same generator from the same published definition on its own side.
+ */
+#ifndef IPC_ORACLE_H
+#define IPC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* PRF domains (high byte of counter word 3). */
+#define ORC_D_SHARE 1u /* client sharing randomness (App. C input sharing)            */
+#define ORC_D_ZA    2u /* arithmetic zero shares re-randomising the dot products       */
+#define ORC_D_AND   3u /* boolean zero shares of the AND gates of Lift and MSB         */
+#define ORC_D_INJ0  4u /* BitInject c_0 (seed_0)                                       */
+#define ORC_D_INJ2  5u /* BitInject c_2, w_0, w_1 (seed_2)                             */
+#define ORC_D_OR    6u /* boolean zero shares of the OR-tree AND gates                 */
+
+/* Gate numbering of the comparison circuit (D_AND counter). */
+#define ORC_LIFT_GATE0 0u  /* 33 gates of BitExtract(.,{17,16}) inside Lift      */
+#define ORC_MSB_GATE0 36u  /* 61 gates of BitExtract(.,{31}) for the MSB        */
+
+/* Philox4x32-10: out = Philox(key, ctr). */
+void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]);
+
+/* Code geometry and rotation. l = rows*cols*cell bits; bit index (r*cols+j)*cell+k.
+ * Rotation by shift s: out[r][j][k] = in[r][(j-s) mod cols][k]. */
+typedef struct {
+  uint32_t rows, cols, cell; /* 16, 200, 4 in the deployed system */
+  int32_t rot_lo;            /* first shift (-15) */
+  uint32_t R;                /* number of rotations (31); shift of index rho is rot_lo+rho */
+} orc_geom;
+
+void orc_rotate_u16(const orc_geom* g, const uint16_t* in, uint16_t* out, int32_t shift);
+void orc_rotate_bits(const orc_geom* g, const uint64_t* in, uint64_t* out, int32_t shift);
+
+/* Masked-bit encoding (Sec. 4.1.1) and client-side sharing (App. C). Bits are packed
+ * 64 per word, bit b of a row in word b/64 at position b%64. Output shares are
+ * [3][n][l] u16 for code and for mask. side = 0 for database rows, 1 for queries;
+ * idx0 is the global index of the first row (enters the PRF counter). */
+void orc_encode_share(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                      uint64_t client_seed, uint32_t side, uint32_t idx0,
+                      uint16_t* code_sh, uint16_t* mask_sh);
+
+/* Alg. 1 for one pair of packed rows: ml = |m & M|, hd = |(c ^ C) & m & M|. */
+void orc_plain_pair(const uint64_t* c, const uint64_t* m, const uint64_t* C, const uint64_t* M,
+                    uint32_t nwords, int32_t* ml, int32_t* hd);
+
+/* Alg. 1 with rotations over a database: for every query q, rotation rho, row i
+ * computes (ml, hd); ml_out/hd_out are [Q][R][s] (may be NULL). match_out[q] is the
+ * OR over rho, i of the rule: rule 0 = hd/ml < tau_num/tau_den with ml > 0 (Alg. 1);
+ * rule 1 = b*dot > a*ml with dot = ml - 2 hd, b = 2^16, a = thr_a (Alg. 3).
+ * threads > 1 uses OpenMP where the library was built with it. */
+void orc_plain_match(const orc_geom* g, const uint64_t* qc, const uint64_t* qm, uint32_t Q,
+                     const uint64_t* dc, const uint64_t* dm, uint32_t s,
+                     int rule, uint32_t tau_num, uint32_t tau_den, uint32_t thr_a,
+                     int32_t* ml_out, int32_t* hd_out, uint8_t* match_out, int threads);
+
+/* ---- 3-party replicated-sharing simulation (App. C, App. D, Alg. 3) ---- */
+
+typedef struct {
+  uint64_t seeds[3]; /* seed_j shared by parties j and j+1 */
+  uint32_t req;      /* request id entering every counter */
+  uint32_t thr_a;    /* a of the threshold a/b, b = 2^16 */
+} orc_mpc_cfg;
+
+typedef struct {
+  uint64_t and_gates;      /* boolean AND gates evaluated */
+  uint64_t bits_sent[3];   /* bits sent by each party */
+  uint32_t depth_lift;     /* rounds of the Lift of one comparison */
+  uint32_t depth_msb;      /* rounds of the MSB extraction of one comparison */
+  uint32_t depth_total;    /* rounds of one comparison from the dot products to its MSB */
+  uint32_t depth_or;       /* rounds of the OR tree of one query */
+  uint32_t and_lift, and_msb; /* gates per comparison */
+  uint32_t replication_errors; /* views that broke (x_i, x_{i-1}) consistency */
+} orc_stats;
+
+/* App. C dot product of DB row x (components [3][l]) with query y ([3][l], already
+ * rotated), re-randomised with the D_ZA zero share of (q, rho, i, vec). Writes the
+ * three additive components z_0,z_1,z_2 (z_i is what party i sends to i+1). */
+void orc_mpc_dot(const orc_mpc_cfg* cfg, const uint16_t* x, uint64_t x_stride,
+                 const uint16_t* y, uint64_t y_stride, uint32_t l,
+                 uint32_t q, uint32_t rho, uint32_t i, uint32_t vec, uint16_t z[3], orc_stats* st);
+
+/* One comparison: from the additive components of dot and ml over Z_{2^16}
+ * (after resharing) run Lift, ConstLift, a*ml' - b*dot' and BitExtract(.,{31}).
+ * Writes the three boolean components of the MSB (1 = match). Optionally returns the
+ * lifted ml' components (Z_{2^32}) and v components. */
+void orc_mpc_compare(const orc_mpc_cfg* cfg, const uint16_t dot[3], const uint16_t ml[3],
+                     uint32_t q, uint32_t rho, uint32_t i, uint8_t msb[3],
+                     uint32_t ml_lift[3], uint32_t v_out[3], orc_stats* st);
+
+/* BitExtract([x]_{2^32}, {m, m-1}) on explicit additive components, with the D_AND
+ * counter of (q, rho, i) and first gate number gate0. Returns bits m and m-1. */
+void orc_bit_extract(const orc_mpc_cfg* cfg, const uint32_t x[3], uint32_t m,
+                     uint32_t q, uint32_t rho, uint32_t i, uint32_t gate0,
+                     uint8_t top[3], uint8_t below[3], orc_stats* st);
+
+/* OR tree of one query over its MSB bit components msb[3][R][s] -> bit[3]. */
+void orc_or_tree(const orc_mpc_cfg* cfg, const uint8_t* msb, uint32_t R, uint32_t s,
+                 uint32_t q, uint8_t bit[3], orc_stats* st);
+
+/* Whole Alg. 3 for Q queries against s DB rows. Shares are [3][n][l] u16. Outputs
+ * (each may be NULL): z_code/z_mask [3][Q*R][s], msb [3][Q*R][s], bits [3][Q]. */
+void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
+                   const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
+                   const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
+                   uint16_t* z_code, uint16_t* z_mask, uint8_t* msb, uint8_t* bits,
+                   orc_stats* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
