@@ -1,0 +1,326 @@
+"""Benchmark of the share-domain iris uniqueness check on GB300.
+
+One step = one pass of the whole hot path over one query batch: query preparation (A2),
+the six share-domain ring GEMMs per resident database chunk (A3, three parties x code/mask),
+lift + threshold + MSB + in-block OR (A4-A8) per chunk, the rest of the OR tree (A8) and the
+copy of the bit components. Workload (default): 100,000 database rows x 32 queries x 31
+rotations, 12,800-bit codes, synthetic (seeded), database shares resident on the device.
+
+Prints one JSON line. `value` is comparisons/s of the int8 tensor-core path with the query
+shares already on the device, timed with CUDA events on the library's control stream;
+`e2e` is the same through host (pinned) buffers with the copies inside the timed region;
+`int32_path` is the plain CUDA-core path on the same workload. --impl reference times the
+CPU oracle (the 3-party simulation of Alg. 3) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "masked-HD comparisons/s, int8-limb TC vs plain int32 path; % of INT8 peak"
+UNIT = "comparisons/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-i32", action="store_true")
+    ap.add_argument("--cpu-sample-rows", type=int, default=2048)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): the 3-party simulation on a bounded sample.
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample(w: synth.Workload, rows: int):
+    import oracle
+    og = oracle.Geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
+    dc, dm = w.db_bits(np.arange(rows))
+    qc, qm = w.query_bits()
+    dbc, dbm = oracle.encode_share(dc, dm, w.l, w.db_share_seed, 0)
+    qsc, qsm = oracle.encode_share(qc[:1], qm[:1], w.l, w.q_share_seed, 1)
+    cfg = oracle.mpc_cfg(w.prf_seeds, req=1, thr_a=w.thr_a)
+
+    def step():
+        t = time.perf_counter()
+        oracle.mpc_match(cfg, og, dbc, dbm, qsc, qsm)
+        return time.perf_counter() - t
+
+    return step, rows * w.R, f"1 query x {w.R} rotations x {rows} database rows of the workload"
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    step, comps, sample = oracle_sample(w, max(64, args.cpu_sample_rows // 2))
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
+    total = sum(times)
+    value = comps * args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16/u32 ring (C, CPU)",
+        "data": "synthetic", "config": {"workload": w.name, "sample": sample},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def ncu_traffic(kernel: str, src: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return float(m.group(1)) if cur == h.group(1) else None
+
+
+def run_ours(args, w):
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    from paper_2405_04463_gb300.workload import load_workload, make_ctx, query_shares_gpu
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.cuda.current_device()
+
+    # ---- setup (untimed): resident database, query shares, contexts ----
+    ctxs = {"i8mma": make_ctx(w, path="i8mma", max_queries=w.Q)}
+    if not args.no_i32:
+        ctxs["i32"] = make_ctx(w, path="i32", max_queries=w.Q)
+    for c in ctxs.values():
+        load_workload(c, w, chunk=32768)
+    qcode, qmask = query_shares_gpu(w)
+    hcode = [qcode[j].cpu().pin_memory() for j in range(3)]
+    hmask = [qmask[j].cpu().pin_memory() for j in range(3)]
+    torch.cuda.synchronize()
+    n_chunks = (w.s + 65535) // 65536
+    launches_per_step = 6 + n_chunks * 7 + 2
+
+    def run_steps(ctx, k, host_inputs):
+        stream = torch.cuda.ExternalStream(ipc.ipc_ctx_stream(ctx))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        code = hcode if host_inputs else [qcode[j] for j in range(3)]
+        mask = hmask if host_inputs else [qmask[j] for j in range(3)]
+        bits = np.zeros(w.Q, np.uint8)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        rids = [ipc.submit_queries(ctx, code, mask, w.Q, 0 if host_inputs else 1) for _ in range(k)]
+        e1.record(stream)
+        for rid in rids:
+            ipc.fetch_match_bits(ctx, rid, bits, w.Q, -1)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / k, wall / k, bits.copy()
+
+    main = ctxs["i8mma"]
+    run_steps(main, args.warmup, False)
+    clocks = Clocks(dev)
+    clocks.start()
+    ms_i8, wall_i8, bits = run_steps(main, args.steps, False)
+    clk = clocks.stop()
+    run_steps(main, 1, True)
+    ms_e2e, wall_e2e, bits_e2e = run_steps(main, args.steps, True)
+    out_i32 = None
+    if "i32" in ctxs:
+        run_steps(ctxs["i32"], 1, False)
+        ms_i32, _, bits_i32 = run_steps(ctxs["i32"], args.steps, False)
+        out_i32 = {"value": w.comparisons * world / (ms_i32 * 1e-3), "ms_per_step": ms_i32,
+                   "bits_equal_to_int8_path": bool((bits_i32 == bits).all())}
+
+    # ---- dominant kernel alone: one i8 GEMM launch over a 65536-row chunk ----
+    l, N = w.l, w.Q * w.R
+    n_pad = (N + 127) // 128 * 128
+    rows = min(65536, w.s)
+    g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
+    planes = [torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda") for _ in range(4)]
+    blo = torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")
+    bhi = torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")
+    tags = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
+    z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def gemm_time(path, reps):
+        for _ in range(2):
+            ipc.ipc_ring_gemm(path, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            ipc.ipc_ring_gemm(path, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_i8 = gemm_time("i8mma", 5)
+    t_i32 = gemm_time("i32", 3) if not args.no_i32 else None
+    ops = 2.0 * 3 * N * rows * 2 * l          # 3 int8 products per ring multiply-add, 2 ops each
+    peak_mma = ipc.ipc_measure_peak(0)
+    peak_imad = ipc.ipc_measure_peak(1)
+    achieved = ops / (t_i8 * 1e-3) / 1e12
+    traffic = ncu_traffic("gemm_i8_kernel", os.path.join(ROOT, "paper_2405_04463_gb300", "csrc", "gemm_i8.cu"))
+    roofline = {"bound": "tensor", "kernel": "gemm_i8_kernel", "achieved": achieved, "peak": peak_mma,
+                "unit": "TOP/s", "frac": achieved / peak_mma, "traffic": traffic,
+                "peak_source": "measured live: register-only mma.sync.m16n8k32 s8 loop (ipc_measure_peak); "
+                               "MEASURED_PEAKS.json has no int8 figure",
+                "launch_ms": t_i8, "ops_per_launch": ops}
+    i32_kernel = None
+    if t_i32:
+        imads = 1.0 * N * rows * 2 * l
+        i32_kernel = {"kernel": "gemm_i32_kernel", "bound": "alu", "achieved": imads / (t_i32 * 1e-3) / 1e12,
+                      "peak": peak_imad, "unit": "T IMAD/s", "frac": imads / (t_i32 * 1e-3) / 1e12 / peak_imad,
+                      "launch_ms": t_i32}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        step, comps, sample = oracle_sample(w, args.cpu_sample_rows)
+        secs = step()
+        cpu = {"value": comps / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs}
+
+    for c in ctxs.values():
+        ipc.ipc_destroy(c)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    value = w.comparisons * world / (ms_i8 * 1e-3)
+    h2d = 2 * 3 * w.Q * w.l * 2
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_i8, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": w.name, "db_rows": w.s, "queries": w.Q, "rotations": w.R, "code_bits": w.l,
+                   "planted": w.planted, "path": "i8mma (mma.sync s8, TMA)", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: resident shares 12 B x rows x 12800 = "
+                         f"{12 * w.s * w.l / 1e9:.1f} GB"},
+        "int8_peak_frac_step": value * 921600 / (peak_mma * 1e12),
+        "int32_path": out_i32,
+        "ratio_int8_vs_int32": (value / out_i32["value"]) if out_i32 else None,
+        "roofline": roofline,
+        "int32_kernel": i32_kernel,
+        "cpu_baseline": cpu,
+        "e2e": {"value": w.comparisons * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 3 * w.Q, "wall_ms_per_step": 1e3 * wall_e2e,
+                "bits_equal": bool((bits_e2e == bits).all())},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "match_bits": int(bits.sum()),
+        "measured_peaks": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+    }
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    w = synth.workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,278 @@
+/*
+ * ipcheck.h -- C ABI of the GB300 share-domain iris uniqueness check.
+ *
+ * The library evaluates, for the 3-party replicated secret sharing of
+ * arXiv 2405.04463 ("Large-Scale MPC: Scaling Private Iris Code Uniqueness
+ * Checks to Millions of Users"), the data-parallel hot path of Alg. 3:
+ * share-domain masked dot products over Z_{2^16} (query code/mask shares
+ * against every database share, for every rotation), the lift of the mask
+ * length to Z_{2^32}, the threshold test as an MSB extraction, and the OR
+ * tree to one shared match bit per query. All three parties are simulated on
+ * one GPU; their messages are device buffers.
+ *
+ * Conventions used throughout:
+ *  - Parties are numbered 0, 1, 2 (the paper counts from 1). A value x in
+ *    Z_{2^k} has additive components x_0, x_1, x_2 (x = sum mod 2^k); party i
+ *    holds the replicated pair (x_i, x_{i-1}) (App. C). Boolean sharings use XOR.
+ *  - seeds[j] is the PRF key shared by parties j and j+1 (App. D, 3OT and
+ *    BitInject). Every random value the protocol draws is one output word of
+ *    Philox4x32-10 (Salmon et al., SC'11) keyed by a seed, with the counter
+ *    layout documented at each entry point, so results are reproducible and
+ *    independent of launch shapes.
+ *  - A code has l = rows*cols*cell bits, bit (r*cols + j)*cell + k; the deployed
+ *    geometry is 16 x 200 x 4 = 12800 (Sec. 3). Rotation index rho in [0, R)
+ *    shifts the 200-column axis by s = rot_lo + rho: out[r][j][k] =
+ *    in[r][(j - s) mod cols][k].
+ *  - Column n of a query batch is (query q, rotation rho) with n = q*R + rho.
+ *    Its PRF tag is col_tags[2n] = request id, col_tags[2n+1] = (q << 5) | rho.
+ *  - Unless stated otherwise pointers are DEVICE pointers owned by the caller,
+ *    calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and return IPC_OK or a negative IPC_E* code without launching
+ *    anything. Errors of an earlier asynchronous call surface at the next call
+ *    that synchronises (ipc_status, fetch_*).
+ *
+ * Thread safety: the stage-level calls are reentrant. A context must not be
+ * used from two host threads at once.
+ */
+#ifndef IPCHECK_H
+#define IPCHECK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IPC_OK 0
+#define IPC_EINVAL -1     /* bad argument (size, alignment, geometry) */
+#define IPC_ENOMEM -2     /* device or host allocation failed, or admission refused */
+#define IPC_ECUDA -3      /* a CUDA runtime call failed (see ipc_last_error) */
+#define IPC_ETIMEOUT -4   /* fetch_* gave up waiting */
+#define IPC_EAGAIN -5     /* request not admitted now; retry later */
+#define IPC_ENOTFOUND -6  /* unknown request id */
+#define IPC_EDEVICE -7    /* a kernel hit a bounded wait limit and returned early */
+#define IPC_ENOSYS -8     /* feature not built for this device */
+
+#define IPC_PATH_I8MMA 0  /* int8 limb GEMM on the tensor cores (mma.sync s8, TMA-fed) */
+#define IPC_PATH_I32 1    /* plain int32 CUDA-core ring GEMM (IMAD) */
+
+/* PRF domains: high byte of Philox counter word 3. */
+#define IPC_D_SHARE 1u
+#define IPC_D_ZA 2u
+#define IPC_D_AND 3u
+#define IPC_D_INJ0 4u
+#define IPC_D_INJ2 5u
+#define IPC_D_OR 6u
+
+typedef struct {
+  uint32_t rows, cols, cell; /* code geometry; l = rows*cols*cell, a multiple of 128 */
+  int32_t rot_lo;            /* shift of rotation 0 (-15 for the deployed +-15 range) */
+  uint32_t R;                /* number of rotations, 1..31 */
+} ipc_geom;
+
+/* ======================================================================== */
+/* Stage-level entry points (one per step of the hot path).                  */
+/* ======================================================================== */
+
+/*
+ * A0 -- input encoding and sharing (client side; Sec. 4.1.1, App. C).
+ * code_bits/mask_bits: [n][ceil(l/64)] uint64, bit b of row r in word b/64 at
+ * position b%64. Each code bit becomes the masked bit m - 2(c AND m) in
+ * Z_{2^16} (T=-1, U=0, F=+1), each mask bit 0/1; each value x is split as
+ * x = x_0 + x_1 + x_2 with x_0 = low and x_1 = high 16 bits of word (b%4) of
+ * Philox(client_seed, (b/4, idx0 + r, side<<8 | vec, IPC_D_SHARE<<24)),
+ * vec = 0 for code, 1 for mask; side = 0 for database rows, 1 for queries.
+ * Output code_sh, mask_sh: [3][n][l] uint16 (component-major).
+ * Errors: IPC_EINVAL if l is 0 or n*l overflows.
+ */
+int ipc_encode_share(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                     uint64_t client_seed, uint32_t side, uint32_t idx0, uint16_t* code_sh,
+                     uint16_t* mask_sh, void* stream);
+
+/*
+ * A1 -- resident limb planes. Splits each Z_{2^16} element x into balanced
+ * signed bytes lo = (int8)(x & 0xFF), hi = (int8)((x - lo) >> 8) so that
+ * x = 256*hi + lo (mod 2^16) (the operand decomposition of Sec. 6.1, here
+ * with signed limbs so that no fix-up kernels are needed). x: count uint16;
+ * lo, hi: count int8 each. Errors: IPC_EINVAL if count is 0.
+ */
+int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8_t* hi, void* stream);
+
+/*
+ * A2 -- query preparation for one party. y: [3][Q][l] uint16, the additive
+ * components of one query vector (code or mask), unrotated. For party i and
+ * column n = q*R + rho it writes the row
+ *     B_i[n] = [ rot_rho(y_i + y_{i-1}) | rot_rho(y_i) ]   (length 2l)
+ * so that [x_i | x_{i-1}] . B_i[n] = x_i y_i + x_i y_{i-1} + x_{i-1} y_i, the
+ * App. C product, with the database kept as raw components. Rotation is
+ * linear, so rotating shares rotates the secret. Rows n >= Q*R up to n_pad
+ * are zero. b_lo, b_hi: [n_pad][2l] int8 limb planes as in A1.
+ * Errors: IPC_EINVAL if party > 2, n_pad < Q*R or the geometry is invalid.
+ */
+int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
+                   int8_t* b_hi, uint32_t n_pad, void* stream);
+
+/*
+ * A3 -- share-domain dot products of one party for one vector (App. C), as a
+ * ring GEMM over Z_{2^16}:
+ *     z[n][r] = sum_k [x_i | x_{i-1}][r][k] * B_i[n][k] + r_i(n, r)  (mod 2^16)
+ * x_lo[0], x_hi[0]: limb planes of the party's own database component x_i;
+ * x_lo[1], x_hi[1]: those of x_{i-1}; each [x_rows][l] int8, row-contiguous.
+ * b_lo, b_hi: A2 output [n_pad][2l] int8 (n_pad >= n_cols, multiple of 128).
+ * r_i = F(seed_own) - F(seed_prev) mod 2^16 is party i's arithmetic zero share
+ * (App. C); F(seed) for global row g = row0 + r is half (g & 1) of word
+ * ((g >> 1) & 3) of Philox(seed, (g >> 3, col_tags[2n+1], col_tags[2n],
+ * IPC_D_ZA<<24 | vec)). z: [n_cols][ldz] uint16, column-major in the sense
+ * that the rows of one query column are contiguous; z_i is the message party
+ * i sends to party i+1 (resharing). path selects the int8 tensor-core GEMM
+ * (exact: |int32 partial sums| < 2^30) or the int32 CUDA-core GEMM; both give
+ * identical results. Errors: IPC_EINVAL for l not a multiple of 128, odd
+ * ldz, ldz < x_rows, or unaligned pointers (16 B); IPC_ECUDA if the tensor
+ * map cannot be encoded.
+ */
+int ipc_ring_gemm(int path, const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows,
+                  const int8_t* b_lo, const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                  const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
+                  uint16_t* z, size_t ldz, uint64_t row0, void* stream);
+
+/*
+ * A4-A8 (per comparison, and the OR tree inside aligned row blocks).
+ * z_code[j], z_mask[j]: the j-th additive components over Z_{2^16} of the
+ * code dot and of ml, [n_cols][ldz] uint16 (A3 outputs of parties 0..2).
+ * For every column n and row r < n_rows (global row g = row0 + r):
+ *   Lift (Sec. 5.1, App. D): BitExtract of bits 17, 16 of ml_0+ml_1+ml_2 over
+ *     Z_{2^32} (33 ANDs), BitInject of bit 17 into Z_{2^15} and bit 16 into
+ *     Z_{2^16} with the 3-party OT, ConstLift by 2^17 and 2^16, subtract;
+ *   ConstLift of the dot by b = 2^16; v = thr_a*ml' - 2^16*dot over Z_{2^32};
+ *   MSB by BitExtract(v, {31}) (61 ANDs; App. D). MSB = 1 means a match.
+ * Boolean AND gates are the App. C product over F_2 with zero share
+ * F_j(gate) = bit (g & 31) of word (G & 3) of Philox(seed_j, (g >> 5,
+ * col_tags[2n+1], col_tags[2n], IPC_D_AND<<24 | G>>2)); Lift gates are
+ * G = 0..32 (full-adder layer positions 0..16, then ripple positions 1..16),
+ * MSB gates G = 36..96 (positions 0..30, then 1..30). BitInject draws c_0 as
+ * half (k-bit) of word (g & 3) of Philox(seed_0, (g >> 2, tag, req,
+ * IPC_D_INJ0<<24)) -- low half for bit 17, high half for bit 16 -- and c_2,
+ * w_0, w_1 from words 0, 1, 2 of Philox(seed_2, (g, tag, req, IPC_D_INJ2<<24)).
+ * The MSB bits of the rows of 32*2^log2_block_words consecutive rows (rows
+ * past n_rows are the public 0) are OR-reduced by the fixed pairwise tree of
+ * ipc_or_finalize; each block's root words (three components, 32 lanes) go to
+ * roots[j][n][b], b = (row0 >> (5 + log2_block_words)) + local block.
+ * msb_out (optional, may be NULL): [3][n_cols][ld_msb] uint8 components of
+ * every comparison's MSB. row0 must be a multiple of 32 << log2_block_words.
+ * Errors: IPC_EINVAL for bad sizes or log2_block_words > 5.
+ */
+int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz, uint32_t n_cols,
+                size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
+                uint32_t log2_block_words, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
+                void* stream);
+
+/*
+ * A8 -- rest of the OR tree (Sec. 4.2: x OR y = x + y + xy, evaluated as a
+ * binary tree). The tree has a fixed shape so that shares do not depend on
+ * launch shapes: per column, the 32-row words g = 0, 1, ... are combined
+ * pairwise level by level (pair j of level L ORs nodes 2j, 2j+1; an odd last
+ * node moves up unchanged), then per query the R column words are combined the
+ * same way, then the 32 lanes are folded in halves (16, 8, 4, 2, 1). The AND
+ * of pair j at level L uses word 0 of Philox(seed_j', (j, tag, req,
+ * IPC_D_OR<<24 | stage<<16 | L)), lane bit = lane, with stage 1 and tag
+ * (q<<5)|rho for rows, stage 2 and tag q<<5 for rotations, stage 3 (j = 0)
+ * for the fold. roots: [3][Q*R][ld_roots] uint32 from ipc_compare, n_blocks
+ * per column; it is overwritten (scratch). bit_shares: [3][Q] uint8 output
+ * components of the OR bit of each query (1 = some row matched).
+ */
+int ipc_or_finalize(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t log2_block_words, uint32_t Q,
+                    uint32_t R, const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares,
+                    void* stream);
+
+/* Reads and clears the device status word of the calling device after
+ * synchronising it: IPC_OK, or IPC_EDEVICE if a kernel gave up a bounded wait. */
+int ipc_status(void);
+
+/* ======================================================================== */
+/* Context-level API: resident database, request submission and fetch.      */
+/* ======================================================================== */
+
+typedef struct ipc_ctx ipc_ctx;
+
+typedef struct {
+  ipc_geom geom;            /* {16, 200, 4, -15, 31} for the deployed system */
+  uint32_t thr_a;           /* a of the threshold a/b with b = 2^16; 16384 for MATCH_RATIO 0.375 */
+  int32_t path;             /* IPC_PATH_I8MMA or IPC_PATH_I32 */
+  uint32_t db_chunk_rows;   /* rows per resident chunk and pipeline step; multiple of 1024; 0 = 65536 */
+  uint32_t max_queries;     /* largest request accepted by submit_queries; 0 = 256 */
+  uint64_t seeds[3];        /* pairwise PRF seeds; seeds[j] shared by parties j and j+1 */
+  uint32_t keep_distances;  /* nonzero: keep each request's dot products for fetch_distances */
+  int32_t device;           /* CUDA device ordinal */
+} ipc_config;
+
+/* Creates a context on cfg->device with per-party streams. Ownership of *out
+ * passes to the caller (release with ipc_destroy). Errors: IPC_EINVAL for an
+ * invalid geometry or path, IPC_ECUDA if the device cannot be used. */
+int ipc_create(const ipc_config* cfg, ipc_ctx** out);
+
+/* Appends n_rows database rows. code[j], mask[j]: [n_rows][l] uint16, the j-th
+ * additive components (A0 output layout per component); host memory if
+ * src_is_device == 0, else device memory. The library copies them into its
+ * resident int8 limb planes (A1); the caller keeps ownership. Returns IPC_OK,
+ * IPC_ENOMEM when the device cannot hold the rows (nothing is appended). */
+int load_db_shares(ipc_ctx* ctx, const uint16_t* const code[3], const uint16_t* const mask[3], size_t n_rows,
+                   int src_is_device);
+
+/* Submits n_queries unrotated queries, code[j]/mask[j]: [n_queries][l] uint16
+ * (host if src_is_device == 0, else device). Non-blocking: the inputs may be
+ * reused on return; the request runs on the device against every resident
+ * row and all R rotations. *req_id receives the request id (also the PRF
+ * request tag). Errors: IPC_EINVAL (0 or > max_queries), IPC_ENOMEM. */
+int submit_queries(ipc_ctx* ctx, const uint16_t* const code[3], const uint16_t* const mask[3], size_t n_queries,
+                   int src_is_device, uint64_t* req_id);
+
+/* Waits up to timeout_ms (< 0: forever) for request req_id and writes the
+ * opened match bit of each query to host bits_out[n_queries] (1 = a database
+ * row matched at some rotation, i.e. the query is not unique). The request is
+ * released afterwards. Errors: IPC_ETIMEOUT (request kept), IPC_ENOTFOUND,
+ * IPC_EINVAL (n_queries mismatch), IPC_EDEVICE. */
+int fetch_match_bits(ipc_ctx* ctx, uint64_t req_id, uint8_t* bits_out, size_t n_queries, int timeout_ms);
+
+/* As fetch_match_bits but writes the three boolean components [3][n_queries]
+ * (host) without opening them, and keeps the request. */
+int fetch_bit_shares(ipc_ctx* ctx, uint64_t req_id, uint8_t* shares_out, size_t n_queries, int timeout_ms);
+
+/* Debug: reconstructed code dot (int16, i.e. ml - 2 hd) and mask length ml of
+ * query q at rotation rho for database rows [row_begin, row_end), host
+ * outputs. Needs keep_distances. Waits for the request. Errors: IPC_EINVAL,
+ * IPC_ENOTFOUND, IPC_ENOSYS (distances not kept). */
+int fetch_distances(ipc_ctx* ctx, uint64_t req_id, uint32_t q, uint32_t rho, size_t row_begin, size_t row_end,
+                    int16_t* dot, uint16_t* ml);
+
+/* Releases a request that will not be fetched. */
+int ipc_release(ipc_ctx* ctx, uint64_t req_id);
+
+/* Number of resident database rows. */
+size_t ipc_db_rows(const ipc_ctx* ctx);
+
+/* The context's control stream (cudaStream_t): every request's work is joined into it
+ * before its completion event, so events recorded on it before submit_queries and after it
+ * bracket the request's device time. Owned by the context. */
+void* ipc_ctx_stream(const ipc_ctx* ctx);
+
+/* Frees every device and host resource of the context. */
+void ipc_destroy(ipc_ctx* ctx);
+
+/* Text of the last error on this context (or of the last stage-level error
+ * of the calling thread when ctx is NULL). Valid until the next call. */
+const char* ipc_last_error(const ipc_ctx* ctx);
+
+/* ======================================================================== */
+/* Measurement utility (no counterpart in the paper).                        */
+/* ======================================================================== */
+
+/* Measures a roofline denominator on the current device with a register-only loop:
+ * what = 0 -> mma.sync.m16n8k32 s8 rate in TOP/s (2 ops per multiply-add);
+ * what = 1 -> 32-bit IMAD rate in T IMAD/s. Synchronous; allocates a small buffer. */
+int ipc_measure_peak(int what, void* stream, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,433 @@
+// A4-A8 -- the comparison phase of Alg. 3 on reshared dot products, bit-sliced.
+//
+// One thread simulates the three parties for one query column and a block of
+// 32-row words: 32 comparisons share one 32-bit word per bit position and share
+// component. The arithmetic-to-boolean steps (ShareSplit, full-adder layer,
+// ripple-carry BinAdd; App. D) then run 32 comparisons per logic instruction.
+// Party p only ever combines its own pair of components (c_p, c_{p-1}) and the
+// PRF outputs of its two seeds, as in the App. C product.
+#include "common.cuh"
+
+namespace ipc {
+namespace {
+
+constexpr int CT = 64;         // threads per CTA
+constexpr int LIFT_GATE0 = 0;  // 33 gates (17 full-adder layer, 16 ripple)
+constexpr int MSB_GATE0 = 36;  // 61 gates (31 full-adder layer, 30 ripple)
+
+struct B3 {
+  uint32_t c0, c1, c2;  // components of a boolean sharing of 32 lanes
+};
+
+__device__ __forceinline__ B3 bx(const B3& a, const B3& b) { return {a.c0 ^ b.c0, a.c1 ^ b.c1, a.c2 ^ b.c2}; }
+
+// App. C product over F_2, each party from its own view plus alpha_p = F_p ^ F_{p-1}.
+__device__ __forceinline__ B3 band(const B3& x, const B3& y, uint32_t F0, uint32_t F1, uint32_t F2) {
+  B3 z;
+  z.c0 = (x.c0 & y.c0) ^ (x.c0 & y.c2) ^ (x.c2 & y.c0) ^ F0 ^ F2;
+  z.c1 = (x.c1 & y.c1) ^ (x.c1 & y.c0) ^ (x.c0 & y.c1) ^ F1 ^ F0;
+  z.c2 = (x.c2 & y.c2) ^ (x.c2 & y.c1) ^ (x.c1 & y.c2) ^ F2 ^ F1;
+  return z;
+}
+
+struct Seeds {
+  uint64_t s[3];
+};
+
+// Zero-share words of the AND gates of one 32-row word: gate G uses word (G & 3) of
+// Philox(seed_j, (g >> 5, tag, req, D_AND << 24 | G >> 2)).
+struct GateRng {
+  uint32_t c0, tag, req;
+  uint4 w[3];
+  __device__ __forceinline__ void refresh(const Seeds& sd, uint32_t quad) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) w[j] = philox(c0, tag, req, (IPC_D_AND << 24) | quad, sd.s[j]);
+  }
+  __device__ __forceinline__ void get(const Seeds& sd, uint32_t gate, bool first, uint32_t& F0, uint32_t& F1,
+                                      uint32_t& F2) {
+    if (first || (gate & 3u) == 0) refresh(sd, gate >> 2);
+    F0 = word_of(w[0], gate & 3u);
+    F1 = word_of(w[1], gate & 3u);
+    F2 = word_of(w[2], gate & 3u);
+  }
+};
+
+// BitExtract(x, {M, M-1}) over bit-sliced inputs: X(j, b) is word b of component j
+// (b > top_in gives 0). Full-adder layer on positions 0..M-1 (gates G0 + b), the sum
+// only at position M; ripple BinAdd of (carries << 1) and sums, positions 1..M-1 with
+// gates G0 + M + b - 1; r[M] = a ^ s ^ carry. Both layers are streamed by position.
+template <int M, int G0, typename Xf>
+__device__ __forceinline__ void bit_extract(const Seeds& sd, GateRng& fa, GateRng& rc, Xf X, B3& top, B3& below) {
+  B3 carry = {0u, 0u, 0u}, cprev = {0u, 0u, 0u};
+  below = {0u, 0u, 0u};
+#pragma unroll
+  for (int b = 0; b <= M; ++b) {
+    const B3 x0 = {X(0, b), 0u, 0u}, x1 = {0u, X(1, b), 0u}, x2 = {0u, 0u, X(2, b)};
+    B3 s, c = {0u, 0u, 0u};
+    if (b < M) {
+      const B3 t1 = bx(x0, x2), t2 = bx(x1, x2);
+      s = bx(t1, x1);
+      uint32_t F0, F1, F2;
+      fa.get(sd, G0 + b, b == 0, F0, F1, F2);
+      c = bx(band(t1, t2, F0, F1, F2), x2);
+    } else {
+      s = bx(bx(x0, x1), x2);
+    }
+    if (b == 0) {
+      if (M == 1) below = s;
+    } else if (b < M) {
+      const B3 t1 = bx(cprev, carry), t2 = bx(s, carry);
+      const B3 sum = bx(t1, s);
+      uint32_t F0, F1, F2;
+      rc.get(sd, G0 + M + b - 1, b == 1, F0, F1, F2);
+      carry = bx(band(t1, t2, F0, F1, F2), carry);
+      if (b == M - 1) below = sum;
+    } else {
+      top = bx(bx(cprev, s), carry);
+    }
+    cprev = c;
+  }
+}
+
+// In-register 32x32 bit transpose: afterwards bit i of a[j] is the former bit j of a[i].
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int j = 16 >> st;
+    const uint32_t m = masks[st];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & j) continue;
+      const uint32_t t = ((a[k] >> j) ^ a[k + j]) & m;
+      a[k] ^= t << j;
+      a[k + j] ^= t;
+    }
+  }
+}
+
+struct CmpParams {
+  const uint16_t* zc[3];
+  const uint16_t* zm[3];
+  uint64_t ldz;
+  uint32_t n_cols;
+  uint64_t n_rows;
+  uint64_t row0;
+  const uint32_t* col_tags;
+  Seeds seeds;
+  uint32_t thr_a;
+  uint32_t p;  // log2 words per block
+  uint32_t n_blocks;
+  uint32_t* roots;
+  uint64_t ld_roots;
+  uint8_t* msb_out;
+  uint64_t ld_msb;
+};
+
+// Shared memory per thread (index [slot][threadIdx.x], conflict-free):
+//   raw ml / dot: 3 x 16 words each (two u16 per word), X (lift input words, later v words): 96,
+//   OR stack: 3 x 6.
+constexpr int S_RAWML = 0, S_RAWDOT = 48, S_X = 96, S_STK = 192, S_WORDS = 210;
+
+__device__ __forceinline__ B3 bor(const Seeds& sd, const B3& a, const B3& b, uint32_t j, uint32_t tag, uint32_t req,
+                                  uint32_t c3) {
+  const uint32_t F0 = philox(j, tag, req, c3, sd.s[0]).x;
+  const uint32_t F1 = philox(j, tag, req, c3, sd.s[1]).x;
+  const uint32_t F2 = philox(j, tag, req, c3, sd.s[2]).x;
+  return bx(bx(a, b), band(a, b, F0, F1, F2));
+}
+
+__global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
+  extern __shared__ uint32_t sm[];  // [S_WORDS][CT]
+  const uint32_t tid = threadIdx.x;
+  auto S = [&](int slot) -> uint32_t& { return sm[slot * CT + tid]; };
+  const uint64_t gtid = blockIdx.x * static_cast<uint64_t>(CT) + tid;
+  if (gtid >= static_cast<uint64_t>(P.n_cols) * P.n_blocks) return;
+  const uint32_t n = static_cast<uint32_t>(gtid % P.n_cols);
+  const uint32_t blk = static_cast<uint32_t>(gtid / P.n_cols);
+  const uint32_t req = P.col_tags[2 * n], tag = P.col_tags[2 * n + 1];
+  const uint32_t words_per_block = 1u << P.p;
+  const uint64_t blk_row = static_cast<uint64_t>(blk) << (5 + P.p);  // local first row of this block
+  const uint64_t rem_words = (P.n_rows - blk_row + 31) >> 5;
+  const uint32_t nwords = static_cast<uint32_t>(rem_words < words_per_block ? rem_words : words_per_block);
+  const uint64_t gword0 = (P.row0 + blk_row) >> 5;  // global index of the first word
+
+  uint32_t valid_levels = 0;
+  for (uint32_t w = 0; w < nwords; ++w) {
+    const uint64_t lrow = blk_row + 32ull * w;
+    const uint64_t grow = P.row0 + lrow;
+    const uint32_t nvalid = static_cast<uint32_t>(P.n_rows - lrow < 32 ? P.n_rows - lrow : 32);
+    const uint32_t lane_mask = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+    // ---- load the 32 rows of this word (3 components of ml and of dot) ----
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint16_t* pm = P.zm[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+      const uint16_t* pd = P.zc[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+      if (nvalid == 32) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const uint4 a = reinterpret_cast<const uint4*>(pm)[v];
+          const uint4 b = reinterpret_cast<const uint4*>(pd)[v];
+          S(S_RAWML + 16 * j + 4 * v + 0) = a.x;
+          S(S_RAWML + 16 * j + 4 * v + 1) = a.y;
+          S(S_RAWML + 16 * j + 4 * v + 2) = a.z;
+          S(S_RAWML + 16 * j + 4 * v + 3) = a.w;
+          S(S_RAWDOT + 16 * j + 4 * v + 0) = b.x;
+          S(S_RAWDOT + 16 * j + 4 * v + 1) = b.y;
+          S(S_RAWDOT + 16 * j + 4 * v + 2) = b.z;
+          S(S_RAWDOT + 16 * j + 4 * v + 3) = b.w;
+        }
+      } else {
+        for (int v = 0; v < 16; ++v) {
+          const uint32_t r0 = 2 * v, r1 = 2 * v + 1;
+          const uint32_t m0 = r0 < nvalid ? pm[r0] : 0u, m1 = r1 < nvalid ? pm[r1] : 0u;
+          const uint32_t d0 = r0 < nvalid ? pd[r0] : 0u, d1 = r1 < nvalid ? pd[r1] : 0u;
+          S(S_RAWML + 16 * j + v) = m0 | (m1 << 16);
+          S(S_RAWDOT + 16 * j + v) = d0 | (d1 << 16);
+        }
+      }
+    }
+    // ---- ShareSplit of ml: bit-slice each component (bits 0..15) ----
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      uint32_t a[32];
+#pragma unroll
+      for (int v = 0; v < 16; ++v) {
+        const uint32_t x = S(S_RAWML + 16 * j + v);
+        a[2 * v] = x & 0xFFFFu;
+        a[2 * v + 1] = x >> 16;
+      }
+      transpose32(a);
+#pragma unroll
+      for (int b = 0; b < 16; ++b) S(S_X + 16 * j + b) = a[b];
+    }
+    GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
+    B3 r17, r16;
+    bit_extract<17, LIFT_GATE0>(
+        P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return b < 16 ? S(S_X + 16 * j + b) : 0u; }, r17, r16);
+    // ---- per comparison: BitInject (3-party OT), ConstLift, v = a*ml' - 2^16*dot ----
+    uint4 q0w = make_uint4(0u, 0u, 0u, 0u);  // D_INJ0 words: one Philox call per 4 rows
+    for (uint32_t l = 0; l < 32; ++l) {
+      const uint64_t g = grow + l;
+      if ((l & 3u) == 0) q0w = philox(static_cast<uint32_t>(g >> 2), tag, req, IPC_D_INJ0 << 24, P.seeds.s[0]);
+      const uint32_t inj0 = word_of(q0w, l & 3u);
+      const uint4 w2 = philox(static_cast<uint32_t>(g), tag, req, IPC_D_INJ2 << 24, P.seeds.s[2]);
+      uint32_t A[3], Bv[3];
+#pragma unroll
+      for (int which = 0; which < 2; ++which) {
+        const uint32_t k = which == 0 ? 15u : 16u;
+        const uint32_t mask = (1u << k) - 1u;
+        const uint32_t sh = which == 0 ? 0u : 16u;
+        const B3& bit = which == 0 ? r17 : r16;
+        const uint32_t x0 = (bit.c0 >> l) & 1u, x1 = (bit.c1 >> l) & 1u, x2 = (bit.c2 >> l) & 1u;
+        const uint32_t c0 = (inj0 >> sh) & mask, c2 = (w2.x >> sh) & mask;
+        const uint32_t w0 = (w2.y >> sh) & mask, w1 = (w2.z >> sh) & mask;
+        // party 0 (OT sender): m_beta = (beta ^ x_0 ^ x_2) - c_0 - c_2, masked k_beta = w_beta ^ m_beta
+        const uint32_t m0 = ((0u ^ x0 ^ x2) - c0 - c2) & mask;
+        const uint32_t m1 = ((1u ^ x0 ^ x2) - c0 - c2) & mask;
+        const uint32_t k0 = w0 ^ m0, k1 = w1 ^ m1;
+        // party 2 (helper) sends w_{x_1}; party 1 (receiver) unmasks k_{x_1}
+        const uint32_t wsel = x1 ? w1 : w0;
+        const uint32_t c1 = (wsel ^ (x1 ? k1 : k0)) & mask;
+        uint32_t* out = which == 0 ? A : Bv;
+        out[0] = c0;
+        out[1] = c1;
+        out[2] = c2;
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const uint32_t mlw = S(S_RAWML + 16 * j + (l >> 1)), dw = S(S_RAWDOT + 16 * j + (l >> 1));
+        const uint32_t ml = (mlw >> (16 * (l & 1))) & 0xFFFFu, dt = (dw >> (16 * (l & 1))) & 0xFFFFu;
+        const uint32_t mll = ml - (A[j] << 17) - (Bv[j] << 16);
+        S(S_X + 32 * j + l) = P.thr_a * mll - (dt << 16);
+      }
+    }
+    // ---- MSB: bit-slice v and BitExtract(v, {31}) ----
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      uint32_t a[32];
+#pragma unroll
+      for (int v = 0; v < 32; ++v) a[v] = S(S_X + 32 * j + v);
+      transpose32(a);
+#pragma unroll
+      for (int v = 0; v < 32; ++v) S(S_X + 32 * j + v) = a[v];
+    }
+    B3 msb, b30;
+    GateRng fa2{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc2{static_cast<uint32_t>(grow >> 5), tag, req, {}};
+    bit_extract<31, MSB_GATE0>(P.seeds, fa2, rc2, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); },
+                               msb, b30);
+    // rows past the end are the public 0 of the OR tree
+    msb.c0 &= lane_mask;
+    msb.c1 &= lane_mask;
+    msb.c2 &= lane_mask;
+    if (P.msb_out) {
+      for (uint32_t l = 0; l < nvalid; ++l) {
+        const uint64_t at = static_cast<uint64_t>(n) * P.ld_msb + lrow + l;
+        const uint64_t plane = static_cast<uint64_t>(P.n_cols) * P.ld_msb;
+        P.msb_out[at] = (msb.c0 >> l) & 1u;
+        P.msb_out[plane + at] = (msb.c1 >> l) & 1u;
+        P.msb_out[2 * plane + at] = (msb.c2 >> l) & 1u;
+      }
+    }
+    // ---- OR tree inside the aligned block (binary counter over word indices) ----
+    B3 cur = msb;
+    uint64_t idx = gword0 + w;
+    uint32_t lvl = 0;
+    while (lvl < P.p && (idx & 1u) && (valid_levels >> lvl & 1u)) {
+      const B3 left = {S(S_STK + 3 * lvl), S(S_STK + 3 * lvl + 1), S(S_STK + 3 * lvl + 2)};
+      cur = bor(P.seeds, left, cur, static_cast<uint32_t>(idx >> 1), tag, req,
+                (IPC_D_OR << 24) | (1u << 16) | (lvl + 1));
+      valid_levels &= ~(1u << lvl);
+      ++lvl;
+      idx >>= 1;
+    }
+    S(S_STK + 3 * lvl) = cur.c0;
+    S(S_STK + 3 * lvl + 1) = cur.c1;
+    S(S_STK + 3 * lvl + 2) = cur.c2;
+    valid_levels |= 1u << lvl;
+  }
+  // ---- block root: a full block ends at level p; a ragged block is flushed upwards ----
+  B3 root = {0u, 0u, 0u};
+  if (valid_levels >> P.p & 1u) {
+    root = {S(S_STK + 3 * P.p), S(S_STK + 3 * P.p + 1), S(S_STK + 3 * P.p + 2)};
+  } else {
+    bool have = false;
+    uint64_t idx = 0;
+    for (uint32_t lvl = 0; lvl < P.p; ++lvl) {
+      if (have) {
+        if (valid_levels >> lvl & 1u) {
+          const B3 left = {S(S_STK + 3 * lvl), S(S_STK + 3 * lvl + 1), S(S_STK + 3 * lvl + 2)};
+          root = bor(P.seeds, left, root, static_cast<uint32_t>(idx >> 1), tag, req,
+                     (IPC_D_OR << 24) | (1u << 16) | (lvl + 1));
+        }
+        idx >>= 1;
+      } else if (valid_levels >> lvl & 1u) {
+        root = {S(S_STK + 3 * lvl), S(S_STK + 3 * lvl + 1), S(S_STK + 3 * lvl + 2)};
+        // index of this entry at level lvl: its words start after the higher entries of the block
+        const uint64_t cnt = nwords;
+        const uint64_t start = gword0 + (cnt & ~((2ull << lvl) - 1ull));
+        idx = start >> lvl;
+        have = true;
+        idx >>= 1;
+      }
+    }
+  }
+  const uint64_t bglob = (P.row0 >> (5 + P.p)) + blk;
+  const uint64_t plane = static_cast<uint64_t>(P.n_cols) * P.ld_roots;
+  const uint64_t at = static_cast<uint64_t>(n) * P.ld_roots + bglob;
+  P.roots[at] = root.c0;
+  P.roots[plane + at] = root.c1;
+  P.roots[2 * plane + at] = root.c2;
+}
+
+// Rows stage of the OR tree above the block roots: per column, pairwise levels p+1, p+2, ...
+__global__ void or_rows_kernel(uint32_t* roots, uint64_t ld_roots, uint32_t n_cols, uint32_t n_blocks, uint32_t p,
+                               const uint32_t* col_tags, Seeds sd) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_cols) return;
+  const uint32_t req = col_tags[2 * n], tag = col_tags[2 * n + 1];
+  const uint64_t plane = static_cast<uint64_t>(n_cols) * ld_roots;
+  uint32_t* r0 = roots + static_cast<uint64_t>(n) * ld_roots;
+  uint32_t cnt = n_blocks, level = p + 1;
+  while (cnt > 1) {
+    const uint32_t half = cnt / 2;
+    for (uint32_t j = 0; j < half; ++j) {
+      const B3 a = {r0[2 * j], r0[plane + 2 * j], r0[2 * plane + 2 * j]};
+      const B3 b = {r0[2 * j + 1], r0[plane + 2 * j + 1], r0[2 * plane + 2 * j + 1]};
+      const B3 c = bor(sd, a, b, j, tag, req, (IPC_D_OR << 24) | (1u << 16) | level);
+      r0[j] = c.c0;
+      r0[plane + j] = c.c1;
+      r0[2 * plane + j] = c.c2;
+    }
+    if (cnt & 1u) {
+      r0[half] = r0[cnt - 1];
+      r0[plane + half] = r0[plane + cnt - 1];
+      r0[2 * plane + half] = r0[2 * plane + cnt - 1];
+    }
+    cnt = half + (cnt & 1u);
+    ++level;
+  }
+}
+
+// Rotation stage and lane fold, per query.
+__global__ void or_queries_kernel(const uint32_t* roots, uint64_t ld_roots, uint32_t n_cols, uint32_t Q, uint32_t R,
+                                  const uint32_t* col_tags, Seeds sd, uint8_t* bit_shares) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const uint64_t plane = static_cast<uint64_t>(n_cols) * ld_roots;
+  const uint32_t req = col_tags[2 * (q * R)], tag = col_tags[2 * (q * R) + 1] & ~31u;
+  B3 w[32];
+  for (uint32_t rho = 0; rho < R; ++rho) {
+    const uint64_t at = static_cast<uint64_t>(q * R + rho) * ld_roots;
+    w[rho] = {roots[at], roots[plane + at], roots[2 * plane + at]};
+  }
+  uint32_t cnt = R, level = 1;
+  while (cnt > 1) {
+    const uint32_t half = cnt / 2;
+    for (uint32_t j = 0; j < half; ++j) w[j] = bor(sd, w[2 * j], w[2 * j + 1], j, tag, req, (IPC_D_OR << 24) | (2u << 16) | level);
+    if (cnt & 1u) w[half] = w[cnt - 1];
+    cnt = half + (cnt & 1u);
+    ++level;
+  }
+  B3 x = w[0];
+  for (uint32_t L = 1; L <= 5; ++L) {
+    const uint32_t h = 32u >> L;
+    const uint32_t m = (1u << h) - 1u;
+    const B3 lo = {x.c0 & m, x.c1 & m, x.c2 & m};
+    const B3 hi = {(x.c0 >> h) & m, (x.c1 >> h) & m, (x.c2 >> h) & m};
+    const B3 y = bor(sd, lo, hi, 0u, tag, req, (IPC_D_OR << 24) | (3u << 16) | L);
+    x = {y.c0 & m, y.c1 & m, y.c2 & m};
+  }
+  bit_shares[q] = x.c0 & 1u;
+  bit_shares[Q + q] = x.c1 & 1u;
+  bit_shares[2 * Q + q] = x.c2 & 1u;
+}
+
+}  // namespace
+
+int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz, uint32_t n_cols,
+                   size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
+                   uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, cudaStream_t st) {
+  CmpParams P;
+  for (int j = 0; j < 3; ++j) {
+    P.zc[j] = z_code[j];
+    P.zm[j] = z_mask[j];
+    P.seeds.s[j] = seeds[j];
+  }
+  P.ldz = ldz;
+  P.n_cols = n_cols;
+  P.n_rows = n_rows;
+  P.row0 = row0;
+  P.col_tags = col_tags;
+  P.thr_a = thr_a;
+  P.p = p;
+  P.n_blocks = static_cast<uint32_t>((n_rows + (32ull << p) - 1) >> (5 + p));
+  P.roots = roots;
+  P.ld_roots = ld_roots;
+  P.msb_out = msb_out;
+  P.ld_msb = ld_msb;
+  const uint64_t threads = static_cast<uint64_t>(n_cols) * P.n_blocks;
+  const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
+  static bool attr = false;
+  if (!attr) {
+    IPC_CUDA_TRY(cudaFuncSetAttribute(compare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    attr = true;
+  }
+  compare_kernel<<<static_cast<unsigned>((threads + CT - 1) / CT), CT, smem, st>>>(P);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t p, uint32_t Q, uint32_t R,
+                       const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares, cudaStream_t st) {
+  Seeds sd;
+  for (int j = 0; j < 3; ++j) sd.s[j] = seeds[j];
+  const uint32_t n_cols = Q * R;
+  or_rows_kernel<<<(n_cols + 127) / 128, 128, 0, st>>>(roots, ld_roots, n_cols, n_blocks, p, col_tags, sd);
+  IPC_CUDA_TRY(cudaGetLastError());
+  or_queries_kernel<<<(Q + 63) / 64, 64, 0, st>>>(roots, ld_roots, n_cols, Q, R, col_tags, sd, bit_shares);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+}  // namespace ipc

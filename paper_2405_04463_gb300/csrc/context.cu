@@ -1,0 +1,449 @@
+// Context-level API: resident database chunks, per-party streams and request lifecycle.
+//
+// Pipeline of one request, per resident database chunk c (buffer set b = c % 2):
+//   party streams 0..2 : wait(compare of the chunk that last used set b)
+//                        A3 GEMM code, A3 GEMM mask  -> z[b][vec][party]   (party i's message to i+1)
+//   compare stream     : wait(all three parties), A4-A8 per comparison + in-block OR -> roots
+// then A8 (rest of the OR tree) and the copy of the three bit components to pinned host memory.
+// Queries are prepared once per request on the party streams (A2).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ipc {
+const char* thread_last_error();
+}
+
+using namespace ipc;
+
+namespace {
+
+constexpr uint32_t kLog2BlockWords = 5;  // 1024-row OR blocks inside ipc_compare
+
+struct Chunk {
+  int8_t* planes = nullptr;  // 12 planes [cap][l]: ((component * 2 + vec) * 2 + limb)
+  size_t cap = 0;
+  size_t rows = 0;
+  uint64_t row0 = 0;
+};
+
+struct Request {
+  uint64_t id = 0;
+  uint32_t Q = 0, N = 0, n_pad = 0;
+  int8_t* bq = nullptr;         // [party][vec][limb][n_pad][2l]
+  uint16_t* qstage = nullptr;   // [vec][3][Q][l] query shares
+  uint32_t* tags = nullptr;     // [N][2]
+  uint32_t* roots = nullptr;    // [3][N][ld_roots]
+  size_t ld_roots = 0;
+  uint8_t* shares_dev = nullptr;  // [3][Q]
+  uint8_t* shares_host = nullptr; // pinned [3][Q]
+  uint16_t* zkeep = nullptr;      // [vec][party][N][rows] when distances are kept
+  size_t zkeep_rows = 0;
+  cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct ipc_ctx {
+  ipc_config cfg{};
+  uint32_t l = 0;
+  cudaStream_t sp[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t sc = nullptr;
+  cudaEvent_t ev_setup = nullptr, ev_gemm[3][2] = {}, ev_cmp[2] = {};
+  std::vector<Chunk> chunks;
+  size_t rows = 0;
+  uint16_t* zbuf = nullptr;  // [2 sets][vec][party][zbuf_cols][chunk_rows]
+  size_t zbuf_cols = 0;
+  uint16_t* stage = nullptr;  // load staging [chunk_rows][l] u16
+  std::map<uint64_t, Request> reqs;
+  uint64_t next_id = 1;
+  std::string err;
+};
+
+namespace {
+
+int fail(ipc_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  set_error(msg);
+  return code;
+}
+
+int cfail(ipc_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, IPC_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define CTX_TRY(ctx, expr)                               \
+  do {                                                   \
+    cudaError_t e__ = (expr);                            \
+    if (e__ != cudaSuccess) return cfail(ctx, e__, #expr); \
+  } while (0)
+
+#define CTX_RC(ctx, expr)                          \
+  do {                                             \
+    int rc__ = (expr);                             \
+    if (rc__ != IPC_OK) {                          \
+      (ctx)->err = ipc::thread_last_error();       \
+      return rc__;                                 \
+    }                                              \
+  } while (0)
+
+int8_t* plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
+  return ch.planes + static_cast<size_t>((comp * 2 + vec) * 2 + limb) * ch.cap * c->l;
+}
+
+uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
+
+void free_request(ipc_ctx* c, Request& r) {
+  cudaFree(r.bq);
+  cudaFree(r.qstage);
+  cudaFree(r.tags);
+  cudaFree(r.roots);
+  cudaFree(r.shares_dev);
+  cudaFree(r.zkeep);
+  if (r.shares_host) cudaFreeHost(r.shares_host);
+  if (r.done) cudaEventDestroy(r.done);
+  (void)c;
+}
+
+int ensure_zbuf(ipc_ctx* c, uint32_t n_pad) {
+  if (c->cfg.keep_distances) return IPC_OK;
+  if (c->zbuf_cols >= n_pad) return IPC_OK;
+  CTX_TRY(c, cudaDeviceSynchronize());
+  cudaFree(c->zbuf);
+  c->zbuf = nullptr;
+  const size_t bytes = 2ull * 2 * 3 * n_pad * static_cast<size_t>(c->cfg.db_chunk_rows) * sizeof(uint16_t);
+  if (cudaMalloc(&c->zbuf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->zbuf_cols = 0;
+    return fail(c, IPC_ENOMEM, "cannot allocate the dot-product scratch for " + std::to_string(n_pad) + " columns");
+  }
+  c->zbuf_cols = n_pad;
+  return IPC_OK;
+}
+
+uint16_t* zslot(ipc_ctx* c, int set, int vec, int party) {
+  return c->zbuf + ((static_cast<size_t>(set) * 2 + vec) * 3 + party) * c->zbuf_cols * c->cfg.db_chunk_rows;
+}
+
+int wait_event(ipc_ctx* c, cudaEvent_t ev, int timeout_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return IPC_OK;
+    if (e != cudaErrorNotReady) return cfail(c, e, "request completion");
+    if (timeout_ms >= 0) {
+      const auto ms =
+          std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (ms >= timeout_ms) return fail(c, IPC_ETIMEOUT, "request not finished within the timeout");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int check_device_status(ipc_ctx* c) {
+  uint32_t* st = status_ptr();
+  if (!st) return IPC_OK;
+  uint32_t v = 0;
+  CTX_TRY(c, cudaMemcpy(&v, st, sizeof v, cudaMemcpyDeviceToHost));
+  if (v) {
+    CTX_TRY(c, cudaMemset(st, 0, sizeof v));
+    return fail(c, IPC_EDEVICE, "a kernel gave up a bounded wait (device status " + std::to_string(v) + ")");
+  }
+  return IPC_OK;
+}
+
+}  // namespace
+
+extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, IPC_EINVAL, "ipc_create: null argument");
+  const ipc_geom& g = cfg->geom;
+  const uint64_t l = static_cast<uint64_t>(g.rows) * g.cols * g.cell;
+  if (l == 0 || l % 128 != 0 || l > 16384 || g.R == 0 || g.R > 31)
+    return fail(nullptr, IPC_EINVAL, "ipc_create: l must be a multiple of 128 up to 16384 and 1 <= R <= 31");
+  if (cfg->path != IPC_PATH_I8MMA && cfg->path != IPC_PATH_I32) return fail(nullptr, IPC_EINVAL, "ipc_create: path");
+  if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
+  ipc_ctx* c = new ipc_ctx();
+  c->cfg = *cfg;
+  if (c->cfg.db_chunk_rows == 0) c->cfg.db_chunk_rows = 65536;
+  if (c->cfg.max_queries == 0) c->cfg.max_queries = 256;
+  c->l = static_cast<uint32_t>(l);
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cfail(nullptr, e, "cudaSetDevice");
+  }
+  for (int i = 0; i < 3; ++i) cudaStreamCreateWithFlags(&c->sp[i], cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&c->sc, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&c->ev_setup, cudaEventDisableTiming);
+  for (int s = 0; s < 2; ++s) {
+    cudaEventCreateWithFlags(&c->ev_cmp[s], cudaEventDisableTiming);
+    for (int i = 0; i < 3; ++i) cudaEventCreateWithFlags(&c->ev_gemm[i][s], cudaEventDisableTiming);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ipc_destroy(c);
+    return cfail(nullptr, e, "stream/event creation");
+  }
+  *out = c;
+  return IPC_OK;
+}
+
+extern "C" void ipc_destroy(ipc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  cudaDeviceSynchronize();
+  for (auto& kv : c->reqs) free_request(c, kv.second);
+  for (auto& ch : c->chunks) cudaFree(ch.planes);
+  cudaFree(c->zbuf);
+  cudaFree(c->stage);
+  for (int i = 0; i < 3; ++i)
+    if (c->sp[i]) cudaStreamDestroy(c->sp[i]);
+  if (c->sc) cudaStreamDestroy(c->sc);
+  if (c->ev_setup) cudaEventDestroy(c->ev_setup);
+  for (int s = 0; s < 2; ++s) {
+    if (c->ev_cmp[s]) cudaEventDestroy(c->ev_cmp[s]);
+    for (int i = 0; i < 3; ++i)
+      if (c->ev_gemm[i][s]) cudaEventDestroy(c->ev_gemm[i][s]);
+  }
+  delete c;
+}
+
+extern "C" const char* ipc_last_error(const ipc_ctx* c) { return c ? c->err.c_str() : ipc::thread_last_error(); }
+
+extern "C" size_t ipc_db_rows(const ipc_ctx* c) { return c ? c->rows : 0; }
+
+extern "C" void* ipc_ctx_stream(const ipc_ctx* c) { return c ? static_cast<void*>(c->sc) : nullptr; }
+
+extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const mask[3],
+                              size_t n_rows, int src_is_device) {
+  if (!c || !code || !mask) return fail(c, IPC_EINVAL, "load_db_shares: null argument");
+  for (int j = 0; j < 3; ++j)
+    if (!code[j] || !mask[j]) return fail(c, IPC_EINVAL, "load_db_shares: null component");
+  if (n_rows == 0) return IPC_OK;
+  CTX_TRY(c, cudaSetDevice(c->cfg.device));
+  const size_t cap = c->cfg.db_chunk_rows, l = c->l;
+  if (!c->stage) {
+    if (cudaMalloc(&c->stage, cap * l * sizeof(uint16_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, IPC_ENOMEM, "load_db_shares: staging buffer");
+    }
+  }
+  // allocate every chunk needed first, so that a failure appends nothing
+  const size_t free_in_last = c->chunks.empty() ? 0 : c->chunks.back().cap - c->chunks.back().rows;
+  std::vector<Chunk> fresh;
+  size_t need = n_rows > free_in_last ? n_rows - free_in_last : 0;
+  uint64_t next_row0 = c->chunks.empty() ? 0 : c->chunks.back().row0 + c->chunks.back().cap;
+  while (need > 0) {
+    Chunk ch;
+    ch.cap = cap;
+    ch.row0 = next_row0;
+    if (cudaMalloc(&ch.planes, 12 * cap * l) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& f : fresh) cudaFree(f.planes);
+      return fail(c, IPC_ENOMEM, "load_db_shares: device memory exhausted");
+    }
+    fresh.push_back(ch);
+    next_row0 += cap;
+    need = need > cap ? need - cap : 0;
+  }
+  for (auto& f : fresh) c->chunks.push_back(f);
+  const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  size_t done = 0;
+  while (done < n_rows) {
+    Chunk* ch = nullptr;
+    for (auto& x : c->chunks)
+      if (x.rows < x.cap) {
+        ch = &x;
+        break;
+      }
+    const size_t take = std::min(n_rows - done, ch->cap - ch->rows);
+    for (int vec = 0; vec < 2; ++vec)
+      for (int j = 0; j < 3; ++j) {
+        const uint16_t* src = (vec == 0 ? code[j] : mask[j]) + done * l;
+        CTX_TRY(c, cudaMemcpyAsync(c->stage, src, take * l * sizeof(uint16_t), kind, c->sc));
+        CTX_RC(c, ipc_split_limbs(c->stage, take * l, plane(c, *ch, j, vec, 0) + ch->rows * l,
+                                  plane(c, *ch, j, vec, 1) + ch->rows * l, c->sc));
+      }
+    ch->rows += take;
+    done += take;
+  }
+  c->rows += n_rows;
+  CTX_TRY(c, cudaStreamSynchronize(c->sc));
+  return IPC_OK;
+}
+
+extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const mask[3],
+                              size_t n_queries, int src_is_device, uint64_t* req_id) {
+  if (!c || !code || !mask || !req_id) return fail(c, IPC_EINVAL, "submit_queries: null argument");
+  if (n_queries == 0 || n_queries > c->cfg.max_queries)
+    return fail(c, IPC_EINVAL, "submit_queries: n_queries must be in 1..max_queries");
+  if (c->rows == 0) return fail(c, IPC_EINVAL, "submit_queries: no database rows loaded");
+  CTX_TRY(c, cudaSetDevice(c->cfg.device));
+  const ipc_geom& g = c->cfg.geom;
+  const uint32_t l = c->l, Q = static_cast<uint32_t>(n_queries), R = g.R, N = Q * R;
+  const uint32_t n_pad = round_up(N, 128);
+  int rc = ensure_zbuf(c, n_pad);
+  if (rc) return rc;
+
+  Request r;
+  r.id = c->next_id;
+  r.Q = Q;
+  r.N = N;
+  r.n_pad = n_pad;
+  const size_t total_blocks = (c->chunks.size() * c->cfg.db_chunk_rows) >> (5 + kLog2BlockWords);
+  r.ld_roots = total_blocks;
+  bool ok = cudaMalloc(&r.bq, 12ull * n_pad * 2 * l) == cudaSuccess &&
+            cudaMalloc(&r.qstage, 2ull * 3 * Q * l * sizeof(uint16_t)) == cudaSuccess &&
+            cudaMalloc(&r.tags, 2ull * N * sizeof(uint32_t)) == cudaSuccess &&
+            cudaMalloc(&r.roots, 3ull * N * r.ld_roots * sizeof(uint32_t)) == cudaSuccess &&
+            cudaMalloc(&r.shares_dev, 3ull * Q) == cudaSuccess &&
+            cudaMallocHost(&r.shares_host, 3ull * Q) == cudaSuccess &&
+            cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && c->cfg.keep_distances) {
+    r.zkeep_rows = round_up(static_cast<uint32_t>(c->chunks.size() * c->cfg.db_chunk_rows), 8);
+    ok = cudaMalloc(&r.zkeep, 2ull * 3 * N * r.zkeep_rows * sizeof(uint16_t)) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    free_request(c, r);
+    return fail(c, IPC_ENOMEM, "submit_queries: not enough device memory for the request");
+  }
+  // column tags: (request id, q << 5 | rho)
+  std::vector<uint32_t> tags(2ull * N);
+  for (uint32_t q = 0; q < Q; ++q)
+    for (uint32_t rho = 0; rho < R; ++rho) {
+      tags[2 * (q * R + rho)] = static_cast<uint32_t>(r.id);
+      tags[2 * (q * R + rho) + 1] = (q << 5) | rho;
+    }
+  const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CTX_TRY(c, cudaMemcpyAsync(r.tags, tags.data(), tags.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
+  for (int vec = 0; vec < 2; ++vec)
+    for (int j = 0; j < 3; ++j)
+      CTX_TRY(c, cudaMemcpyAsync(r.qstage + (static_cast<size_t>(vec) * 3 + j) * Q * l, vec == 0 ? code[j] : mask[j],
+                                 static_cast<size_t>(Q) * l * sizeof(uint16_t), kind, c->sc));
+  CTX_TRY(c, cudaEventRecord(c->ev_setup, c->sc));
+  // the host tags vector dies at return: make the copy complete before that
+  const size_t qplane = static_cast<size_t>(n_pad) * 2 * l;
+  auto bq = [&](int party, int vec, int limb) { return r.bq + ((party * 2 + vec) * 2 + limb) * qplane; };
+  for (int i = 0; i < 3; ++i) {
+    CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
+    for (int vec = 0; vec < 2; ++vec)
+      CTX_RC(c, ipc_prep_query(r.qstage + static_cast<size_t>(vec) * 3 * Q * l, Q, &g, i, bq(i, vec, 0),
+                               bq(i, vec, 1), n_pad, c->sp[i]));
+  }
+  for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
+    const Chunk& ch = c->chunks[ci];
+    if (ch.rows == 0) continue;
+    const int set = static_cast<int>(ci & 1);
+    uint16_t* zc[3];
+    uint16_t* zm[3];
+    size_t ldz;
+    for (int i = 0; i < 3; ++i) {
+      if (c->cfg.keep_distances) {
+        zc[i] = r.zkeep + (static_cast<size_t>(0) * 3 + i) * N * r.zkeep_rows + ch.row0;
+        zm[i] = r.zkeep + (static_cast<size_t>(1) * 3 + i) * N * r.zkeep_rows + ch.row0;
+        ldz = r.zkeep_rows;
+      } else {
+        zc[i] = zslot(c, set, 0, i);
+        zm[i] = zslot(c, set, 1, i);
+        ldz = c->cfg.db_chunk_rows;
+      }
+    }
+    for (int i = 0; i < 3; ++i) {
+      const int prev = (i + 2) % 3;
+      CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
+      for (int vec = 0; vec < 2; ++vec) {
+        const int8_t* xl[2] = {plane(c, ch, i, vec, 0), plane(c, ch, prev, vec, 0)};
+        const int8_t* xh[2] = {plane(c, ch, i, vec, 1), plane(c, ch, prev, vec, 1)};
+        CTX_RC(c, ipc_ring_gemm(c->cfg.path, xl, xh, ch.rows, bq(i, vec, 0), bq(i, vec, 1), N, n_pad, l, r.tags,
+                                c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec),
+                                vec == 0 ? zc[i] : zm[i], ldz, ch.row0, c->sp[i]));
+      }
+      CTX_TRY(c, cudaEventRecord(c->ev_gemm[i][set], c->sp[i]));
+      CTX_TRY(c, cudaStreamWaitEvent(c->sc, c->ev_gemm[i][set], 0));
+    }
+    const uint16_t* zcc[3] = {zc[0], zc[1], zc[2]};
+    const uint16_t* zmc[3] = {zm[0], zm[1], zm[2]};
+    CTX_RC(c, ipc_compare(zcc, zmc, ldz, N, ch.rows, ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a, kLog2BlockWords,
+                          r.roots, r.ld_roots, nullptr, 0, c->sc));
+    CTX_TRY(c, cudaEventRecord(c->ev_cmp[set], c->sc));
+  }
+  const uint32_t n_blocks =
+      static_cast<uint32_t>((c->rows + (32ull << kLog2BlockWords) - 1) >> (5 + kLog2BlockWords));
+  CTX_RC(c, ipc_or_finalize(r.roots, r.ld_roots, n_blocks, kLog2BlockWords, Q, R, r.tags, c->cfg.seeds, r.shares_dev,
+                            c->sc));
+  CTX_TRY(c, cudaMemcpyAsync(r.shares_host, r.shares_dev, 3ull * Q, cudaMemcpyDeviceToHost, c->sc));
+  CTX_TRY(c, cudaEventRecord(r.done, c->sc));
+  CTX_TRY(c, cudaEventSynchronize(c->ev_setup));  // the tag vector above is a host temporary
+  c->reqs[r.id] = r;
+  *req_id = r.id;
+  ++c->next_id;
+  return IPC_OK;
+}
+
+extern "C" int fetch_bit_shares(ipc_ctx* c, uint64_t req_id, uint8_t* shares_out, size_t n_queries, int timeout_ms) {
+  if (!c || !shares_out) return fail(c, IPC_EINVAL, "fetch_bit_shares: null argument");
+  auto it = c->reqs.find(req_id);
+  if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
+  Request& r = it->second;
+  if (n_queries != r.Q) return fail(c, IPC_EINVAL, "n_queries does not match the request");
+  int rc = wait_event(c, r.done, timeout_ms);
+  if (rc) return rc;
+  rc = check_device_status(c);
+  if (rc) return rc;
+  std::memcpy(shares_out, r.shares_host, 3ull * r.Q);
+  return IPC_OK;
+}
+
+extern "C" int fetch_match_bits(ipc_ctx* c, uint64_t req_id, uint8_t* bits_out, size_t n_queries, int timeout_ms) {
+  if (!c || !bits_out) return fail(c, IPC_EINVAL, "fetch_match_bits: null argument");
+  std::vector<uint8_t> sh(3 * n_queries);
+  int rc = fetch_bit_shares(c, req_id, sh.data(), n_queries, timeout_ms);
+  if (rc) return rc;
+  // Open the bit at the output node: XOR of the three boolean components.
+  for (size_t q = 0; q < n_queries; ++q) bits_out[q] = (sh[q] ^ sh[n_queries + q] ^ sh[2 * n_queries + q]) & 1u;
+  return ipc_release(c, req_id);
+}
+
+extern "C" int fetch_distances(ipc_ctx* c, uint64_t req_id, uint32_t q, uint32_t rho, size_t row_begin,
+                               size_t row_end, int16_t* dot, uint16_t* ml) {
+  if (!c || !dot || !ml) return fail(c, IPC_EINVAL, "fetch_distances: null argument");
+  auto it = c->reqs.find(req_id);
+  if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
+  Request& r = it->second;
+  if (!r.zkeep) return fail(c, IPC_ENOSYS, "fetch_distances needs keep_distances");
+  if (q >= r.Q || rho >= c->cfg.geom.R || row_begin > row_end || row_end > c->rows)
+    return fail(c, IPC_EINVAL, "fetch_distances: range");
+  int rc = wait_event(c, r.done, -1);
+  if (rc) return rc;
+  const size_t n = static_cast<size_t>(q) * c->cfg.geom.R + rho, cnt = row_end - row_begin;
+  std::vector<uint16_t> tmp(cnt);
+  std::vector<uint32_t> acc[2] = {std::vector<uint32_t>(cnt, 0), std::vector<uint32_t>(cnt, 0)};
+  for (int vec = 0; vec < 2; ++vec)
+    for (int i = 0; i < 3; ++i) {
+      const uint16_t* src = r.zkeep + ((static_cast<size_t>(vec) * 3 + i) * r.N + n) * r.zkeep_rows + row_begin;
+      CTX_TRY(c, cudaMemcpy(tmp.data(), src, cnt * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+      for (size_t k = 0; k < cnt; ++k) acc[vec][k] += tmp[k];
+    }
+  for (size_t k = 0; k < cnt; ++k) {
+    dot[k] = static_cast<int16_t>(static_cast<uint16_t>(acc[0][k] & 0xFFFFu));
+    ml[k] = static_cast<uint16_t>(acc[1][k] & 0xFFFFu);
+  }
+  return IPC_OK;
+}
+
+extern "C" int ipc_release(ipc_ctx* c, uint64_t req_id) {
+  if (!c) return fail(c, IPC_EINVAL, "ipc_release: null context");
+  auto it = c->reqs.find(req_id);
+  if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
+  cudaEventSynchronize(it->second.done);
+  free_request(c, it->second);
+  c->reqs.erase(it);
+  return IPC_OK;
+}

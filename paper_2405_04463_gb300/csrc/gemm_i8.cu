@@ -1,0 +1,328 @@
+// A3 -- share-domain dot products as an int8-limb ring GEMM on the tensor cores.
+//
+// Each Z_{2^16} operand is stored as balanced signed limbs x = 256*hi + lo, so
+//     x*y = lo*lo' + 256*(lo*hi' + hi*lo') + 2^16*hi*hi'  ==  L + 256*C  (mod 2^16)
+// and only three int8 products are needed (Sec. 6.1: 3 int8 GEMMs for Z_{2^16}; the
+// higher cross term vanishes mod 2^16). |L|, |C| < 2^30 for K <= 2^15, so the int32
+// accumulators never wrap and the result is exact.
+//
+// sm_103a has no tcgen05 integer MMA kind, so the tensor-core path is the warp-level
+// mma.sync.m16n8k32.s32.s8.s8.s32. Operand tiles are moved by TMA (cp.async.bulk.tensor,
+// 128-byte swizzle) into a 3-stage shared-memory ring guarded by mbarriers; one producer
+// warp issues the copies, eight consumer warps read fragments with ldmatrix.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace ipc {
+namespace {
+
+constexpr int BMQ = 128;  // query columns per CTA (mma M)
+constexpr int BND = 128;  // database rows per CTA (mma N)
+constexpr int BK = 128;   // bytes of K per stage and limb plane (= swizzle span)
+constexpr int STAGES = 3;
+constexpr int CONSUMER_WARPS = 8;
+constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
+constexpr int TILE_BYTES = BMQ * BK;  // 16 KiB; BND == BMQ
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 2 * STAGES * 8;
+
+struct Params {
+  uint32_t n_cols;
+  uint32_t x_rows;
+  uint32_t ktiles;       // 2l / BK
+  uint32_t ktiles_half;  // l / BK
+  const uint32_t* col_tags;
+  uint64_t seed_own, seed_prev;
+  uint32_t vec;
+  uint16_t* z;
+  uint64_t ldz;
+  uint64_t row0;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of the given parity; gives up after 2 s of wall time, raising the status word.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > 2000000000ull) {
+      raise_status(status, ST_WAIT_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void ldsm4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_s8(int (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Byte offset of the 16-byte chunk `chunk` of row `row` in a 128-byte-row tile written by TMA
+// with CU_TENSOR_MAP_SWIZZLE_128B (chunk index XOR row mod 8, tile base 1024-byte aligned).
+__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
+  return row * 128u + ((chunk ^ (row & 7u)) << 4);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_i8_kernel(const __grid_constant__ CUtensorMap tq_lo, const __grid_constant__ CUtensorMap tq_hi,
+                   const __grid_constant__ CUtensorMap tx0_lo, const __grid_constant__ CUtensorMap tx0_hi,
+                   const __grid_constant__ CUtensorMap tx1_lo, const __grid_constant__ CUtensorMap tx1_hi,
+                   const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t tiles = smem_addr(smem);
+  const uint32_t bars = tiles + STAGES * STAGE_BYTES;  // full[s] at bars + 8s, empty[s] at bars + 8(STAGES + s)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t q0 = blockIdx.x * BMQ;
+  const uint32_t d0 = blockIdx.y * BND;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(bars + 8 * s, 1);
+      mbar_init(bars + 8 * (STAGES + s), CONSUMER_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == CONSUMER_WARPS) {
+    // ---------------- producer: one lane issues all TMA copies ----------------
+    if (lane == 0) {
+      uint32_t issued = 0;
+      bool failed = false;
+      for (uint32_t kt = 0; kt < p.ktiles; ++kt) {
+        const uint32_t s = kt % STAGES, ph = (kt / STAGES) & 1u;
+        if (!mbar_wait(bars + 8 * (STAGES + s), ph ^ 1u, p.status)) {
+          failed = true;
+          break;
+        }
+        const uint32_t full = bars + 8 * s;
+        const uint32_t base = tiles + s * STAGE_BYTES;
+        mbar_expect_tx(full, STAGE_BYTES);
+        tma_load(base, &tq_lo, static_cast<int32_t>(kt * BK), static_cast<int32_t>(q0), full);
+        tma_load(base + TILE_BYTES, &tq_hi, static_cast<int32_t>(kt * BK), static_cast<int32_t>(q0), full);
+        const bool first = kt < p.ktiles_half;
+        const int32_t kx = static_cast<int32_t>((first ? kt : kt - p.ktiles_half) * BK);
+        tma_load(base + 2 * TILE_BYTES, first ? &tx0_lo : &tx1_lo, kx, static_cast<int32_t>(d0), full);
+        tma_load(base + 3 * TILE_BYTES, first ? &tx0_hi : &tx1_hi, kx, static_cast<int32_t>(d0), full);
+        ++issued;
+      }
+      if (failed) {
+        // Consumers stopped: wait (bounded) for the copies still in flight before leaving.
+        const uint32_t first_pending = issued > STAGES ? issued - STAGES : 0;
+        for (uint32_t kt = first_pending; kt < issued; ++kt)
+          mbar_wait(bars + 8 * (kt % STAGES), (kt / STAGES) & 1u, p.status);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers: 2 (query) x 4 (database) warps, 64 x 32 each ----------------
+  const int wq = warp >> 2, wd = warp & 3;
+  int accL[4][4][4], accC[4][4][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        accL[m][n][e] = 0;
+        accC[m][n][e] = 0;
+      }
+
+  // ldmatrix row/chunk of this lane: A (query) x4 = rows 0-7/8-15 x k-chunks 0/1;
+  // B (database) x4 = (n 0-7, k0), (n 0-7, k1), (n 8-15, k0), (n 8-15, k1).
+  const uint32_t a_row = wq * 64 + (lane & 7) + ((lane >> 3) & 1) * 8;
+  const uint32_t a_chk = lane >> 4;
+  const uint32_t b_row = wd * 32 + (lane & 7) + (lane >> 4) * 8;
+  const uint32_t b_chk = (lane >> 3) & 1;
+
+  bool ok = true;
+  for (uint32_t kt = 0; kt < p.ktiles; ++kt) {
+    const uint32_t s = kt % STAGES, ph = (kt / STAGES) & 1u;
+    if (!mbar_wait(bars + 8 * s, ph, p.status)) {
+      ok = false;
+      break;
+    }
+    const uint32_t base = tiles + s * STAGE_BYTES;
+    const uint32_t qlo = base, qhi = base + TILE_BYTES, xlo = base + 2 * TILE_BYTES, xhi = base + 3 * TILE_BYTES;
+#pragma unroll
+    for (uint32_t ks = 0; ks < BK / 32; ++ks) {
+      uint32_t alo[4][4], ahi[4][4], blo[4][2], bhi[4][2];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const uint32_t off = swz(a_row + 16 * m, 2 * ks + a_chk);
+        ldsm4(qlo + off, alo[m][0], alo[m][1], alo[m][2], alo[m][3]);
+        ldsm4(qhi + off, ahi[m][0], ahi[m][1], ahi[m][2], ahi[m][3]);
+      }
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const uint32_t off = swz(b_row + 16 * np, 2 * ks + b_chk);
+        ldsm4(xlo + off, blo[2 * np][0], blo[2 * np][1], blo[2 * np + 1][0], blo[2 * np + 1][1]);
+        ldsm4(xhi + off, bhi[2 * np][0], bhi[2 * np][1], bhi[2 * np + 1][0], bhi[2 * np + 1][1]);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          mma_s8(accL[m][n], alo[m], blo[n][0], blo[n][1]);
+          mma_s8(accC[m][n], alo[m], bhi[n][0], bhi[n][1]);
+          mma_s8(accC[m][n], ahi[m], blo[n][0], blo[n][1]);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bars + 8 * (STAGES + s));
+  }
+  if (!ok) return;
+
+  // ---------------- epilogue: z = L + 256 C + r_i  (mod 2^16) ----------------
+  const uint32_t g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t col = q0 + wq * 64 + m * 16 + g + 8 * h;
+      if (col >= p.n_cols) continue;
+      const uint32_t req = p.col_tags[2 * col], tag = p.col_tags[2 * col + 1];
+      uint16_t* zc = p.z + static_cast<uint64_t>(col) * p.ldz;
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const uint32_t r = d0 + wd * 32 + n * 8 + 2 * t;  // even; rows r, r+1
+        if (r >= p.x_rows) continue;
+        const uint64_t gr = p.row0 + r;
+        const uint32_t grp = static_cast<uint32_t>(gr >> 3), wi = static_cast<uint32_t>((gr >> 1) & 3u);
+        const uint32_t fo = word_of(philox(grp, tag, req, (IPC_D_ZA << 24) | p.vec, p.seed_own), wi);
+        const uint32_t fp = word_of(philox(grp, tag, req, (IPC_D_ZA << 24) | p.vec, p.seed_prev), wi);
+        const uint32_t z0 = static_cast<uint32_t>(accL[m][n][2 * h]) + (static_cast<uint32_t>(accC[m][n][2 * h]) << 8) +
+                            (fo & 0xFFFFu) - (fp & 0xFFFFu);
+        const uint32_t z1 = static_cast<uint32_t>(accL[m][n][2 * h + 1]) +
+                            (static_cast<uint32_t>(accC[m][n][2 * h + 1]) << 8) + (fo >> 16) - (fp >> 16);
+        if (r + 1 < p.x_rows)
+          *reinterpret_cast<uint32_t*>(zc + r) = (z0 & 0xFFFFu) | (z1 << 16);
+        else
+          zc[r] = static_cast<uint16_t>(z0);
+      }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 2-D int8 tensor [rows][cols] (row stride `cols` bytes), box 128 x 128, 128-byte swizzle,
+// zero fill outside the tensor (ragged row tails).
+int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return IPC_ECUDA;
+  }
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols};
+  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string(static_cast<int>(r)));
+    return IPC_ECUDA;
+  }
+  return IPC_OK;
+}
+
+}  // namespace
+
+int ring_gemm_i8(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
+                 const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+                 uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                 cudaStream_t stream) {
+  CUtensorMap m[6];
+  int rc;
+  if ((rc = make_map(&m[0], b_lo, 2ull * l, n_pad)) || (rc = make_map(&m[1], b_hi, 2ull * l, n_pad)) ||
+      (rc = make_map(&m[2], x_lo[0], l, x_rows)) || (rc = make_map(&m[3], x_hi[0], l, x_rows)) ||
+      (rc = make_map(&m[4], x_lo[1], l, x_rows)) || (rc = make_map(&m[5], x_hi[1], l, x_rows)))
+    return rc;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(gemm_i8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  IPC_CUDA_TRY(attr_err);
+  Params p;
+  p.n_cols = n_cols;
+  p.x_rows = static_cast<uint32_t>(x_rows);
+  p.ktiles = 2 * l / BK;
+  p.ktiles_half = l / BK;
+  p.col_tags = col_tags;
+  p.seed_own = seed_own;
+  p.seed_prev = seed_prev;
+  p.vec = vec;
+  p.z = z;
+  p.ldz = ldz;
+  p.row0 = row0;
+  p.status = status_ptr();
+  dim3 grid((n_cols + BMQ - 1) / BMQ, static_cast<unsigned>((x_rows + BND - 1) / BND));
+  gemm_i8_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+}  // namespace ipc

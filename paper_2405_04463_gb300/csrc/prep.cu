@@ -1,0 +1,161 @@
+// A0 (client encoding and sharing), A1 (limb planes) and A2 (query preparation).
+#include <string>
+
+#include "common.cuh"
+
+namespace ipc {
+namespace {
+
+// Balanced signed limbs: x = 256*hi + lo (mod 2^16), lo, hi in [-128, 127].
+__device__ __forceinline__ void limbs(uint32_t x, int8_t& lo, int8_t& hi) {
+  const int l = static_cast<int8_t>(x & 0xFFu);
+  lo = static_cast<int8_t>(l);
+  hi = static_cast<int8_t>(((x - static_cast<uint32_t>(l)) & 0xFFFFu) >> 8);
+}
+
+// A0: one thread per (row, 4 consecutive elements); one Philox call per vector covers them.
+__global__ void encode_share_kernel(const uint64_t* __restrict__ code_bits, const uint64_t* __restrict__ mask_bits,
+                                    uint32_t n, uint32_t l, uint64_t seed, uint32_t side, uint32_t idx0,
+                                    uint16_t* __restrict__ code_sh, uint16_t* __restrict__ mask_sh) {
+  const uint32_t groups = l >> 2;
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (tid >= static_cast<uint64_t>(n) * groups) return;
+  const uint32_t r = static_cast<uint32_t>(tid / groups), t = static_cast<uint32_t>(tid % groups);
+  const uint32_t nw = (l + 63) >> 6;
+  const uint32_t b0 = t << 2;
+  const uint32_t cw = static_cast<uint32_t>(code_bits[static_cast<uint64_t>(r) * nw + (b0 >> 6)] >> (b0 & 63)) & 0xFu;
+  const uint32_t mw = static_cast<uint32_t>(mask_bits[static_cast<uint64_t>(r) * nw + (b0 >> 6)] >> (b0 & 63)) & 0xFu;
+  const uint64_t plane = static_cast<uint64_t>(n) * l;
+  const uint64_t at = static_cast<uint64_t>(r) * l + b0;
+#pragma unroll
+  for (uint32_t vec = 0; vec < 2; ++vec) {
+    const uint4 w = philox(t, idx0 + r, (side << 8) | vec, IPC_D_SHARE << 24, seed);
+    uint16_t x0[4], x1[4], x2[4];
+#pragma unroll
+    for (uint32_t e = 0; e < 4; ++e) {
+      const uint32_t cb = (cw >> e) & 1u, mb = (mw >> e) & 1u;
+      const uint32_t val = vec == 0 ? (mb - 2u * (cb & mb)) : mb;  // masked bit T=-1, U=0, F=+1 / mask bit
+      const uint32_t word = word_of(w, e);
+      x0[e] = static_cast<uint16_t>(word & 0xFFFFu);
+      x1[e] = static_cast<uint16_t>(word >> 16);
+      x2[e] = static_cast<uint16_t>(val - x0[e] - x1[e]);
+    }
+    uint16_t* dst = vec == 0 ? code_sh : mask_sh;
+    *reinterpret_cast<uint2*>(dst + at) = make_uint2(x0[0] | (uint32_t(x0[1]) << 16), x0[2] | (uint32_t(x0[3]) << 16));
+    *reinterpret_cast<uint2*>(dst + plane + at) =
+        make_uint2(x1[0] | (uint32_t(x1[1]) << 16), x1[2] | (uint32_t(x1[3]) << 16));
+    *reinterpret_cast<uint2*>(dst + 2 * plane + at) =
+        make_uint2(x2[0] | (uint32_t(x2[1]) << 16), x2[2] | (uint32_t(x2[3]) << 16));
+  }
+}
+
+// A1: 8 elements per thread.
+__global__ void split_limbs_kernel(const uint16_t* __restrict__ x, size_t count, int8_t* __restrict__ lo,
+                                   int8_t* __restrict__ hi) {
+  const size_t i8 = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) * 8;
+  if (i8 >= count) return;
+  if (i8 + 8 <= count) {
+    const uint4 v = *reinterpret_cast<const uint4*>(x + i8);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t l2[2] = {0, 0}, h2[2] = {0, 0};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int8_t a, b;
+      limbs((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu, a, b);
+      l2[e >> 2] |= (uint32_t(uint8_t(a)) << (8 * (e & 3)));
+      h2[e >> 2] |= (uint32_t(uint8_t(b)) << (8 * (e & 3)));
+    }
+    *reinterpret_cast<uint2*>(lo + i8) = make_uint2(l2[0], l2[1]);
+    *reinterpret_cast<uint2*>(hi + i8) = make_uint2(h2[0], h2[1]);
+  } else {
+    for (size_t i = i8; i < count; ++i) limbs(x[i], lo[i], hi[i]);
+  }
+}
+
+// A2: one thread per output element of B_i (row n, position k of 2l).
+__global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint32_t Q, ipc_geom g, uint32_t party,
+                                  int8_t* __restrict__ b_lo, int8_t* __restrict__ b_hi, uint32_t n_pad) {
+  const uint32_t l = g.rows * g.cols * g.cell;
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  const uint64_t total = static_cast<uint64_t>(n_pad) * 2 * l;
+  if (tid >= total) return;
+  const uint32_t n = static_cast<uint32_t>(tid / (2 * l));
+  const uint32_t k = static_cast<uint32_t>(tid % (2 * l));
+  uint32_t val = 0;
+  if (n < Q * g.R) {
+    const uint32_t q = n / g.R, rho = n % g.R;
+    const int32_t shift = g.rot_lo + static_cast<int32_t>(rho);
+    const uint32_t kk = k < l ? k : k - l;
+    const uint32_t c = kk % g.cell, j = (kk / g.cell) % g.cols, r = kk / (g.cell * g.cols);
+    int32_t js = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
+    if (js < 0) js += g.cols;
+    const uint32_t src = (r * g.cols + static_cast<uint32_t>(js)) * g.cell + c;
+    const uint64_t plane = static_cast<uint64_t>(Q) * l;
+    const uint32_t prev = (party + 2) % 3;
+    const uint32_t yi = y[party * plane + static_cast<uint64_t>(q) * l + src];
+    if (k < l) {
+      val = yi + y[prev * plane + static_cast<uint64_t>(q) * l + src];  // y_i + y_{i-1}
+    } else {
+      val = yi;  // y_i
+    }
+  }
+  int8_t a, b;
+  limbs(val & 0xFFFFu, a, b);
+  b_lo[tid] = a;
+  b_hi[tid] = b;
+}
+
+bool geom_ok(const ipc_geom* g) {
+  if (!g || g->rows == 0 || g->cols == 0 || g->cell == 0 || g->R == 0 || g->R > 31) return false;
+  const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
+  return l > 0 && l % 128 == 0 && l <= (1u << 14);  // l < 2^14 keeps b*l < 2^32/4 (Lemma 2 with b = 2^16)
+}
+
+}  // namespace
+}  // namespace ipc
+
+using namespace ipc;
+
+extern "C" int ipc_encode_share(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                                uint64_t client_seed, uint32_t side, uint32_t idx0, uint16_t* code_sh,
+                                uint16_t* mask_sh, void* stream) {
+  if (l == 0 || l % 4 != 0 || !code_bits || !mask_bits || !code_sh || !mask_sh) {
+    set_error("ipc_encode_share: l must be a positive multiple of 4 and pointers non-null");
+    return IPC_EINVAL;
+  }
+  if (n == 0) return IPC_OK;
+  const uint64_t threads = static_cast<uint64_t>(n) * (l / 4);
+  const uint32_t bs = 256;
+  encode_share_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+      code_bits, mask_bits, n, l, client_seed, side, idx0, code_sh, mask_sh);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+extern "C" int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8_t* hi, void* stream) {
+  if (count == 0 || !x || !lo || !hi || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(lo) & 7) ||
+      (reinterpret_cast<uintptr_t>(hi) & 7)) {
+    set_error("ipc_split_limbs: count > 0, x 16-byte and lo/hi 8-byte aligned");
+    return IPC_EINVAL;
+  }
+  const size_t threads = (count + 7) / 8;
+  const uint32_t bs = 256;
+  split_limbs_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(x, count, lo, hi);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+extern "C" int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
+                              int8_t* b_hi, uint32_t n_pad, void* stream) {
+  if (!geom_ok(g) || party > 2 || !y || !b_lo || !b_hi || Q == 0 || static_cast<uint64_t>(Q) * g->R > n_pad) {
+    set_error("ipc_prep_query: invalid geometry, party, or n_pad < Q*R");
+    return IPC_EINVAL;
+  }
+  const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
+  const uint64_t total = static_cast<uint64_t>(n_pad) * 2 * l;
+  const uint32_t bs = 256;
+  prep_query_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(y, Q, *g, party, b_lo,
+                                                                                               b_hi, n_pad);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}

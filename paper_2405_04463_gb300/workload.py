@@ -1,0 +1,88 @@
+"""Loading a seeded synthetic workload into the library through its C ABI.
+
+The database bits come from the seeded generator (synth, device half), the client-side
+encoding and sharing (A0) from ipc_encode_share, and the resident planes (A1) from
+load_db_shares. Used by the benchmark, the smoke check and the GPU tests."""
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def lib():
+    from . import binding
+    return binding
+
+
+def dev_u64(a):
+    torch = torch_mod()
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def encode_gpu(code_bits, mask_bits, l, seed, side, idx0=0):
+    """A0 on the device through the C ABI; returns torch int16 [3][n][l] code and mask shares."""
+    torch = torch_mod()
+    ipc = lib()
+    cb = code_bits if hasattr(code_bits, "data_ptr") else dev_u64(code_bits)
+    mb = mask_bits if hasattr(mask_bits, "data_ptr") else dev_u64(mask_bits)
+    n = cb.shape[0]
+    code = torch.empty((3, n, l), dtype=torch.int16, device="cuda")
+    mask = torch.empty((3, n, l), dtype=torch.int16, device="cuda")
+    ipc.ipc_encode_share(cb, mb, n, l, seed, side, idx0, code, mask)
+    return code, mask
+
+
+def u16(t) -> np.ndarray:
+    """torch int16 tensor -> numpy uint16."""
+    return t.cpu().numpy().view(np.uint16)
+
+
+def tags_for(req: int, Q: int, R: int):
+    t = np.zeros((Q * R, 2), np.uint32)
+    for q in range(Q):
+        for rho in range(R):
+            t[q * R + rho] = (req, (q << 5) | rho)
+    return t
+
+
+def db_bits_device(w: synth.Workload, row0: int, n: int):
+    """Database bits of rows row0..row0+n-1 generated on the device (synth device generator)."""
+    torch = torch_mod()
+    code = torch.empty((n, w.nwords), dtype=torch.int64, device="cuda")
+    mask = torch.empty((n, w.nwords), dtype=torch.int64, device="cuda")
+    synth.device_db_bits(w.seed, row0, n, w.l, code.data_ptr(), mask.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    return code, mask
+
+
+def load_workload(ctx, w: synth.Workload, chunk: int = 16384):
+    """Generate the workload's database on the device, share it (A0) and load it (A1)."""
+    torch = torch_mod()
+    ipc = lib()
+    for r0 in range(0, w.s, chunk):
+        n = min(chunk, w.s - r0)
+        cb, mb = db_bits_device(w, r0, n)
+        code, mask = encode_gpu(cb, mb, w.l, w.db_share_seed, 0, idx0=r0)
+        ipc.load_db_shares(ctx, [code[j] for j in range(3)], [mask[j] for j in range(3)], n, 1)
+        del code, mask
+    torch.cuda.synchronize()
+
+
+def query_shares_gpu(w: synth.Workload, qc=None, qm=None):
+    if qc is None:
+        qc, qm = w.query_bits()
+    return encode_gpu(qc, qm, w.l, w.q_share_seed, 1)
+
+
+def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0):
+    ipc = lib()
+    g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
+    cfg = ipc.make_config(g, thr_a=w.thr_a, path=path, db_chunk_rows=chunk_rows, max_queries=max_queries or w.Q,
+                          seeds=w.prf_seeds, keep_distances=keep)
+    return ipc.ipc_create(cfg)

@@ -206,3 +206,32 @@ def workload(name: str) -> Workload:
         return Workload("largest: 600000 x 256 queries x 31 rotations", s=600_000, Q=256, planted=13,
                         flip=(0.05, 0.15), seed=0x1A150005)
     raise KeyError(name)
+
+
+# ----------------------------------------------------------------------------------------
+# Device half (synth_gen.cu -> libsynth.so): the same database-bit generator on the GPU.
+# ----------------------------------------------------------------------------------------
+_synth_lib = None
+
+
+def _device_lib():
+    global _synth_lib
+    if _synth_lib is None:
+        import ctypes
+        import os
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsynth.so")
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run the package build first")
+        L = ctypes.CDLL(path)
+        L.synth_db_bits.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.synth_db_bits.restype = ctypes.c_int
+        _synth_lib = L
+    return _synth_lib
+
+
+def device_db_bits(seed: int, row0: int, n: int, l: int, code_ptr: int, mask_ptr: int, stream: int | None = None):
+    """Write the packed code/mask bits of rows row0..row0+n-1 to device buffers [n][ceil(l/64)] uint64."""
+    rc = _device_lib().synth_db_bits(seed & 0xFFFFFFFFFFFFFFFF, row0, n, l, code_ptr, mask_ptr, stream)
+    if rc != 0:
+        raise RuntimeError("synth_db_bits launch failed")
