@@ -211,6 +211,12 @@ typedef struct {
  * invalid geometry or path, IPC_ECUDA if the device cannot be used. */
 int ipc_create(const ipc_config* cfg, ipc_ctx** out);
 
+/* Device inputs of load_db_shares and submit_queries (src_is_device != 0) are read on the
+ * library's own non-blocking streams, ordered after all work enqueued so far on `stream`
+ * (a cudaStream_t; NULL, the default, means the legacy default stream). Set it to the
+ * stream on which the caller produces those inputs. */
+int ipc_set_input_stream(ipc_ctx* ctx, void* stream);
+
 /* Appends n_rows database rows. code[j], mask[j]: [n_rows][l] uint16, the j-th
  * additive components (A0 output layout per component); host memory if
  * src_is_device == 0, else device memory. The library copies them into its
@@ -218,6 +224,7 @@ int ipc_create(const ipc_config* cfg, ipc_ctx** out);
  * IPC_ENOMEM when the device cannot hold the rows (nothing is appended). */
 int load_db_shares(ipc_ctx* ctx, const uint16_t* const code[3], const uint16_t* const mask[3], size_t n_rows,
                    int src_is_device);
+/* (load_db_shares returns after the rows are copied: the inputs may be freed on return.) */
 
 /* Submits n_queries unrotated queries, code[j]/mask[j]: [n_queries][l] uint16
  * (host if src_is_device == 0, else device). Non-blocking: the inputs may be

@@ -78,6 +78,7 @@ _SIGS = {
     "ipc_destroy": [_vp],
     "ipc_last_error": [_vp],
     "ipc_ctx_stream": [_vp],
+    "ipc_set_input_stream": [_vp, _vp],
     "ipc_measure_peak": [_int, _vp, ctypes.POINTER(ctypes.c_double)],
 }
 for _name, _args in _SIGS.items():
@@ -224,6 +225,10 @@ def ipc_db_rows(ctx) -> int:
 
 def ipc_destroy(ctx):
     lib.ipc_destroy(ctx)
+
+
+def ipc_set_input_stream(ctx, stream=None):
+    _check(lib.ipc_set_input_stream(ctx, _stream(stream)), ctx)
 
 
 def ipc_ctx_stream(ctx) -> int:

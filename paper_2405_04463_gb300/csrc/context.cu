@@ -56,6 +56,8 @@ struct ipc_ctx {
   cudaStream_t sp[3] = {nullptr, nullptr, nullptr};
   cudaStream_t sc = nullptr;
   cudaEvent_t ev_setup = nullptr, ev_gemm[3][2] = {}, ev_cmp[2] = {};
+  cudaEvent_t ev_input = nullptr;        // recorded on input_stream before reading caller device buffers
+  cudaStream_t input_stream = nullptr;   // stream whose earlier work produces device inputs (NULL = legacy)
   std::vector<Chunk> chunks;
   size_t rows = 0;
   uint16_t* zbuf = nullptr;  // [2 sets][vec][party][zbuf_cols][chunk_rows]
@@ -146,6 +148,14 @@ int wait_event(ipc_ctx* c, cudaEvent_t ev, int timeout_ms) {
   }
 }
 
+// Device inputs are produced by the caller's work on c->input_stream; the library's streams
+// are non-blocking, so they must wait for that work explicitly before reading the inputs.
+int order_after_input(ipc_ctx* c) {
+  CTX_TRY(c, cudaEventRecord(c->ev_input, c->input_stream));
+  CTX_TRY(c, cudaStreamWaitEvent(c->sc, c->ev_input, 0));
+  return IPC_OK;
+}
+
 int check_device_status(ipc_ctx* c) {
   uint32_t* st = status_ptr();
   if (!st) return IPC_OK;
@@ -181,6 +191,7 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   for (int i = 0; i < 3; ++i) cudaStreamCreateWithFlags(&c->sp[i], cudaStreamNonBlocking);
   cudaStreamCreateWithFlags(&c->sc, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&c->ev_setup, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_input, cudaEventDisableTiming);
   for (int s = 0; s < 2; ++s) {
     cudaEventCreateWithFlags(&c->ev_cmp[s], cudaEventDisableTiming);
     for (int i = 0; i < 3; ++i) cudaEventCreateWithFlags(&c->ev_gemm[i][s], cudaEventDisableTiming);
@@ -206,6 +217,7 @@ extern "C" void ipc_destroy(ipc_ctx* c) {
     if (c->sp[i]) cudaStreamDestroy(c->sp[i]);
   if (c->sc) cudaStreamDestroy(c->sc);
   if (c->ev_setup) cudaEventDestroy(c->ev_setup);
+  if (c->ev_input) cudaEventDestroy(c->ev_input);
   for (int s = 0; s < 2; ++s) {
     if (c->ev_cmp[s]) cudaEventDestroy(c->ev_cmp[s]);
     for (int i = 0; i < 3; ++i)
@@ -219,6 +231,12 @@ extern "C" const char* ipc_last_error(const ipc_ctx* c) { return c ? c->err.c_st
 extern "C" size_t ipc_db_rows(const ipc_ctx* c) { return c ? c->rows : 0; }
 
 extern "C" void* ipc_ctx_stream(const ipc_ctx* c) { return c ? static_cast<void*>(c->sc) : nullptr; }
+
+extern "C" int ipc_set_input_stream(ipc_ctx* c, void* stream) {
+  if (!c) return fail(c, IPC_EINVAL, "ipc_set_input_stream: null context");
+  c->input_stream = static_cast<cudaStream_t>(stream);
+  return IPC_OK;
+}
 
 extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const mask[3],
                               size_t n_rows, int src_is_device) {
@@ -253,6 +271,10 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
     need = need > cap ? need - cap : 0;
   }
   for (auto& f : fresh) c->chunks.push_back(f);
+  if (src_is_device) {
+    int rc = order_after_input(c);
+    if (rc) return rc;
+  }
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   size_t done = 0;
   while (done < n_rows) {
@@ -321,6 +343,13 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       tags[2 * (q * R + rho)] = static_cast<uint32_t>(r.id);
       tags[2 * (q * R + rho) + 1] = (q << 5) | rho;
     }
+  if (src_is_device) {
+    rc = order_after_input(c);
+    if (rc) {
+      free_request(c, r);
+      return rc;
+    }
+  }
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CTX_TRY(c, cudaMemcpyAsync(r.tags, tags.data(), tags.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
   for (int vec = 0; vec < 2; ++vec)

@@ -85,4 +85,6 @@ def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_quer
     g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
     cfg = ipc.make_config(g, thr_a=w.thr_a, path=path, db_chunk_rows=chunk_rows, max_queries=max_queries or w.Q,
                           seeds=w.prf_seeds, keep_distances=keep)
-    return ipc.ipc_create(cfg)
+    ctx = ipc.ipc_create(cfg)
+    ipc.ipc_set_input_stream(ctx)   # device inputs come from torch's current stream
+    return ctx
