@@ -185,6 +185,25 @@ int ipc_or_finalize(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_
                     uint32_t R, const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares,
                     void* stream);
 
+/*
+ * A4-A8 without any device allocation (no counterpart in the paper: a convenience for
+ * callers that may not allocate). Same result as ipc_compare(..., row0 = 0,
+ * log2_block_words = 5, ...) followed by ipc_or_finalize over n_cols = Q*R columns: the
+ * bit components [3][Q] of each query's OR over all rows and rotations. Meant for callers
+ * that cannot call cudaMalloc once running -- e.g. a host framework that owns the device
+ * memory pool, or a service that reserves all memory at start-up. The block-root scratch
+ * is a fixed 4 MiB array inside the library (held on every GPU that loads it until exit),
+ * so 3 * Q * R * ceil(n_rows / 1024) must not exceed 2^20 words; larger calls fail with
+ * IPC_EINVAL before launching anything. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that may overlap on the GPU (different streams,
+ * or different host threads) race with each other and must be serialised by the caller.
+ * Arguments as in ipc_compare / ipc_or_finalize; bit_shares: [3][Q] uint8 device output.
+ */
+int ipc_compare_or_noalloc(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz, uint32_t Q,
+                           uint32_t R, size_t n_rows, const uint32_t* col_tags, const uint64_t seeds[3],
+                           uint32_t thr_a, uint8_t* bit_shares, void* stream);
+
 /* Reads and clears the device status word of the calling device after
  * synchronising it: IPC_OK, or IPC_EDEVICE if a kernel gave up a bounded wait. */
 int ipc_status(void);

@@ -67,6 +67,7 @@ _SIGS = {
     "ipc_compare": [_VP3, _VP3, _sz, _u32, _sz, _u64, _vp, _U64x3, _u32, _u32, _vp, _sz, _vp, _sz, _vp],
     "ipc_or_finalize": [_vp, _sz, _u32, _u32, _u32, _u32, _vp, _U64x3, _vp, _vp],
     "ipc_status": [],
+    "ipc_compare_or_noalloc": [_VP3, _VP3, _sz, _u32, _u32, _sz, _vp, _U64x3, _u32, _vp, _vp],
     "ipc_create": [ctypes.POINTER(ipc_config), ctypes.POINTER(_vp)],
     "load_db_shares": [_vp, _VP3, _VP3, _sz, _int],
     "submit_queries": [_vp, _VP3, _VP3, _sz, _int, ctypes.POINTER(_u64)],
@@ -159,6 +160,12 @@ def ipc_compare(z_code, z_mask, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_
 def ipc_or_finalize(roots, ld_roots, n_blocks, log2_block_words, Q, R, col_tags, seeds, bit_shares, stream=None):
     _check(lib.ipc_or_finalize(ptr(roots), ld_roots, n_blocks, log2_block_words, Q, R, ptr(col_tags),
                                _U64x3(*[s & (2**64 - 1) for s in seeds]), ptr(bit_shares), _stream(stream)))
+
+
+def ipc_compare_or_noalloc(z_code, z_mask, ldz, Q, R, n_rows, col_tags, seeds, thr_a, bit_shares, stream=None):
+    _check(lib.ipc_compare_or_noalloc(_VP3(*[ptr(a) for a in z_code]), _VP3(*[ptr(a) for a in z_mask]), ldz, Q, R,
+                                      n_rows, ptr(col_tags), _U64x3(*[s & (2**64 - 1) for s in seeds]), thr_a,
+                                      ptr(bit_shares), _stream(stream)))
 
 
 def ipc_status():

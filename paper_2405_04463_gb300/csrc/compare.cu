@@ -431,3 +431,86 @@ int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint
 }
 
 }  // namespace ipc
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free comparison + OR reduction.
+//
+// Some callers may not allocate device memory once they are running: a host framework that
+// owns the whole device memory pool and forbids extensions from calling cudaMalloc, or a
+// service that reserves all of its memory at start-up so that no allocation can fail or
+// synchronise the device mid-flight. For them the block-root scratch that ipc_compare
+// writes and ipc_or_finalize reads lives in a fixed array compiled into this library
+// (g_noalloc_roots, 4 MiB, present on every GPU that loads the library until exit).
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace ipc {
+namespace {
+
+constexpr size_t kNoAllocRootWords = size_t(1) << 20;  // 4 MiB of 32-bit block-root words
+constexpr uint32_t kNoAllocLog2Block = 5;              // 1024-row blocks
+
+__device__ __align__(256) uint32_t g_noalloc_roots[kNoAllocRootWords];
+
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_addr[128] = {};
+
+// Device address of g_noalloc_roots on the current device (looked up once per device; the
+// host-side symbol is only a stand-in for it and must never be handed to a kernel).
+int noalloc_scratch(uint32_t** out) {
+  int dev = 0;
+  IPC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) {
+    set_error("ipc_compare_or_noalloc: device ordinal out of range");
+    return IPC_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    IPC_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_roots));
+    g_noalloc_addr[dev] = static_cast<uint32_t*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return IPC_OK;
+}
+
+}  // namespace
+}  // namespace ipc
+
+extern "C" int ipc_compare_or_noalloc(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
+                                      uint32_t Q, uint32_t R, size_t n_rows, const uint32_t* col_tags,
+                                      const uint64_t seeds[3], uint32_t thr_a, uint8_t* bit_shares, void* stream) {
+  using namespace ipc;
+  if (!z_code || !z_mask || !col_tags || !seeds || !bit_shares) {
+    set_error("ipc_compare_or_noalloc: null pointer");
+    return IPC_EINVAL;
+  }
+  for (int j = 0; j < 3; ++j)
+    if (!z_code[j] || !z_mask[j] || (reinterpret_cast<uintptr_t>(z_code[j]) & 15) ||
+        (reinterpret_cast<uintptr_t>(z_mask[j]) & 15)) {
+      set_error("ipc_compare_or_noalloc: dot planes must be non-null and 16-byte aligned");
+      return IPC_EINVAL;
+    }
+  if (Q == 0 || R == 0 || R > 31 || n_rows == 0 || ldz % 8 != 0 || ldz < n_rows) {
+    set_error("ipc_compare_or_noalloc: need Q >= 1, 1 <= R <= 31, n_rows >= 1, ldz >= n_rows, ldz % 8 == 0");
+    return IPC_EINVAL;
+  }
+  const uint64_t n_cols = static_cast<uint64_t>(Q) * R;
+  const uint64_t n_blocks = (n_rows + (32ull << kNoAllocLog2Block) - 1) >> (5 + kNoAllocLog2Block);
+  if (3 * n_cols * n_blocks > kNoAllocRootWords) {
+    set_error("ipc_compare_or_noalloc: 3 * Q * R * ceil(n_rows / 1024) = " + std::to_string(3 * n_cols * n_blocks) +
+              " block-root words exceed the fixed scratch of " + std::to_string(kNoAllocRootWords) +
+              " words; use ipc_compare + ipc_or_finalize with caller-allocated roots");
+    return IPC_EINVAL;
+  }
+  uint32_t* roots = nullptr;
+  int rc = noalloc_scratch(&roots);
+  if (rc) return rc;
+  // Every root word that ipc_or_finalize reads is written first by this same call, so the
+  // previous call's contents never leak into the result and nothing needs clearing.
+  rc = compare_launch(z_code, z_mask, ldz, static_cast<uint32_t>(n_cols), n_rows, 0, col_tags, seeds, thr_a,
+                      kNoAllocLog2Block, roots, n_blocks, nullptr, 0, as_stream(stream));
+  if (rc) return rc;
+  return or_finalize_launch(roots, n_blocks, static_cast<uint32_t>(n_blocks), kNoAllocLog2Block, Q, R, col_tags,
+                            seeds, bit_shares, as_stream(stream));
+}
