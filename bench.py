@@ -46,7 +46,40 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
+    ap.add_argument("--kernel", default=None, help="time one ring-GEMM path alone (i8mma | i32), for profiling")
+    ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
+    ap.add_argument("--reps", type=int, default=2)
     return ap.parse_args()
+
+
+def run_kernel(args, w):
+    """One ring-GEMM launch shape of the workload (all its query columns x --rows rows), random
+    operands, timed alone with CUDA events; used for ncu captures on a small case."""
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    l, N = w.l, w.Q * w.R
+    n_pad = (N + 127) // 128 * 128
+    rows = args.rows
+    planes = [torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda") for _ in range(4)]
+    blo = torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")
+    bhi = torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")
+    tags = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
+    z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ipc.ipc_ring_gemm(args.kernel, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+    e0.record(st)
+    for _ in range(args.reps):
+        ipc.ipc_ring_gemm(args.kernel, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+    e1.record(st)
+    e1.synchronize()
+    ipc.ipc_status()
+    ms = e0.elapsed_time(e1) / args.reps
+    macs = 3.0 * N * rows * 2 * l if args.kernel != "i32" else 1.0 * N * rows * 2 * l
+    print(json.dumps({"kernel": args.kernel, "rows": rows, "cols": N, "ms_per_launch": ms,
+                      "algorithmic_ops_per_launch": 2 * macs, "achieved_tops": 2 * macs / (ms * 1e-3) / 1e12,
+                      "operand_bytes_per_launch": 4 * rows * l + 2 * n_pad * 2 * l, "z_bytes": 2 * N * rows}))
 
 
 def dist_env():
@@ -180,7 +213,7 @@ def run_ours(args, w):
     dev = torch.cuda.current_device()
 
     # ---- setup (untimed): resident database, query shares, contexts ----
-    ctxs = {"i8mma": make_ctx(w, path="i8mma", max_queries=w.Q)}
+    ctxs = {"i8mix": make_ctx(w, path="i8mix", max_queries=w.Q), "i8mma": make_ctx(w, path="i8mma", max_queries=w.Q)}
     if not args.no_i32:
         ctxs["i32"] = make_ctx(w, path="i32", max_queries=w.Q)
     for c in ctxs.values():
@@ -217,7 +250,7 @@ def run_ours(args, w):
             ms = float(t.item())
         return ms / k, wall / k, bits.copy()
 
-    main = ctxs["i8mma"]
+    main = ctxs["i8mix"]
     run_steps(main, args.warmup, False)
     clocks = Clocks(dev)
     clocks.start()
@@ -225,12 +258,15 @@ def run_ours(args, w):
     clk = clocks.stop()
     run_steps(main, 1, True)
     ms_e2e, wall_e2e, bits_e2e = run_steps(main, args.steps, True)
-    out_i32 = None
-    if "i32" in ctxs:
-        run_steps(ctxs["i32"], 1, False)
-        ms_i32, _, bits_i32 = run_steps(ctxs["i32"], args.steps, False)
-        out_i32 = {"value": w.comparisons * world / (ms_i32 * 1e-3), "ms_per_step": ms_i32,
-                   "bits_equal_to_int8_path": bool((bits_i32 == bits).all())}
+
+    def other(path):
+        run_steps(ctxs[path], 1, False)
+        ms, _, b = run_steps(ctxs[path], args.steps, False)
+        return {"value": w.comparisons * world / (ms * 1e-3), "ms_per_step": ms,
+                "bits_equal_to_headline_path": bool((b == bits).all())}
+
+    out_tc = other("i8mma")
+    out_i32 = other("i32") if "i32" in ctxs else None
 
     # ---- dominant kernel alone: one i8 GEMM launch over a 65536-row chunk ----
     l, N = w.l, w.Q * w.R
@@ -255,18 +291,24 @@ def run_ours(args, w):
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    t_mix = gemm_time("i8mix", 5)
     t_i8 = gemm_time("i8mma", 5)
     t_i32 = gemm_time("i32", 3) if not args.no_i32 else None
     ops = 2.0 * 3 * N * rows * 2 * l          # 3 int8 products per ring multiply-add, 2 ops each
     peak_mma = ipc.ipc_measure_peak(0)
     peak_imad = ipc.ipc_measure_peak(1)
-    achieved = ops / (t_i8 * 1e-3) / 1e12
+    peak_dp4a = ipc.ipc_measure_peak(2)
+    peak_int8 = peak_mma + peak_dp4a
+    achieved = ops / (t_mix * 1e-3) / 1e12
     traffic = ncu_traffic("gemm_i8_kernel", os.path.join(ROOT, "paper_2405_04463_gb300", "csrc", "gemm_i8.cu"))
-    roofline = {"bound": "tensor", "kernel": "gemm_i8_kernel", "achieved": achieved, "peak": peak_mma,
-                "unit": "TOP/s", "frac": achieved / peak_mma, "traffic": traffic,
-                "peak_source": "measured live: register-only mma.sync.m16n8k32 s8 loop (ipc_measure_peak); "
-                               "MEASURED_PEAKS.json has no int8 figure",
-                "launch_ms": t_i8, "ops_per_launch": ops}
+    roofline = {"bound": "tensor", "kernel": "gemm_i8_kernel<1> (mma.sync s8 + dp4a)", "achieved": achieved,
+                "peak": peak_int8, "unit": "TOP/s", "frac": achieved / peak_int8, "traffic": traffic,
+                "peak_source": "measured live: register-only mma.sync.m16n8k32 s8 loop + dp4a loop "
+                               "(ipc_measure_peak); MEASURED_PEAKS.json has no int8 figure",
+                "peak_mma_s8": peak_mma, "peak_dp4a": peak_dp4a, "launch_ms": t_mix, "ops_per_launch": ops,
+                "tensor_only_kernel": {"kernel": "gemm_i8_kernel<0>", "launch_ms": t_i8,
+                                       "achieved": ops / (t_i8 * 1e-3) / 1e12,
+                                       "frac_of_mma_peak": ops / (t_i8 * 1e-3) / 1e12 / peak_mma}}
     i32_kernel = None
     if t_i32:
         imads = 1.0 * N * rows * 2 * l
@@ -293,10 +335,12 @@ def run_ours(args, w):
         "warmup": args.warmup, "ms_per_step": ms_i8, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
         "config": {"workload": w.name, "db_rows": w.s, "queries": w.Q, "rotations": w.R, "code_bits": w.l,
-                   "planted": w.planted, "path": "i8mma (mma.sync s8, TMA)", "parallelism": f"replicas x{world}",
+                   "planted": w.planted, "path": "i8mix (TMA-fed tiles split between mma.sync s8 and dp4a)",
+                   "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: resident shares 12 B x rows x 12800 = "
                          f"{12 * w.s * w.l / 1e9:.1f} GB"},
-        "int8_peak_frac_step": value * 921600 / (peak_mma * 1e12),
+        "int8_peak_frac_step": value * 921600 / (peak_int8 * 1e12),
+        "int8_tensor_only_path": out_tc,
         "int32_path": out_i32,
         "ratio_int8_vs_int32": (value / out_i32["value"]) if out_i32 else None,
         "roofline": roofline,
@@ -316,7 +360,9 @@ def run_ours(args, w):
 def main():
     args = parse()
     w = synth.workload(args.workload)
-    if args.impl == "reference":
+    if args.kernel:
+        run_kernel(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)

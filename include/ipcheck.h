@@ -56,6 +56,7 @@ extern "C" {
 
 #define IPC_PATH_I8MMA 0  /* int8 limb GEMM on the tensor cores (mma.sync s8, TMA-fed) */
 #define IPC_PATH_I32 1    /* plain int32 CUDA-core ring GEMM (IMAD) */
+#define IPC_PATH_I8MIX 2  /* int8 limb GEMM split between mma.sync s8 and dp4a in every tile */
 
 /* PRF domains: high byte of Philox counter word 3. */
 #define IPC_D_SHARE 1u
@@ -126,7 +127,8 @@ int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t pa
  * IPC_D_ZA<<24 | vec)). z: [n_cols][ldz] uint16, column-major in the sense
  * that the rows of one query column are contiguous; z_i is the message party
  * i sends to party i+1 (resharing). path selects the int8 tensor-core GEMM
- * (exact: |int32 partial sums| < 2^30) or the int32 CUDA-core GEMM; both give
+ * (exact: |int32 partial sums| < 2^30), the int8 GEMM split between the tensor
+ * cores and the integer pipe's dp4a, or the int32 CUDA-core GEMM; all give
  * identical results. Errors: IPC_EINVAL for l not a multiple of 128, odd
  * ldz, ldz < x_rows, or unaligned pointers (16 B); IPC_ECUDA if the tensor
  * map cannot be encoded.
@@ -217,7 +219,7 @@ typedef struct ipc_ctx ipc_ctx;
 typedef struct {
   ipc_geom geom;            /* {16, 200, 4, -15, 31} for the deployed system */
   uint32_t thr_a;           /* a of the threshold a/b with b = 2^16; 16384 for MATCH_RATIO 0.375 */
-  int32_t path;             /* IPC_PATH_I8MMA or IPC_PATH_I32 */
+  int32_t path;             /* IPC_PATH_I8MMA, IPC_PATH_I8MIX or IPC_PATH_I32 */
   uint32_t db_chunk_rows;   /* rows per resident chunk and pipeline step; multiple of 1024; 0 = 65536 */
   uint32_t max_queries;     /* largest request accepted by submit_queries; 0 = 256 */
   uint64_t seeds[3];        /* pairwise PRF seeds; seeds[j] shared by parties j and j+1 */
@@ -295,7 +297,8 @@ const char* ipc_last_error(const ipc_ctx* ctx);
 
 /* Measures a roofline denominator on the current device with a register-only loop:
  * what = 0 -> mma.sync.m16n8k32 s8 rate in TOP/s (2 ops per multiply-add);
- * what = 1 -> 32-bit IMAD rate in T IMAD/s. Synchronous; allocates a small buffer. */
+ * what = 1 -> 32-bit IMAD rate in T IMAD/s; what = 2 -> dp4a rate in TOP/s (8 ops per
+ * instruction). Synchronous; allocates a small buffer. */
 int ipc_measure_peak(int what, void* stream, double* out);
 
 #ifdef __cplusplus

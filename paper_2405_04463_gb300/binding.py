@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libipcheck.so")
 
 IPC_OK, IPC_EINVAL, IPC_ENOMEM, IPC_ECUDA, IPC_ETIMEOUT = 0, -1, -2, -3, -4
 IPC_EAGAIN, IPC_ENOTFOUND, IPC_EDEVICE, IPC_ENOSYS = -5, -6, -7, -8
-IPC_PATH_I8MMA, IPC_PATH_I32 = 0, 1
-PATHS = {"i8mma": IPC_PATH_I8MMA, "i32": IPC_PATH_I32}
+IPC_PATH_I8MMA, IPC_PATH_I32, IPC_PATH_I8MIX = 0, 1, 2
+PATHS = {"i8mma": IPC_PATH_I8MMA, "i32": IPC_PATH_I32, "i8mix": IPC_PATH_I8MIX}
 
 
 class IpcError(RuntimeError):

@@ -5,7 +5,7 @@
 #include "common.cuh"
 
 namespace ipc {
-int ring_gemm_i8(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
+int ring_gemm_i8(int mode, const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
                  const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream);
@@ -46,8 +46,8 @@ extern "C" int ipc_ring_gemm(int path, const int8_t* const x_lo[2], const int8_t
   if (vec > 1) return bad("ipc_ring_gemm: vec is 0 (code) or 1 (mask)");
   if (x_rows > (1u << 30)) return bad("ipc_ring_gemm: too many rows in one call");
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
-  if (path == IPC_PATH_I8MMA)
-    return ring_gemm_i8(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
+  if (path == IPC_PATH_I8MMA || path == IPC_PATH_I8MIX)
+    return ring_gemm_i8(path == IPC_PATH_I8MMA ? 0 : 1, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
                         row0, as_stream(stream));
   if (path == IPC_PATH_I32)
     return ring_gemm_i32(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, l, col_tags, seed_own, seed_prev, vec, z, ldz, row0,

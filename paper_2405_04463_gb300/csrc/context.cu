@@ -176,7 +176,8 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   const uint64_t l = static_cast<uint64_t>(g.rows) * g.cols * g.cell;
   if (l == 0 || l % 128 != 0 || l > 16384 || g.R == 0 || g.R > 31)
     return fail(nullptr, IPC_EINVAL, "ipc_create: l must be a multiple of 128 up to 16384 and 1 <= R <= 31");
-  if (cfg->path != IPC_PATH_I8MMA && cfg->path != IPC_PATH_I32) return fail(nullptr, IPC_EINVAL, "ipc_create: path");
+  if (cfg->path != IPC_PATH_I8MMA && cfg->path != IPC_PATH_I32 && cfg->path != IPC_PATH_I8MIX)
+    return fail(nullptr, IPC_EINVAL, "ipc_create: path");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
   ipc_ctx* c = new ipc_ctx();
   c->cfg = *cfg;

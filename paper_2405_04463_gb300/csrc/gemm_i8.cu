@@ -9,7 +9,14 @@
 // sm_103a has no tcgen05 integer MMA kind, so the tensor-core path is the warp-level
 // mma.sync.m16n8k32.s32.s8.s8.s32. Operand tiles are moved by TMA (cp.async.bulk.tensor,
 // 128-byte swizzle) into a 3-stage shared-memory ring guarded by mbarriers; one producer
-// warp issues the copies, eight consumer warps read fragments with ldmatrix.
+// warp issues the copies, eight consumer warps read them.
+//
+// Two consumer layouts (template MODE):
+//   MODE 0 (IPC_PATH_I8MMA): eight mma.sync warps, 2 (query) x 4 (database) of 64 x 32.
+//   MODE 1 (IPC_PATH_I8MIX): eight mma.sync warps (32 x 32) cover database rows 0..63 of the
+//     tile and eight dp4a warps cover rows 64..127. On sm_103 the int8 mma.sync rate (256 MAC/clk/SM)
+//     equals the dp4a rate of the integer pipe, and the two do not share an issue pipe, so
+//     splitting each tile between them runs both units at once on the same staged operands.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -25,8 +32,15 @@ constexpr int BMQ = 128;  // query columns per CTA (mma M)
 constexpr int BND = 128;  // database rows per CTA (mma N)
 constexpr int BK = 128;   // bytes of K per stage and limb plane (= swizzle span)
 constexpr int STAGES = 3;
-constexpr int CONSUMER_WARPS = 8;
-constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
+// MODE 0: 8 mma consumer warps + 1 producer warp.
+// MODE 1: 8 mma warps (32 x 32 each) + 8 dp4a warps (8 x 4 per thread): two of each per SM
+// sub-partition, every consumer thread with 64 accumulators, which keeps both the tensor pipe and
+// the integer pipe near their full rates when they run together; the first dp4a warp's lane 0
+// also issues the copies.
+template <int MODE>
+constexpr int kConsumerWarps = MODE == 0 ? 8 : 16;
+template <int MODE>
+constexpr int kThreads = MODE == 0 ? (8 + 1) * 32 : 16 * 32;
 constexpr int TILE_BYTES = BMQ * BK;  // 16 KiB; BND == BMQ
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 2 * STAGES * 8;
@@ -105,13 +119,128 @@ __device__ __forceinline__ void mma_s8(int (&d)[4], const uint32_t (&a)[4], uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// 32-bit shared-memory load (volatile: it must stay after the stage's barrier wait).
+__device__ __forceinline__ int lds32(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
 // Byte offset of the 16-byte chunk `chunk` of row `row` in a 128-byte-row tile written by TMA
 // with CU_TENSOR_MAP_SWIZZLE_128B (chunk index XOR row mod 8, tile base 1024-byte aligned).
 __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
   return row * 128u + ((chunk ^ (row & 7u)) << 4);
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+// Party i's zero share for query column `col` and global row gr: F(seed_own) - F(seed_prev)
+// with F = half (gr & 1) of word ((gr >> 1) & 3) of Philox(seed, (gr >> 3, tag, req, D_ZA | vec)).
+__device__ __forceinline__ uint32_t zero_share_word(const Params& p, uint32_t col, uint64_t gr) {
+  const uint32_t req = p.col_tags[2 * col], tag = p.col_tags[2 * col + 1];
+  const uint32_t grp = static_cast<uint32_t>(gr >> 3), wi = static_cast<uint32_t>((gr >> 1) & 3u);
+  const uint32_t fo = word_of(philox(grp, tag, req, (IPC_D_ZA << 24) | p.vec, p.seed_own), wi);
+  const uint32_t fp = word_of(philox(grp, tag, req, (IPC_D_ZA << 24) | p.vec, p.seed_prev), wi);
+  // both halves at once: low half for the even row, high half for the odd row
+  return (((fo & 0xFFFFu) - (fp & 0xFFFFu)) & 0xFFFFu) | (((fo >> 16) - (fp >> 16)) << 16);
+}
+
+// z = L + 256 C + r (mod 2^16) for rows r (even) and r+1 of query column col.
+__device__ __forceinline__ void store_pair(const Params& p, uint32_t col, uint32_t r, uint32_t L0, uint32_t C0,
+                                           uint32_t L1, uint32_t C1) {
+  if (r >= p.x_rows) return;
+  const uint32_t zs = zero_share_word(p, col, p.row0 + r);
+  const uint32_t z0 = L0 + (C0 << 8) + (zs & 0xFFFFu);
+  const uint32_t z1 = L1 + (C1 << 8) + (zs >> 16);
+  uint16_t* zc = p.z + static_cast<uint64_t>(col) * p.ldz;
+  if (r + 1 < p.x_rows)
+    *reinterpret_cast<uint32_t*>(zc + r) = (z0 & 0xFFFFu) | (z1 << 16);
+  else
+    zc[r] = static_cast<uint16_t>(z0);
+}
+
+// dp4a consumer warps of MODE 1: 256 threads cover query rows 0..127 x database rows 64..127
+// of the tile, 8 x 4 per thread: thread (tq, td), tq < 16, td < 16, owns query rows tq + 16 i and
+// database rows 64 + td + 16 j. All rows of a thread share one swizzle phase (row & 7), so one XOR
+// offset serves all its loads of a k-quad. A warp holds 8 tq (lane & 7) x 4 td (lane >> 3): each
+// of its loads touches 8 (A) or 4 (B) rows of distinct phases, i.e. distinct banks, so every
+// shared load is a single wavefront. Per k-quad and thread: 24 loads, 96 dp4a.
+template <typename Refill, typename Drain>
+__device__ __forceinline__ void dp4a_consumer(const Params& p, const uint8_t* smem, uint32_t bars, int dw, int lane,
+                                              uint32_t q0, uint32_t d0, Refill refill, Drain drain) {
+  const uint32_t tq = (lane & 7u) + 8u * (dw & 1), td = (lane >> 3) + 4u * (dw >> 1);
+  int accL[8][4], accC[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      accL[i][j] = 0;
+      accC[i][j] = 0;
+    }
+  const uint32_t ra7 = tq & 7u, rb7 = td & 7u;  // swizzle phase of this thread's rows
+  bool ok = true;
+  for (uint32_t kt = 0; kt < p.ktiles; ++kt) {
+    const uint32_t s = kt % STAGES, ph = (kt / STAGES) & 1u;
+    if (!mbar_wait(bars + 8 * s, ph, p.status)) {
+      ok = false;
+      drain(kt);
+      break;
+    }
+    const uint32_t base = smem_addr(smem) + s * STAGE_BYTES;
+    const uint32_t qlo = base + tq * 128u, qhi = qlo + TILE_BYTES;
+    const uint32_t xlo = base + 2 * TILE_BYTES + (64u + td) * 128u, xhi = xlo + TILE_BYTES;
+#pragma unroll 1
+    for (uint32_t c = 0; c < BK / 16; ++c) {
+      const uint32_t oa = (c ^ ra7) << 4, ob = (c ^ rb7) << 4;
+#pragma unroll 1  // the sibling dp4a warp hides this warp's load latency; unrolling would spill
+      for (uint32_t wv = 0; wv < 4; ++wv) {
+        int alo[8], ahi[8], blo[4], bhi[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          alo[i] = lds32(qlo + 2048u * i + oa + 4u * wv);
+          ahi[i] = lds32(qhi + 2048u * i + oa + 4u * wv);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          blo[j] = lds32(xlo + 2048u * j + ob + 4u * wv);
+          bhi[j] = lds32(xhi + 2048u * j + ob + 4u * wv);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            accL[i][j] = __dp4a(alo[i], blo[j], accL[i][j]);
+            accC[i][j] = __dp4a(alo[i], bhi[j], accC[i][j]);
+            accC[i][j] = __dp4a(ahi[i], blo[j], accC[i][j]);
+          }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bars + 8 * (STAGES + s));
+    if (!refill(kt)) {
+      ok = false;
+      drain(kt);
+      break;
+    }
+  }
+  if (!ok) return;
+  // epilogue: lanes l and l + 8 (l & 8 == 0) hold database rows td and td + 1; the lower lane
+  // takes its partner's pair through a shuffle and stores both rows
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t col = q0 + tq + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t L_nb = __shfl_down_sync(0xFFFFFFFFu, static_cast<uint32_t>(accL[i][j]), 8);
+      const uint32_t C_nb = __shfl_down_sync(0xFFFFFFFFu, static_cast<uint32_t>(accC[i][j]), 8);
+      if ((td & 1u) == 0 && col < p.n_cols) {
+        const uint32_t r = d0 + 64 + td + 16 * j;
+        store_pair(p, col, r, static_cast<uint32_t>(accL[i][j]), static_cast<uint32_t>(accC[i][j]), L_nb, C_nb);
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads<MODE>, 1)
     gemm_i8_kernel(const __grid_constant__ CUtensorMap tq_lo, const __grid_constant__ CUtensorMap tq_hi,
                    const __grid_constant__ CUtensorMap tx0_lo, const __grid_constant__ CUtensorMap tx0_hi,
                    const __grid_constant__ CUtensorMap tx1_lo, const __grid_constant__ CUtensorMap tx1_hi,
@@ -127,14 +256,28 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(bars + 8 * s, 1);
-      mbar_init(bars + 8 * (STAGES + s), CONSUMER_WARPS);
+      mbar_init(bars + 8 * (STAGES + s), kConsumerWarps<MODE>);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == CONSUMER_WARPS) {
-    // ---------------- producer: one lane issues all TMA copies ----------------
+  // Issues the four TMA copies of k-tile kt into stage kt % STAGES.
+  auto issue = [&](uint32_t kt) {
+    const uint32_t s = kt % STAGES;
+    const uint32_t full = bars + 8 * s;
+    const uint32_t base = tiles + s * STAGE_BYTES;
+    mbar_expect_tx(full, STAGE_BYTES);
+    tma_load(base, &tq_lo, static_cast<int32_t>(kt * BK), static_cast<int32_t>(q0), full);
+    tma_load(base + TILE_BYTES, &tq_hi, static_cast<int32_t>(kt * BK), static_cast<int32_t>(q0), full);
+    const bool first = kt < p.ktiles_half;
+    const int32_t kx = static_cast<int32_t>((first ? kt : kt - p.ktiles_half) * BK);
+    tma_load(base + 2 * TILE_BYTES, first ? &tx0_lo : &tx1_lo, kx, static_cast<int32_t>(d0), full);
+    tma_load(base + 3 * TILE_BYTES, first ? &tx0_hi : &tx1_hi, kx, static_cast<int32_t>(d0), full);
+  };
+
+  if (MODE == 0 && warp == 8) {
+    // ---------------- producer warp: one lane issues all TMA copies ----------------
     if (lane == 0) {
       uint32_t issued = 0;
       bool failed = false;
@@ -144,15 +287,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           failed = true;
           break;
         }
-        const uint32_t full = bars + 8 * s;
-        const uint32_t base = tiles + s * STAGE_BYTES;
-        mbar_expect_tx(full, STAGE_BYTES);
-        tma_load(base, &tq_lo, static_cast<int32_t>(kt * BK), static_cast<int32_t>(q0), full);
-        tma_load(base + TILE_BYTES, &tq_hi, static_cast<int32_t>(kt * BK), static_cast<int32_t>(q0), full);
-        const bool first = kt < p.ktiles_half;
-        const int32_t kx = static_cast<int32_t>((first ? kt : kt - p.ktiles_half) * BK);
-        tma_load(base + 2 * TILE_BYTES, first ? &tx0_lo : &tx1_lo, kx, static_cast<int32_t>(d0), full);
-        tma_load(base + 3 * TILE_BYTES, first ? &tx0_hi : &tx1_hi, kx, static_cast<int32_t>(d0), full);
+        issue(kt);
         ++issued;
       }
       if (failed) {
@@ -164,12 +299,43 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     return;
   }
+  // MODE 1: the first dp4a warp's lane 0 issues the copies. After finishing k-tile kt it refills
+  // the stage of k-tile kt-1 (all consumers are done with it by then in the common case) with
+  // k-tile kt-1+STAGES; its sibling dp4a warp keeps the integer pipe busy while it waits.
+  constexpr uint32_t kIssuer = 8 * 32;
+  if (MODE == 1 && threadIdx.x == kIssuer) {
+    const uint32_t pro = p.ktiles < STAGES ? p.ktiles : STAGES;
+    for (uint32_t kt = 0; kt < pro; ++kt) issue(kt);
+  }
+  auto refill = [&](uint32_t kt) -> bool {
+    if (MODE != 1 || threadIdx.x != kIssuer || kt == 0) return true;
+    const uint32_t kr = kt - 1 + STAGES;
+    if (kr >= p.ktiles) return true;
+    const uint32_t sp = (kt - 1) % STAGES, php = ((kt - 1) / STAGES) & 1u;
+    if (!mbar_wait(bars + 8 * (STAGES + sp), php, p.status)) return false;
+    issue(kr);
+    return true;
+  };
+  // Before leaving early, the issuing thread waits (bounded) for its copies still in flight.
+  auto drain = [&](uint32_t kt_failed) {
+    if (MODE != 1 || threadIdx.x != kIssuer) return;
+    // copies issued so far: k-tiles below kt_failed + STAGES - 1 (refills run one tile behind)
+    const uint32_t issued = (kt_failed + STAGES - 1 < p.ktiles) ? kt_failed + STAGES - 1 : p.ktiles;
+    for (uint32_t kt = kt_failed; kt < issued; ++kt)
+      mbar_wait(bars + 8 * (kt % STAGES), (kt / STAGES) & 1u, p.status);
+  };
 
-  // ---------------- consumers: 2 (query) x 4 (database) warps, 64 x 32 each ----------------
-  const int wq = warp >> 2, wd = warp & 3;
-  int accL[4][4][4], accC[4][4][4];
+  if (MODE == 1 && warp >= 8) {
+    dp4a_consumer(p, smem, bars, warp - 8, lane, q0, d0, refill, drain);
+    return;
+  }
+  // ---------------- mma.sync consumers: 2 (query) x WD (database) warps, 64 x 32 each ----------------
+  constexpr int WD = MODE == 0 ? 4 : 2;   // warps along the database rows
+  constexpr int MF = MODE == 0 ? 4 : 2;   // 16-row query fragments per warp
+  const int wq = warp / WD, wd = warp % WD;
+  int accL[MF][4][4], accC[MF][4][4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < MF; ++m)
 #pragma unroll
     for (int n = 0; n < 4; ++n)
 #pragma unroll
@@ -180,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   // ldmatrix row/chunk of this lane: A (query) x4 = rows 0-7/8-15 x k-chunks 0/1;
   // B (database) x4 = (n 0-7, k0), (n 0-7, k1), (n 8-15, k0), (n 8-15, k1).
-  const uint32_t a_row = wq * 64 + (lane & 7) + ((lane >> 3) & 1) * 8;
+  const uint32_t a_row = wq * (16 * MF) + (lane & 7) + ((lane >> 3) & 1) * 8;
   const uint32_t a_chk = lane >> 4;
   const uint32_t b_row = wd * 32 + (lane & 7) + (lane >> 4) * 8;
   const uint32_t b_chk = (lane >> 3) & 1;
@@ -196,9 +362,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t qlo = base, qhi = base + TILE_BYTES, xlo = base + 2 * TILE_BYTES, xhi = base + 3 * TILE_BYTES;
 #pragma unroll
     for (uint32_t ks = 0; ks < BK / 32; ++ks) {
-      uint32_t alo[4][4], ahi[4][4], blo[4][2], bhi[4][2];
+      uint32_t alo[MF][4], ahi[MF][4], blo[4][2], bhi[4][2];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
+      for (int m = 0; m < MF; ++m) {
         const uint32_t off = swz(a_row + 16 * m, 2 * ks + a_chk);
         ldsm4(qlo + off, alo[m][0], alo[m][1], alo[m][2], alo[m][3]);
         ldsm4(qhi + off, ahi[m][0], ahi[m][1], ahi[m][2], ahi[m][3]);
@@ -210,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         ldsm4(xhi + off, bhi[2 * np][0], bhi[2 * np][1], bhi[2 * np + 1][0], bhi[2 * np + 1][1]);
       }
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
+      for (int m = 0; m < MF; ++m)
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
           mma_s8(accL[m][n], alo[m], blo[n][0], blo[n][1]);
@@ -226,29 +392,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   // ---------------- epilogue: z = L + 256 C + r_i  (mod 2^16) ----------------
   const uint32_t g = lane >> 2, t = lane & 3;
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < MF; ++m)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const uint32_t col = q0 + wq * 64 + m * 16 + g + 8 * h;
+      const uint32_t col = q0 + wq * (16 * MF) + m * 16 + g + 8 * h;
       if (col >= p.n_cols) continue;
-      const uint32_t req = p.col_tags[2 * col], tag = p.col_tags[2 * col + 1];
-      uint16_t* zc = p.z + static_cast<uint64_t>(col) * p.ldz;
 #pragma unroll
       for (int n = 0; n < 4; ++n) {
         const uint32_t r = d0 + wd * 32 + n * 8 + 2 * t;  // even; rows r, r+1
-        if (r >= p.x_rows) continue;
-        const uint64_t gr = p.row0 + r;
-        const uint32_t grp = static_cast<uint32_t>(gr >> 3), wi = static_cast<uint32_t>((gr >> 1) & 3u);
-        const uint32_t fo = word_of(philox(grp, tag, req, (IPC_D_ZA << 24) | p.vec, p.seed_own), wi);
-        const uint32_t fp = word_of(philox(grp, tag, req, (IPC_D_ZA << 24) | p.vec, p.seed_prev), wi);
-        const uint32_t z0 = static_cast<uint32_t>(accL[m][n][2 * h]) + (static_cast<uint32_t>(accC[m][n][2 * h]) << 8) +
-                            (fo & 0xFFFFu) - (fp & 0xFFFFu);
-        const uint32_t z1 = static_cast<uint32_t>(accL[m][n][2 * h + 1]) +
-                            (static_cast<uint32_t>(accC[m][n][2 * h + 1]) << 8) + (fo >> 16) - (fp >> 16);
-        if (r + 1 < p.x_rows)
-          *reinterpret_cast<uint32_t*>(zc + r) = (z0 & 0xFFFFu) | (z1 << 16);
-        else
-          zc[r] = static_cast<uint16_t>(z0);
+        store_pair(p, col, r, static_cast<uint32_t>(accL[m][n][2 * h]), static_cast<uint32_t>(accC[m][n][2 * h]),
+                   static_cast<uint32_t>(accL[m][n][2 * h + 1]), static_cast<uint32_t>(accC[m][n][2 * h + 1]));
       }
     }
 }
@@ -290,7 +443,7 @@ int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows) {
 
 }  // namespace
 
-int ring_gemm_i8(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
+int ring_gemm_i8(int mode, const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
                  const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream) {
@@ -303,7 +456,9 @@ int ring_gemm_i8(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(gemm_i8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(gemm_i8_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(gemm_i8_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   IPC_CUDA_TRY(attr_err);
   Params p;
@@ -320,7 +475,10 @@ int ring_gemm_i8(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_
   p.row0 = row0;
   p.status = status_ptr();
   dim3 grid((n_cols + BMQ - 1) / BMQ, static_cast<unsigned>((x_rows + BND - 1) / BND));
-  gemm_i8_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
+  if (mode == 0)
+    gemm_i8_kernel<0><<<grid, kThreads<0>, SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
+  else
+    gemm_i8_kernel<1><<<grid, kThreads<1>, SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }

@@ -47,19 +47,36 @@ __global__ void imad_loop(uint32_t* out, int iters, uint32_t p, uint32_t q) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void dp4a_loop(uint32_t* out, int iters, uint32_t p, uint32_t q) {
+  int x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * (i + 1) + p;
+  const int y = static_cast<int>(q ^ threadIdx.x), z = static_cast<int>(q + blockIdx.x);
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = __dp4a(x[i], y, z);
+  int s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s ^= x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = static_cast<uint32_t>(s);
+}
+
 }  // namespace
 
-// what = 0: mma.sync s8 (returns TOP/s, 2 ops per MAC); what = 1: IMAD (returns T IMAD/s).
+// what = 0: mma.sync s8 (returns TOP/s, 2 ops per MAC); what = 1: IMAD (returns T IMAD/s);
+// what = 2: dp4a (returns TOP/s, 4 MACs = 8 ops per instruction).
 extern "C" int ipc_measure_peak(int what, void* stream, double* out) {
-  if (!out || (what != 0 && what != 1)) {
-    ipc::set_error("ipc_measure_peak: what must be 0 or 1 and out non-null");
+  if (!out || what < 0 || what > 2) {
+    ipc::set_error("ipc_measure_peak: what must be 0, 1 or 2 and out non-null");
     return IPC_EINVAL;
   }
   int dev = 0, sms = 0;
   IPC_CUDA_TRY(cudaGetDevice(&dev));
   IPC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int blocks = sms * 2, threads = 256;
-  const int iters = what == 0 ? 4096 : 2048;
+  const int iters = what == 0 ? 4096 : 2048;  // each variant runs a few milliseconds
   int* buf = nullptr;
   IPC_CUDA_TRY(cudaMalloc(&buf, sizeof(int) * 4 * blocks * threads));  // imad_loop runs 4x the CTAs
   cudaStream_t st = ipc::as_stream(stream);
@@ -71,8 +88,10 @@ extern "C" int ipc_measure_peak(int what, void* stream, double* out) {
     cudaEventRecord(e0, st);
     if (what == 0)
       mma_s8_loop<<<blocks, threads, 0, st>>>(buf, iters);
-    else
+    else if (what == 1)
       imad_loop<<<blocks * 4, threads, 0, st>>>(reinterpret_cast<uint32_t*>(buf), iters, 3u, 5u);
+    else
+      dp4a_loop<<<blocks * 4, threads, 0, st>>>(reinterpret_cast<uint32_t*>(buf), iters, 3u, 5u);
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -87,7 +106,9 @@ extern "C" int ipc_measure_peak(int what, void* stream, double* out) {
   const double warps = blocks * threads / 32.0;
   if (what == 0)
     *out = warps * iters * 8 * (16.0 * 8 * 32 * 2) / (best * 1e-3) / 1e12;
-  else
+  else if (what == 1)
     *out = 4.0 * blocks * threads * iters * 4 * 8 / (best * 1e-3) / 1e12;
+  else
+    *out = 8.0 * 4.0 * blocks * threads * iters * 4 * 8 / (best * 1e-3) / 1e12;
   return IPC_OK;
 }

@@ -58,12 +58,15 @@ def test_plain_vs_precision_full_size(c2):
     w = c2["w"]
     rid8, sh8, dist = _run(w, "i8mma", True, c2["qc"], c2["qm"])
     rid32, sh32, _ = _run(w, "i32", False, c2["qc"], c2["qm"])
-    assert (oracle.reconstruct_bits(sh8) == c2["match"]).all()
-    assert (oracle.reconstruct_bits(sh32) == c2["match"]).all()
+    ridx, shx, distx = _run(w, "i8mix", True, c2["qc"], c2["qm"])
+    for sh in (sh8, sh32, shx):
+        assert (oracle.reconstruct_bits(sh) == c2["match"]).all()
     assert c2["match"].sum() == w.planted
-    # same request id and seeds: the two paths must agree share for share
-    assert rid8 == rid32
-    assert (sh8 == sh32).all()
+    # same request id and seeds: the three paths must agree share for share
+    assert rid8 == rid32 == ridx
+    assert (sh8 == sh32).all() and (sh8 == shx).all()
+    for k in dist:
+        assert (dist[k][0] == distx[k][0]).all() and (dist[k][1] == distx[k][1]).all()
     for (q, rho), (dot, ml) in dist.items():
         assert (ml == c2["ml"][q, rho]).all()
         assert (dot == c2["ml"][q, rho] - 2 * c2["hd"][q, rho]).all()

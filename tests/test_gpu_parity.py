@@ -134,7 +134,7 @@ def _gemm_all(torch, small, path):
     return out
 
 
-@pytest.mark.parametrize("path", ["i8mma", "i32"])
+@pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32"])
 def test_ring_gemm_matches_oracle_shares(small, torch, path):
     zc, zm = _gemm_all(torch, small, path)
     assert (zc == small["ref"]["z_code"]).all()
@@ -171,7 +171,7 @@ def test_compare_and_or_tree_match_oracle_shares(small, torch):
     assert (oracle.reconstruct_bits(small["ref"]["bits"]) == small["match"]).all()
 
 
-@pytest.mark.parametrize("path", ["i8mma", "i32"])
+@pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32"])
 def test_context_end_to_end_small(small, torch, path):
     ipc = lib()
     w = small["w"]
@@ -209,7 +209,7 @@ def test_context_multi_chunk(torch):
     dbc, dbm = oracle.encode_share(dc, dm, L, w.db_share_seed, 0)
     qsc, qsm = oracle.encode_share(qc, qm, L, w.q_share_seed, 1)
     match, _, _ = oracle.plain_match(oracle.Geom(16, 200, 4, -1, 3), qc, qm, dc, dm)
-    for path in ("i8mma", "i32"):
+    for path in ("i8mma", "i8mix", "i32"):
         ctx = make_ctx(w, path=path, chunk_rows=1024)
         try:
             load_workload(ctx, w, chunk=700)
@@ -241,7 +241,7 @@ def test_gemm_exact_at_max_length_and_extreme_limbs(torch):
     y[2] = 0  # party 0's operand is [y_0 + y_2 | y_0] = [0x7F80 | 0x7F80]: C reaches 2l * 2 * 128^2 = 2^30
     tags = torch.from_numpy(tags_for(1, Q, R).view(np.int32)).cuda()
     res = {}
-    for path in ("i8mma", "i32"):
+    for path in ("i8mma", "i8mix", "i32"):
         blo = torch.empty((128, 2 * Lm), dtype=torch.int8, device="cuda")
         bhi = torch.empty((128, 2 * Lm), dtype=torch.int8, device="cuda")
         ipc.ipc_prep_query(y, Q, g, 0, blo, bhi, 128)
@@ -252,8 +252,8 @@ def test_gemm_exact_at_max_length_and_extreme_limbs(torch):
         res[path] = u16(z)[:, :s]
     # equal seeds: the zero share is F - F = 0; z = sum over 2l of 0x7F80^2 (mod 2^16)
     expect = (2 * Lm * 0x7F80 * 0x7F80) & 0xFFFF
-    assert (res["i8mma"] == expect).all()
-    assert (res["i32"] == expect).all()
+    for path in res:
+        assert (res[path] == expect).all(), path
 
 
 def test_degenerate_queries(torch):
