@@ -70,3 +70,93 @@ def test_plain_vs_precision_full_size(c2):
     for (q, rho), (dot, ml) in dist.items():
         assert (ml == c2["ml"][q, rho]).all()
         assert (dot == c2["ml"][q, rho] - 2 * c2["hd"][q, rho]).all()
+
+
+def test_tiny_workload_share_for_share():
+    """1,000 rows x 4 queries, no rotations: every share against the 3-party oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ipc = lib()
+    w = synth.workload("c1")
+    g = oracle.Geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
+    dc, dm = w.db_bits()
+    qc, qm = w.query_bits()
+    dbc, dbm = oracle.encode_share(dc, dm, w.l, w.db_share_seed, 0)
+    qsc, qsm = oracle.encode_share(qc, qm, w.l, w.q_share_seed, 1)
+    match, ml, hd = oracle.plain_match(g, qc, qm, dc, dm, distances=True)
+    for path in ("i8mix", "i8mma", "i32"):
+        ctx = make_ctx(w, path=path, keep=True)
+        try:
+            load_workload(ctx, w)
+            qcode, qmask = query_shares_gpu(w, qc, qm)
+            rid = ipc.submit_queries(ctx, [qcode[j] for j in range(3)], [qmask[j] for j in range(3)], w.Q, 1)
+            sh = np.zeros((3, w.Q), np.uint8)
+            ipc.fetch_bit_shares(ctx, rid, sh, w.Q, 60000)
+            ref = oracle.mpc_match(oracle.mpc_cfg(w.prf_seeds, req=rid), g, dbc, dbm, qsc, qsm)
+            assert (sh == ref["bits"]).all()
+            assert (oracle.reconstruct_bits(sh) == match).all()
+            for q in range(w.Q):
+                dot = np.zeros(w.s, np.int16)
+                mlg = np.zeros(w.s, np.uint16)
+                ipc.fetch_distances(ctx, rid, q, 0, 0, w.s, dot, mlg)
+                assert (mlg == ml[q, 0]).all() and (dot == ml[q, 0] - 2 * hd[q, 0]).all()
+        finally:
+            ipc.ipc_destroy(ctx)
+
+
+def _full_size(name, keep):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ipc = lib()
+    w = synth.workload(name)
+    cb, mb = db_bits_device(w, 0, w.s)
+    dc = cb.cpu().numpy().view(np.uint64)
+    dm = mb.cpu().numpy().view(np.uint64)
+    del cb, mb
+    qc, qm = w.query_bits()
+    match, _, _ = oracle.plain_match(oracle.iris_geom(), qc, qm, dc, dm, threads=os.cpu_count() or 1)
+    ctx = make_ctx(w, path="i8mix", keep=keep, max_queries=w.Q)
+    try:
+        load_workload(ctx, w, chunk=32768)
+        assert ipc.ipc_db_rows(ctx) == w.s
+        qcode, qmask = query_shares_gpu(w, qc, qm)
+        rid = ipc.submit_queries(ctx, [qcode[j] for j in range(3)], [qmask[j] for j in range(3)], w.Q, 1)
+        bits = np.zeros(w.Q, np.uint8)
+        if keep:
+            # distances of each planted query at its planted rotation, every database row
+            for q in w.planted_set()[:4]:
+                p = w.plant(int(q))
+                rho = -p["u"] - w.rot_lo
+                rows = np.array([p["src"], 0, w.s - 1])
+                dot = np.zeros(w.s, np.int16)
+                mlg = np.zeros(w.s, np.uint16)
+                ipc.fetch_distances(ctx, rid, int(q), rho, 0, w.s, dot, mlg)
+                rqc = oracle.rotate_bits(oracle.iris_geom(), qc[q], w.rot_lo + rho)
+                rqm = oracle.rotate_bits(oracle.iris_geom(), qm[q], w.rot_lo + rho)
+                for i in rows:
+                    mli, hdi = oracle.plain_pair(rqc, rqm, dc[i], dm[i])
+                    assert mlg[i] == mli and dot[i] == mli - 2 * hdi
+                assert abs(hdi_frac(dot[p["src"]], mlg[p["src"]]) - p["rate"]) < 0.02
+        ipc.fetch_match_bits(ctx, rid, bits, w.Q, 600000)
+    finally:
+        ipc.ipc_destroy(ctx)
+    assert (bits == match).all()
+    assert sorted(np.nonzero(bits)[0].tolist()) == w.planted_set().tolist()
+
+
+def hdi_frac(dot, ml):
+    """Fraction of masked bits that differ, from the masked dot product: hd = (ml - dot) / 2."""
+    return (int(ml) - int(dot)) / 2 / max(int(ml), 1)
+
+
+def test_planted_workload_full_size():
+    """500,000 rows x 64 queries x 31 rotations (992 M comparisons), half the queries planted."""
+    _full_size("c3", keep=True)
+
+
+def test_largest_workload_full_size():
+    """600,000 rows (about 92 GB of resident shares) x 256 queries x 31 rotations (4.76 G
+    comparisons), 13 planted near-duplicates at 5-15% flipped bits."""
+    _full_size("c5", keep=False)
