@@ -130,13 +130,35 @@ int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t pa
  * (exact: |int32 partial sums| < 2^30), the int8 GEMM split between the tensor
  * cores and the integer pipe's dp4a, or the int32 CUDA-core GEMM; all give
  * identical results. Errors: IPC_EINVAL for l not a multiple of 128, odd
- * ldz, ldz < x_rows, or unaligned pointers (16 B); IPC_ECUDA if the tensor
- * map cannot be encoded.
+ * ldz, ldz < x_rows, x_rows > IPC_MAX_GEMM_ROWS, or unaligned pointers (16 B);
+ * IPC_ECUDA if the tensor map cannot be encoded.
  */
+#define IPC_MAX_GEMM_ROWS (65535u * 128u)
 int ipc_ring_gemm(int path, const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows,
                   const int8_t* b_lo, const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
                   const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
                   uint16_t* z, size_t ldz, uint64_t row0, void* stream);
+
+/*
+ * A3 with an explicit kernel variant and an optional list of column tiles (the form the
+ * serving loop replays inside a CUDA graph). variant: IPC_GEMM_MIX128 (mma.sync + dp4a,
+ * 128-column tiles), IPC_GEMM_MMA128, IPC_GEMM_MMA64, IPC_GEMM_MMA32 (mma.sync only, 128/64/32
+ * query columns per tile). col_tiles (device, may be NULL): indices of the tiles of that width
+ * to compute, n_col_list (device) their count, read when the kernel starts; with NULL every tile
+ * of [0, n_cols) is computed, one CTA per tile. With a list the launch is persistent (one CTA
+ * per SM walking the list), so its grid does not depend on the list's length and the launch can
+ * be replayed from a CUDA graph while the list changes. n_pad must be a multiple of 128 and
+ * cover every listed tile. Other arguments and errors as ipc_ring_gemm.
+ */
+#define IPC_GEMM_MIX128 0
+#define IPC_GEMM_MMA128 1
+#define IPC_GEMM_MMA64 2
+#define IPC_GEMM_MMA32 3
+int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows,
+                        const int8_t* b_lo, const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                        const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
+                        size_t ldz, uint64_t row0, const uint32_t* col_tiles, const uint32_t* n_col_list,
+                        void* stream);
 
 /*
  * A4-A8 (per comparison, and the OR tree inside aligned row blocks).

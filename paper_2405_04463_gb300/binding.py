@@ -64,6 +64,8 @@ _SIGS = {
     "ipc_split_limbs": [_vp, _sz, _vp, _vp, _vp],
     "ipc_prep_query": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_ring_gemm": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
+    "ipc_ring_gemm_tiles": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
+                            _u64, _vp, _vp, _vp],
     "ipc_compare": [_VP3, _VP3, _sz, _u32, _sz, _u64, _vp, _U64x3, _u32, _u32, _vp, _sz, _vp, _sz, _vp],
     "ipc_or_finalize": [_vp, _sz, _u32, _u32, _u32, _u32, _vp, _U64x3, _vp, _vp],
     "ipc_status": [],
@@ -148,6 +150,17 @@ def ipc_ring_gemm(path, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_ta
     _check(lib.ipc_ring_gemm(path, _VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
                              ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
                              seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
+
+
+IPC_GEMM_MIX128, IPC_GEMM_MMA128, IPC_GEMM_MMA64, IPC_GEMM_MMA32 = 0, 1, 2, 3
+
+
+def ipc_ring_gemm_tiles(variant, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev,
+                        vec, z, ldz, row0, col_tiles=None, n_col_list=None, stream=None):
+    _check(lib.ipc_ring_gemm_tiles(variant, _VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows,
+                                   ptr(b_lo), ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
+                                   seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, ptr(col_tiles),
+                                   ptr(n_col_list), _stream(stream)))
 
 
 def ipc_compare(z_code, z_mask, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, log2_block_words, roots,

@@ -9,6 +9,11 @@ int ring_gemm_i8(int mode, const int8_t* const x_lo[2], const int8_t* const x_hi
                  const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream);
+int ring_gemm_i8_variant(int variant, const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows,
+                         const int8_t* b_lo, const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                         const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
+                         size_t ldz, uint64_t row0, const uint32_t* col_tiles, const uint32_t* n_col_list,
+                         cudaStream_t stream);
 int ring_gemm_i32(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
                   const int8_t* b_hi, uint32_t n_cols, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
                   uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, cudaStream_t stream);
@@ -44,7 +49,7 @@ extern "C" int ipc_ring_gemm(int path, const int8_t* const x_lo[2], const int8_t
   if (n_pad < n_cols || n_pad % 128 != 0) return bad("ipc_ring_gemm: n_pad must be >= n_cols and a multiple of 128");
   if (row0 % 8 != 0) return bad("ipc_ring_gemm: row0 must be a multiple of 8");
   if (vec > 1) return bad("ipc_ring_gemm: vec is 0 (code) or 1 (mask)");
-  if (x_rows > (1u << 30)) return bad("ipc_ring_gemm: too many rows in one call");
+  if (x_rows > IPC_MAX_GEMM_ROWS) return bad("ipc_ring_gemm: too many rows in one call");
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
   if (path == IPC_PATH_I8MMA || path == IPC_PATH_I8MIX)
     return ring_gemm_i8(path == IPC_PATH_I8MMA ? 0 : 1, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
@@ -53,6 +58,42 @@ extern "C" int ipc_ring_gemm(int path, const int8_t* const x_lo[2], const int8_t
     return ring_gemm_i32(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, l, col_tags, seed_own, seed_prev, vec, z, ldz, row0,
                          as_stream(stream));
   return bad("ipc_ring_gemm: unknown path");
+}
+
+namespace {
+int check_gemm_args(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
+                    const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+                    uint32_t vec, const uint16_t* z, size_t ldz, uint64_t row0, const char* who) {
+  auto fail = [&](const char* what) { return bad((std::string(who) + ": " + what).c_str()); };
+  if (!x_lo || !x_hi || !b_lo || !b_hi || !col_tags || !z) return fail("null pointer");
+  for (int i = 0; i < 2; ++i)
+    if (!x_lo[i] || !x_hi[i] || !aligned(x_lo[i], 16) || !aligned(x_hi[i], 16))
+      return fail("database planes must be non-null and 16-byte aligned");
+  if (!aligned(b_lo, 16) || !aligned(b_hi, 16) || !aligned(z, 16)) return fail("unaligned operand");
+  if (l == 0 || l % 128 != 0 || l > 16384) return fail("l must be a multiple of 128, at most 16384");
+  if (ldz % 8 != 0 || ldz < x_rows) return fail("ldz must be a multiple of 8 and >= x_rows");
+  if (n_pad < n_cols || n_pad % 128 != 0) return fail("n_pad must be >= n_cols and a multiple of 128");
+  if (row0 % 8 != 0) return fail("row0 must be a multiple of 8");
+  if (vec > 1) return fail("vec is 0 (code) or 1 (mask)");
+  if (x_rows > IPC_MAX_GEMM_ROWS) return fail("too many rows in one call");
+  return IPC_OK;
+}
+}  // namespace
+
+extern "C" int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], const int8_t* const x_hi[2],
+                                   size_t x_rows, const int8_t* b_lo, const int8_t* b_hi, uint32_t n_cols,
+                                   uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                                   uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                                   const uint32_t* col_tiles, const uint32_t* n_col_list, void* stream) {
+  int rc = check_gemm_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                           "ipc_ring_gemm_tiles");
+  if (rc) return rc;
+  if (variant < IPC_GEMM_MIX128 || variant > IPC_GEMM_MMA32) return bad("ipc_ring_gemm_tiles: unknown variant");
+  if ((col_tiles == nullptr) != (n_col_list == nullptr))
+    return bad("ipc_ring_gemm_tiles: col_tiles and n_col_list go together");
+  if (x_rows == 0 || n_cols == 0) return IPC_OK;
+  return ring_gemm_i8_variant(variant, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+                              seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
 }
 
 extern "C" int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,

@@ -293,3 +293,41 @@ def test_empty_and_invalid_calls_are_rejected_without_launch(torch):
             ipc.fetch_match_bits(ctx, 12345, np.zeros(1, np.uint8), 1, 0)
     finally:
         ipc.ipc_destroy(ctx)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_gemm_variants_and_tile_lists_match_int32(torch, variant):
+    """Every GEMM variant (mixed / tensor-only with 128, 64, 32-column tiles), over all tiles and
+    over a sparse list of column tiles, equals the int32 path on random full-range operands."""
+    ipc = lib()
+    rows, N, n_pad = 1000, 300, 384
+    g = torch.Generator(device="cpu").manual_seed(variant)
+    planes = [torch.randint(-128, 128, (rows, L), dtype=torch.int8, generator=g).cuda() for _ in range(4)]
+    blo = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    bhi = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    tags = torch.from_numpy(tags_for(3, 10, 30).view(np.int32)).cuda()
+    ldz = 1000
+    ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, ref, ldz, 8)
+    z = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tiles(variant, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, z, ldz, 8)
+    torch.cuda.synchronize()
+    ipc.ipc_status()
+    assert (z.cpu() == ref.cpu()).all()
+    bq = (128, 128, 64, 32)[variant]
+    ntile = (N + bq - 1) // bq
+    chosen = [t for t in range(ntile) if t % 3 != 1]
+    lst = torch.tensor(chosen, dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([len(chosen)], dtype=torch.int32, device="cuda")
+    z2 = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tiles(variant, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, z2, ldz, 8,
+                            lst, cnt)
+    torch.cuda.synchronize()
+    ipc.ipc_status()
+    z2, refc = z2.cpu(), ref.cpu()
+    for t in range(ntile):
+        cols = slice(t * bq, min(N, (t + 1) * bq))
+        if t in chosen:
+            assert (z2[cols, :rows] == refc[cols, :rows]).all(), t
+        else:
+            assert (z2[cols] == 77).all(), t
