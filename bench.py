@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
-    ap.add_argument("--kernel", default=None, help="time one ring-GEMM path alone (i8mma | i32), for profiling")
+    ap.add_argument("--kernel", default=None, help="time one ring-GEMM path alone (i8mix | i8mma | i32 | tc), for profiling")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
     return ap.parse_args()
@@ -68,10 +68,21 @@ def run_kernel(args, w):
     z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ipc.ipc_ring_gemm(args.kernel, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+    if args.kernel == "tc":
+        # the same limbs as bf16 bit patterns (operand conversion outside the timed launches)
+        planes = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in planes]
+        blo, bhi = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in (blo, bhi)]
+
+        def launch():
+            ipc.ipc_ring_gemm_tc(planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+    else:
+        def launch():
+            ipc.ipc_ring_gemm(args.kernel, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z,
+                              rows, 0)
+    launch()
     e0.record(st)
     for _ in range(args.reps):
-        ipc.ipc_ring_gemm(args.kernel, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+        launch()
     e1.record(st)
     e1.synchronize()
     ipc.ipc_status()
@@ -79,7 +90,8 @@ def run_kernel(args, w):
     macs = 3.0 * N * rows * 2 * l if args.kernel != "i32" else 1.0 * N * rows * 2 * l
     print(json.dumps({"kernel": args.kernel, "rows": rows, "cols": N, "ms_per_launch": ms,
                       "algorithmic_ops_per_launch": 2 * macs, "achieved_tops": 2 * macs / (ms * 1e-3) / 1e12,
-                      "operand_bytes_per_launch": 4 * rows * l + 2 * n_pad * 2 * l, "z_bytes": 2 * N * rows}))
+                      "operand_bytes_per_launch": (2 if args.kernel == "tc" else 1) * (4 * rows * l + 2 * n_pad * 2 * l),
+                      "z_bytes": 2 * N * rows}))
 
 
 def dist_env():

@@ -57,6 +57,7 @@ extern "C" {
 #define IPC_PATH_I8MMA 0  /* int8 limb GEMM on the tensor cores (mma.sync s8, TMA-fed) */
 #define IPC_PATH_I32 1    /* plain int32 CUDA-core ring GEMM (IMAD) */
 #define IPC_PATH_I8MIX 2  /* int8 limb GEMM split between mma.sync s8 and dp4a in every tile */
+#define IPC_PATH_TC 3     /* the same limbs as bf16 on tcgen05 (TMEM accumulators, exact) */
 
 /* PRF domains: high byte of Philox counter word 3. */
 #define IPC_D_SHARE 1u
@@ -101,6 +102,13 @@ int ipc_encode_share(const uint64_t* code_bits, const uint64_t* mask_bits, uint3
 int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8_t* hi, void* stream);
 
 /*
+ * A1 for IPC_PATH_TC: the same limbs, each written as the bf16 bit pattern of
+ * its integer value (exact: |limb| <= 128). lo, hi: count uint16 each.
+ * Errors: IPC_EINVAL if count is 0 or a pointer is not 16-byte aligned.
+ */
+int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* lo, uint16_t* hi, void* stream);
+
+/*
  * A2 -- query preparation for one party. y: [3][Q][l] uint16, the additive
  * components of one query vector (code or mask), unrotated. For party i and
  * column n = q*R + rho it writes the row
@@ -113,6 +121,10 @@ int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8_t* hi, voi
  */
 int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
                    int8_t* b_hi, uint32_t n_pad, void* stream);
+
+/* A2 for IPC_PATH_TC: as ipc_prep_query, limbs written as bf16 bit patterns. */
+int ipc_prep_query_bf16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
+                        uint16_t* b_hi, uint32_t n_pad, void* stream);
 
 /*
  * A3 -- share-domain dot products of one party for one vector (App. C), as a
@@ -159,6 +171,21 @@ int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], const int8_t* 
                         const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
                         size_t ldz, uint64_t row0, const uint32_t* col_tiles, const uint32_t* n_col_list,
                         void* stream);
+
+/*
+ * A3 on the tcgen05 tensor cores (IPC_PATH_TC): the same ring GEMM and the same
+ * z as ipc_ring_gemm, with operands from ipc_split_limbs_bf16 and
+ * ipc_prep_query_bf16 (bf16 bit patterns of the int8 limbs; x planes
+ * [x_rows][l], b planes [n_pad][2l]). The products run as bf16 MMAs with fp32
+ * accumulators in tensor memory; each accumulator restarts every 64 k at
+ * 1.5 * 2^23, so all partial sums stay integers inside [2^23, 2^24) where fp32
+ * addition is exact, and the result is bit-identical to the integer paths.
+ * Arguments, alignment rules and errors as ipc_ring_gemm.
+ */
+int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+                     const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                     const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
+                     size_t ldz, uint64_t row0, void* stream);
 
 /*
  * A4-A8 (per comparison, and the OR tree inside aligned row blocks).
@@ -241,7 +268,7 @@ typedef struct ipc_ctx ipc_ctx;
 typedef struct {
   ipc_geom geom;            /* {16, 200, 4, -15, 31} for the deployed system */
   uint32_t thr_a;           /* a of the threshold a/b with b = 2^16; 16384 for MATCH_RATIO 0.375 */
-  int32_t path;             /* IPC_PATH_I8MMA, IPC_PATH_I8MIX or IPC_PATH_I32 */
+  int32_t path;             /* IPC_PATH_I8MMA, IPC_PATH_I8MIX, IPC_PATH_I32 or IPC_PATH_TC */
   uint32_t db_chunk_rows;   /* rows per resident chunk and pipeline step; multiple of 1024; 0 = 65536 */
   uint32_t max_queries;     /* largest request accepted by submit_queries; 0 = 256 */
   uint64_t seeds[3];        /* pairwise PRF seeds; seeds[j] shared by parties j and j+1 */

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libipcheck.so")
 
 IPC_OK, IPC_EINVAL, IPC_ENOMEM, IPC_ECUDA, IPC_ETIMEOUT = 0, -1, -2, -3, -4
 IPC_EAGAIN, IPC_ENOTFOUND, IPC_EDEVICE, IPC_ENOSYS = -5, -6, -7, -8
-IPC_PATH_I8MMA, IPC_PATH_I32, IPC_PATH_I8MIX = 0, 1, 2
-PATHS = {"i8mma": IPC_PATH_I8MMA, "i32": IPC_PATH_I32, "i8mix": IPC_PATH_I8MIX}
+IPC_PATH_I8MMA, IPC_PATH_I32, IPC_PATH_I8MIX, IPC_PATH_TC = 0, 1, 2, 3
+PATHS = {"i8mma": IPC_PATH_I8MMA, "i32": IPC_PATH_I32, "i8mix": IPC_PATH_I8MIX, "tc": IPC_PATH_TC}
 
 
 class IpcError(RuntimeError):
@@ -63,6 +63,9 @@ _SIGS = {
     "ipc_encode_share": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
     "ipc_split_limbs": [_vp, _sz, _vp, _vp, _vp],
     "ipc_prep_query": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
+    "ipc_split_limbs_bf16": [_vp, _sz, _vp, _vp, _vp],
+    "ipc_prep_query_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
+    "ipc_ring_gemm_tc": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
     "ipc_ring_gemm": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
     "ipc_ring_gemm_tiles": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
                             _u64, _vp, _vp, _vp],
@@ -150,6 +153,22 @@ def ipc_ring_gemm(path, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_ta
     _check(lib.ipc_ring_gemm(path, _VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
                              ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
                              seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
+
+
+def ipc_split_limbs_bf16(x, count, lo, hi, stream=None):
+    _check(lib.ipc_split_limbs_bf16(ptr(x), count, ptr(lo), ptr(hi), _stream(stream)))
+
+
+def ipc_prep_query_bf16(y, Q, geom: ipc_geom, party, b_lo, b_hi, n_pad, stream=None):
+    _check(lib.ipc_prep_query_bf16(ptr(y), Q, ctypes.byref(geom), party, ptr(b_lo), ptr(b_hi), n_pad,
+                                   _stream(stream)))
+
+
+def ipc_ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
+                     row0, stream=None):
+    _check(lib.ipc_ring_gemm_tc(_VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
+                                ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
+                                seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
 
 
 IPC_GEMM_MIX128, IPC_GEMM_MMA128, IPC_GEMM_MMA64, IPC_GEMM_MMA32 = 0, 1, 2, 3

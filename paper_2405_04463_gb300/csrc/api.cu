@@ -22,6 +22,10 @@ int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask
                    uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, cudaStream_t st);
 int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t p, uint32_t Q, uint32_t R,
                        const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares, cudaStream_t st);
+int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+                 const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+                 uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                 cudaStream_t stream);
 const char* thread_last_error();
 
 namespace {
@@ -94,6 +98,28 @@ extern "C" int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], con
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
   return ring_gemm_i8_variant(variant, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
+}
+
+extern "C" int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+                                const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
+                                uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
+                                uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, void* stream) {
+  const char* who = "ipc_ring_gemm_tc";
+  auto fail = [&](const char* what) { return bad((std::string(who) + ": " + what).c_str()); };
+  if (!x_lo || !x_hi || !b_lo || !b_hi || !col_tags || !z) return fail("null pointer");
+  for (int i = 0; i < 2; ++i)
+    if (!x_lo[i] || !x_hi[i] || !aligned(x_lo[i], 16) || !aligned(x_hi[i], 16))
+      return fail("database planes must be non-null and 16-byte aligned");
+  if (!aligned(b_lo, 16) || !aligned(b_hi, 16) || !aligned(z, 16)) return fail("unaligned operand");
+  if (l == 0 || l % 128 != 0 || l > 16384) return fail("l must be a multiple of 128, at most 16384");
+  if (ldz % 8 != 0 || ldz < x_rows) return fail("ldz must be a multiple of 8 and >= x_rows");
+  if (n_pad < n_cols || n_pad % 128 != 0) return fail("n_pad must be >= n_cols and a multiple of 128");
+  if (row0 % 8 != 0) return fail("row0 must be a multiple of 8");
+  if (vec > 1) return fail("vec is 0 (code) or 1 (mask)");
+  if (x_rows > IPC_MAX_GEMM_ROWS) return fail("too many rows in one call");
+  if (x_rows == 0 || n_cols == 0) return IPC_OK;
+  return ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
+                      row0, as_stream(stream));
 }
 
 extern "C" int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,

@@ -27,7 +27,7 @@ namespace {
 constexpr uint32_t kLog2BlockWords = 5;  // 1024-row OR blocks inside ipc_compare
 
 struct Chunk {
-  int8_t* planes = nullptr;  // 12 planes [cap][l]: ((component * 2 + vec) * 2 + limb)
+  uint8_t* planes = nullptr;  // 12 planes [cap][l] of limbs: ((component * 2 + vec) * 2 + limb)
   size_t cap = 0;
   size_t rows = 0;
   uint64_t row0 = 0;
@@ -36,7 +36,7 @@ struct Chunk {
 struct Request {
   uint64_t id = 0;
   uint32_t Q = 0, N = 0, n_pad = 0;
-  int8_t* bq = nullptr;         // [party][vec][limb][n_pad][2l]
+  uint8_t* bq = nullptr;        // [party][vec][limb][n_pad][2l] limbs
   uint16_t* qstage = nullptr;   // [vec][3][Q][l] query shares
   uint32_t* tags = nullptr;     // [N][2]
   uint32_t* roots = nullptr;    // [3][N][ld_roots]
@@ -53,6 +53,7 @@ struct Request {
 struct ipc_ctx {
   ipc_config cfg{};
   uint32_t l = 0;
+  uint32_t esz = 1;  // bytes per limb: int8, or bf16 for IPC_PATH_TC
   cudaStream_t sp[3] = {nullptr, nullptr, nullptr};
   cudaStream_t sc = nullptr;
   cudaEvent_t ev_setup = nullptr, ev_gemm[3][2] = {}, ev_cmp[2] = {};
@@ -95,8 +96,8 @@ int cfail(ipc_ctx* c, cudaError_t e, const char* what) {
     }                                              \
   } while (0)
 
-int8_t* plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
-  return ch.planes + static_cast<size_t>((comp * 2 + vec) * 2 + limb) * ch.cap * c->l;
+uint8_t* plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
+  return ch.planes + static_cast<size_t>((comp * 2 + vec) * 2 + limb) * ch.cap * c->l * c->esz;
 }
 
 uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
@@ -176,7 +177,8 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   const uint64_t l = static_cast<uint64_t>(g.rows) * g.cols * g.cell;
   if (l == 0 || l % 128 != 0 || l > 16384 || g.R == 0 || g.R > 31)
     return fail(nullptr, IPC_EINVAL, "ipc_create: l must be a multiple of 128 up to 16384 and 1 <= R <= 31");
-  if (cfg->path != IPC_PATH_I8MMA && cfg->path != IPC_PATH_I32 && cfg->path != IPC_PATH_I8MIX)
+  if (cfg->path != IPC_PATH_I8MMA && cfg->path != IPC_PATH_I32 && cfg->path != IPC_PATH_I8MIX &&
+      cfg->path != IPC_PATH_TC)
     return fail(nullptr, IPC_EINVAL, "ipc_create: path");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
   ipc_ctx* c = new ipc_ctx();
@@ -184,6 +186,7 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   if (c->cfg.db_chunk_rows == 0) c->cfg.db_chunk_rows = 65536;
   if (c->cfg.max_queries == 0) c->cfg.max_queries = 256;
   c->l = static_cast<uint32_t>(l);
+  c->esz = cfg->path == IPC_PATH_TC ? 2 : 1;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete c;
@@ -262,7 +265,7 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
     Chunk ch;
     ch.cap = cap;
     ch.row0 = next_row0;
-    if (cudaMalloc(&ch.planes, 12 * cap * l) != cudaSuccess) {
+    if (cudaMalloc(&ch.planes, 12 * cap * l * c->esz) != cudaSuccess) {
       cudaGetLastError();
       for (auto& f : fresh) cudaFree(f.planes);
       return fail(c, IPC_ENOMEM, "load_db_shares: device memory exhausted");
@@ -290,8 +293,14 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
       for (int j = 0; j < 3; ++j) {
         const uint16_t* src = (vec == 0 ? code[j] : mask[j]) + done * l;
         CTX_TRY(c, cudaMemcpyAsync(c->stage, src, take * l * sizeof(uint16_t), kind, c->sc));
-        CTX_RC(c, ipc_split_limbs(c->stage, take * l, plane(c, *ch, j, vec, 0) + ch->rows * l,
-                                  plane(c, *ch, j, vec, 1) + ch->rows * l, c->sc));
+        uint8_t* lo = plane(c, *ch, j, vec, 0) + ch->rows * l * c->esz;
+        uint8_t* hi = plane(c, *ch, j, vec, 1) + ch->rows * l * c->esz;
+        if (c->esz == 2)
+          CTX_RC(c, ipc_split_limbs_bf16(c->stage, take * l, reinterpret_cast<uint16_t*>(lo),
+                                         reinterpret_cast<uint16_t*>(hi), c->sc));
+        else
+          CTX_RC(c, ipc_split_limbs(c->stage, take * l, reinterpret_cast<int8_t*>(lo), reinterpret_cast<int8_t*>(hi),
+                                    c->sc));
       }
     ch->rows += take;
     done += take;
@@ -321,7 +330,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   r.n_pad = n_pad;
   const size_t total_blocks = (c->chunks.size() * c->cfg.db_chunk_rows) >> (5 + kLog2BlockWords);
   r.ld_roots = total_blocks;
-  bool ok = cudaMalloc(&r.bq, 12ull * n_pad * 2 * l) == cudaSuccess &&
+  bool ok = cudaMalloc(&r.bq, 12ull * n_pad * 2 * l * c->esz) == cudaSuccess &&
             cudaMalloc(&r.qstage, 2ull * 3 * Q * l * sizeof(uint16_t)) == cudaSuccess &&
             cudaMalloc(&r.tags, 2ull * N * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&r.roots, 3ull * N * r.ld_roots * sizeof(uint32_t)) == cudaSuccess &&
@@ -359,13 +368,19 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
                                  static_cast<size_t>(Q) * l * sizeof(uint16_t), kind, c->sc));
   CTX_TRY(c, cudaEventRecord(c->ev_setup, c->sc));
   // the host tags vector dies at return: make the copy complete before that
-  const size_t qplane = static_cast<size_t>(n_pad) * 2 * l;
+  const size_t qplane = static_cast<size_t>(n_pad) * 2 * l * c->esz;
   auto bq = [&](int party, int vec, int limb) { return r.bq + ((party * 2 + vec) * 2 + limb) * qplane; };
   for (int i = 0; i < 3; ++i) {
     CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
-    for (int vec = 0; vec < 2; ++vec)
-      CTX_RC(c, ipc_prep_query(r.qstage + static_cast<size_t>(vec) * 3 * Q * l, Q, &g, i, bq(i, vec, 0),
-                               bq(i, vec, 1), n_pad, c->sp[i]));
+    for (int vec = 0; vec < 2; ++vec) {
+      const uint16_t* y = r.qstage + static_cast<size_t>(vec) * 3 * Q * l;
+      if (c->esz == 2)
+        CTX_RC(c, ipc_prep_query_bf16(y, Q, &g, i, reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
+                                      reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
+      else
+        CTX_RC(c, ipc_prep_query(y, Q, &g, i, reinterpret_cast<int8_t*>(bq(i, vec, 0)),
+                                 reinterpret_cast<int8_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
+    }
   }
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const Chunk& ch = c->chunks[ci];
@@ -389,11 +404,22 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       const int prev = (i + 2) % 3;
       CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
       for (int vec = 0; vec < 2; ++vec) {
-        const int8_t* xl[2] = {plane(c, ch, i, vec, 0), plane(c, ch, prev, vec, 0)};
-        const int8_t* xh[2] = {plane(c, ch, i, vec, 1), plane(c, ch, prev, vec, 1)};
-        CTX_RC(c, ipc_ring_gemm(c->cfg.path, xl, xh, ch.rows, bq(i, vec, 0), bq(i, vec, 1), N, n_pad, l, r.tags,
-                                c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec),
-                                vec == 0 ? zc[i] : zm[i], ldz, ch.row0, c->sp[i]));
+        uint16_t* zo = vec == 0 ? zc[i] : zm[i];
+        if (c->cfg.path == IPC_PATH_TC) {
+          auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
+          const uint16_t* xl[2] = {p16(plane(c, ch, i, vec, 0)), p16(plane(c, ch, prev, vec, 0))};
+          const uint16_t* xh[2] = {p16(plane(c, ch, i, vec, 1)), p16(plane(c, ch, prev, vec, 1))};
+          CTX_RC(c, ipc_ring_gemm_tc(xl, xh, ch.rows, p16(bq(i, vec, 0)), p16(bq(i, vec, 1)), N, n_pad, l, r.tags,
+                                     c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz,
+                                     ch.row0, c->sp[i]));
+        } else {
+          auto p8 = [](const uint8_t* p) { return reinterpret_cast<const int8_t*>(p); };
+          const int8_t* xl[2] = {p8(plane(c, ch, i, vec, 0)), p8(plane(c, ch, prev, vec, 0))};
+          const int8_t* xh[2] = {p8(plane(c, ch, i, vec, 1)), p8(plane(c, ch, prev, vec, 1))};
+          CTX_RC(c, ipc_ring_gemm(c->cfg.path, xl, xh, ch.rows, p8(bq(i, vec, 0)), p8(bq(i, vec, 1)), N, n_pad, l,
+                                  r.tags, c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz,
+                                  ch.row0, c->sp[i]));
+        }
       }
       CTX_TRY(c, cudaEventRecord(c->ev_gemm[i][set], c->sp[i]));
       CTX_TRY(c, cudaStreamWaitEvent(c->sc, c->ev_gemm[i][set], 0));

@@ -1,0 +1,475 @@
+// A3 on the 5th-generation tensor cores: tcgen05.mma (kind::f16) with bf16 operands carrying the
+// balanced int8 limbs, fp32 accumulators in tensor memory.
+//
+// The ring product is the same three limb products as the int8 paths (Sec. 6.1):
+//     z = L + 256 C + r  (mod 2^16),  L = sum lo*lo',  C = sum (lo*hi' + hi*lo').
+// sm_103a has no integer tcgen05 kind, but the arithmetic stays exact on the bf16 kind:
+//   * every limb is an integer in [-128, 127], exactly a bf16 value;
+//   * every product is an integer with |p| <= 2^14, exact in fp32;
+//   * an accumulator starts each chunk of 64 k at M = 1.5 * 2^23 and receives at most 128 products
+//     (C: two per k), so every partial sum is an integer within M +- 2^21, inside [2^23, 2^24),
+//     where consecutive fp32 values are 1 apart: whatever the order or rounding of the additions,
+//     each one is exact;
+//   * in that binade the fp32 bit pattern of M + v is bits(M) + v, and bits(M) = 0x4B400000 is
+//     0 mod 2^16, so the raw bits of the two accumulators, added as integers (L + (C << 8)) over
+//     all chunks, give z - r mod 2^16 with no conversion instruction.
+//
+// Pipeline (one CTA per 128 database rows x 256 query columns, 10 warps):
+//   warp 0 lane 0  TMA producer: per k-block of 32 elements, four tiles (database lo/hi 128 x 32,
+//                  query lo/hi 256 x 32, 64-byte swizzle) into a 4-stage ring.
+//   warp 1 lane 0  MMA issuer: per chunk of two k-blocks, the C products (8 MMAs of 128x256x16)
+//                  then the L products (4 MMAs), committing C-full, stage-empty and L-full.
+//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 128 columns; after
+//                  C-full it reads C, adds C << 8 to its int32 running sums and stores M back, then
+//                  the same for L. C is drained while the L products run and L while the next
+//                  chunk's C products run, so the tensor pipe does not wait for the drain.
+// TMEM: L in columns [0, 256), C in [256, 512).
+// Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
+// status word, lets its copies and MMAs finish, frees its tensor memory and stores nothing.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace ipc {
+namespace {
+
+constexpr int TM = 128;          // database rows per tile (MMA M = TMEM lanes)
+constexpr int TN = 256;          // query columns per tile (MMA N)
+constexpr int KB = 32;           // bf16 elements of K per stage: one 64-byte swizzled row
+constexpr int STAGES = 4;
+constexpr int KB_PER_CHUNK = 2;  // k-blocks per accumulator chunk (64 k)
+constexpr int A_BYTES = TM * KB * 2;                    // 8 KiB
+constexpr int B_BYTES = TN * KB * 2;                    // 16 KiB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 KiB
+constexpr int THREADS = 10 * 32;
+constexpr int DRAIN_THREADS = 8 * 32;
+constexpr int NUM_BARS = 2 * STAGES + 5;  // full[S], empty[S], c_full, c_empty, l_full, l_empty, done
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NUM_BARS;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_C = 256;          // column offset of the C accumulator
+constexpr uint32_t MAGIC = 0x4B400000u;   // fp32 bits of 1.5 * 2^23
+// z of one tile, [TN][TM] uint16, staged in the (then idle) stage ring
+static_assert(TN * TM * 2 <= STAGES * STAGE_BYTES, "z tile must fit the stage ring");
+
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1), B bf16
+// (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
+                           (static_cast<uint32_t>(TM >> 4) << 24);
+
+struct TcParams {
+  uint32_t n_cols;
+  uint32_t x_rows;
+  uint32_t kb_total;  // 2l / KB
+  uint32_t kb_half;   // l / KB
+  const uint32_t* col_tags;
+  uint64_t seed_own, seed_prev;
+  uint32_t vec;
+  uint16_t* z;
+  uint64_t ldz;
+  uint64_t row0;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of the given parity. Gives up after 2 s (raising the status word and the
+// CTA's abort flag) or, when `abort` is given, as soon as another role has raised that flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status, volatile uint32_t* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (abort && *abort) return false;
+    if (global_ns() - t0 > 2000000000ull) {
+      raise_status(status, ST_WAIT_TIMEOUT);
+      if (abort) *abort = 1u;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row core-matrix groups 512 bytes
+// apart (SBO), LBO unused for this layout (1), descriptor version 1 (bits 46-47), layout type
+// SWIZZLE_64B (4 at bits 61-63). Stage tiles are 1024-byte aligned, so the base offset is 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (static_cast<uint64_t>(512 >> 4) << 32) |
+         (1ull << 46) | (4ull << 61);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(1u)
+      : "memory");
+}
+
+// Arrives on the mbarrier once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 8 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+// Stores v into 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(v)
+      : "memory");
+}
+
+// a += d, hidden from the compiler so that it keeps one running TMEM address instead of
+// materialising every offset of an unrolled loop in its own register
+__device__ __forceinline__ void bump(uint32_t& a, uint32_t d) { asm volatile("add.u32 %0, %0, %1;" : "+r"(a) : "r"(d)); }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tb_lo, const __grid_constant__ CUtensorMap tb_hi,
+                   const __grid_constant__ CUtensorMap ta0_lo, const __grid_constant__ CUtensorMap ta0_hi,
+                   const __grid_constant__ CUtensorMap ta1_lo, const __grid_constant__ CUtensorMap ta1_hi,
+                   const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ uint32_t s_abort;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t tiles = smem_addr(smem);
+  const uint32_t bars = tiles + STAGES * STAGE_BYTES;
+  const uint32_t full0 = bars, empty0 = bars + 8 * STAGES;
+  const uint32_t c_full = bars + 16 * STAGES, c_empty = c_full + 8, l_full = c_full + 16, l_empty = c_full + 24,
+                 done_bar = c_full + 32;
+  volatile uint32_t* abort = &s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t q0 = blockIdx.x * TN, d0 = blockIdx.y * TM;
+  const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(c_full, 1);
+    mbar_init(c_empty, DRAIN_THREADS / 32);
+    mbar_init(l_full, 1);
+    mbar_init(l_empty, DRAIN_THREADS / 32);
+    mbar_init(done_bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    // ------------------------------- TMA producer -------------------------------
+    if (lane == 0) {
+      uint32_t issued = 0;
+      for (uint32_t G = 0; G < p.kb_total; ++G) {
+        const uint32_t s = G % STAGES;
+        if (!mbar_wait(empty0 + 8 * s, ((G / STAGES) & 1u) ^ 1u, p.status, abort)) break;
+        const uint32_t full = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
+        mbar_expect_tx(full, STAGE_BYTES);
+        const bool first = G < p.kb_half;
+        const int32_t kx = static_cast<int32_t>((first ? G : G - p.kb_half) * KB);
+        tma_load(base, first ? &ta0_lo : &ta1_lo, kx, static_cast<int32_t>(d0), full);
+        tma_load(base + A_BYTES, first ? &ta0_hi : &ta1_hi, kx, static_cast<int32_t>(d0), full);
+        tma_load(base + 2 * A_BYTES, &tb_lo, static_cast<int32_t>(G * KB), static_cast<int32_t>(q0), full);
+        tma_load(base + 2 * A_BYTES + B_BYTES, &tb_hi, static_cast<int32_t>(G * KB), static_cast<int32_t>(q0), full);
+        issued = G + 1;
+      }
+      if (*abort) {
+        // copies that may still be in flight land before the CTA leaves (bounded, no abort)
+        for (uint32_t G = issued > STAGES ? issued - STAGES : 0; G < issued; ++G)
+          mbar_wait(full0 + 8 * (G % STAGES), (G / STAGES) & 1u, p.status, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    // -------------------------------- MMA issuer --------------------------------
+    if (lane == 0) {
+      const uint32_t tL = tmem, tC = tmem + TMEM_C;
+      for (uint32_t c = 0; c < n_chunks; ++c) {
+        const uint32_t par = c & 1u, G0 = c * KB_PER_CHUNK;
+        if (!mbar_wait(c_empty, par, p.status, abort)) break;
+        fence_after();
+        bool ok = true;
+        for (uint32_t kb = 0; kb < KB_PER_CHUNK; ++kb) {
+          const uint32_t G = G0 + kb, s = G % STAGES;
+          if (!mbar_wait(full0 + 8 * s, (G / STAGES) & 1u, p.status, abort)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t base = tiles + s * STAGE_BYTES;
+#pragma unroll
+          for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+            const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
+            umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o));      // lo * hi'
+            umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o));      // hi * lo'
+          }
+        }
+        if (!ok) break;
+        umma_commit(c_full);
+        if (!mbar_wait(l_empty, par, p.status, abort)) break;
+        fence_after();
+        for (uint32_t kb = 0; kb < KB_PER_CHUNK; ++kb) {
+          const uint32_t s = (G0 + kb) % STAGES;
+          const uint32_t base = tiles + s * STAGE_BYTES;
+#pragma unroll
+          for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+            const uint32_t o = 32u * ks;
+            umma(tL, sdesc(base + o), sdesc(base + 2 * A_BYTES + o));  // lo * lo'
+          }
+          umma_commit(empty0 + 8 * s);
+        }
+        umma_commit(l_full);
+      }
+      // every MMA issued above completes before the tensor memory is freed
+      umma_commit(done_bar);
+      mbar_wait(done_bar, 0, p.status, nullptr);
+    }
+  } else {
+    // ----------------------------------- drain ----------------------------------
+    const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - 2) >> 2;
+    const uint32_t tL = tmem + ((32u * q) << 16) + 128u * h, tC = tL + TMEM_C;
+    uint32_t z[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) z[j] = 0;
+#pragma unroll
+    for (uint32_t g = 0; g < 4; ++g) {
+      tmem_fill32(tL + 32 * g, MAGIC);
+      tmem_fill32(tC + 32 * g, MAGIC);
+    }
+    tmem_wait_st();
+    fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(c_empty);
+      mbar_arrive(l_empty);
+    }
+    for (uint32_t c = 0; c < n_chunks; ++c) {
+      const uint32_t par = c & 1u;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(c_full, par, p.status, abort))) break;
+      fence_after();
+{
+        uint32_t ta = tC, tf = tC;
+#pragma unroll
+        for (uint32_t g = 0; g < 16; ++g) {
+          uint32_t r[8];
+          tmem_ld8(ta, r);
+          bump(ta, 8);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) z[8 * g + j] += r[j] << 8;
+          if ((g & 3) == 3) {
+            tmem_fill32(tf, MAGIC);
+            bump(tf, 32);
+          }
+        }
+      }
+      tmem_wait_st();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(c_empty);
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(l_full, par, p.status, abort))) break;
+      fence_after();
+{
+        uint32_t ta = tL, tf = tL;
+#pragma unroll
+        for (uint32_t g = 0; g < 16; ++g) {
+          uint32_t r[8];
+          tmem_ld8(ta, r);
+          bump(ta, 8);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) z[8 * g + j] += r[j];
+          if ((g & 3) == 3) {
+            tmem_fill32(tf, MAGIC);
+            bump(tf, 32);
+          }
+        }
+      }
+      tmem_wait_st();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(l_empty);
+    }
+    // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) (App. C) ----
+    // The running sums go to shared memory (the stage ring is idle once every drainer has seen
+    // the last L-full), then each (column, 8-row group) item adds its zero shares, which one
+    // Philox block per seed gives for all 8 rows, and writes 16 bytes of z.
+    named_sync(1, DRAIN_THREADS);
+    if (!*abort) {
+      uint16_t* zs = reinterpret_cast<uint16_t*>(smem);  // [TN][TM]
+      const uint32_t row = 32 * q + lane;
+#pragma unroll
+      for (int j = 0; j < 128; ++j) zs[(128 * h + j) * TM + row] = static_cast<uint16_t>(z[j]);
+      named_sync(1, DRAIN_THREADS);
+      const uint32_t dt = threadIdx.x - 64;
+      const uint32_t grp0 = static_cast<uint32_t>((p.row0 + d0) >> 3);
+      const uint32_t ctr3 = (IPC_D_ZA << 24) | p.vec;
+      for (uint32_t it = dt; it < TN * (TM / 8); it += DRAIN_THREADS) {
+        const uint32_t cc = it / (TM / 8), g = it % (TM / 8), col = q0 + cc, r0 = d0 + 8 * g;
+        if (col >= p.n_cols || r0 >= p.x_rows) continue;
+        const uint32_t req = p.col_tags[2 * col], tag = p.col_tags[2 * col + 1];
+        const uint4 fo = philox(grp0 + g, tag, req, ctr3, p.seed_own);
+        const uint4 fp = philox(grp0 + g, tag, req, ctr3, p.seed_prev);
+        const uint4 acc = *reinterpret_cast<const uint4*>(zs + cc * TM + 8 * g);
+        // per 16-bit half: z = acc + (F_own - F_prev)  (mod 2^16)
+        auto add2 = [](uint32_t a, uint32_t o, uint32_t f) {
+          const uint32_t lo = (a + o - f) & 0xFFFFu;
+          const uint32_t hi = ((a >> 16) + (o >> 16) - (f >> 16)) << 16;
+          return lo | hi;
+        };
+        const uint4 v = make_uint4(add2(acc.x, fo.x, fp.x), add2(acc.y, fo.y, fp.y), add2(acc.z, fo.z, fp.z),
+                                   add2(acc.w, fo.w, fp.w));
+        uint16_t* dst = p.z + static_cast<uint64_t>(col) * p.ldz + r0;
+        if (r0 + 8 <= p.x_rows) {
+          *reinterpret_cast<uint4*>(dst) = v;
+        } else {
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+          for (uint32_t e = 0; e < p.x_rows - r0; ++e) dst[e] = static_cast<uint16_t>(w[e >> 1] >> (16 * (e & 1)));
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 2-D bf16 tensor [rows][cols], box 32 elements (64 bytes) x box_rows, 64-byte swizzle, zero fill
+// outside the tensor (ragged row tails and query rows past n_pad).
+int make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return IPC_ECUDA;
+  }
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {KB, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (bf16) failed with CUresult " + std::to_string(static_cast<int>(r)));
+    return IPC_ECUDA;
+  }
+  return IPC_OK;
+}
+
+}  // namespace
+
+int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+                 const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+                 uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                 cudaStream_t stream) {
+  CUtensorMap m[6];
+  int rc;
+  if ((rc = make_map_bf16(&m[0], b_lo, 2ull * l, n_pad, TN)) || (rc = make_map_bf16(&m[1], b_hi, 2ull * l, n_pad, TN)) ||
+      (rc = make_map_bf16(&m[2], x_lo[0], l, x_rows, TM)) || (rc = make_map_bf16(&m[3], x_hi[0], l, x_rows, TM)) ||
+      (rc = make_map_bf16(&m[4], x_lo[1], l, x_rows, TM)) || (rc = make_map_bf16(&m[5], x_hi[1], l, x_rows, TM)))
+    return rc;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  IPC_CUDA_TRY(attr);
+  TcParams p;
+  p.n_cols = n_cols;
+  p.x_rows = static_cast<uint32_t>(x_rows);
+  p.kb_total = 2 * l / KB;
+  p.kb_half = l / KB;
+  p.col_tags = col_tags;
+  p.seed_own = seed_own;
+  p.seed_prev = seed_prev;
+  p.vec = vec;
+  p.z = z;
+  p.ldz = ldz;
+  p.row0 = row0;
+  p.status = status_ptr();
+  const dim3 grid((n_cols + TN - 1) / TN, static_cast<unsigned>((x_rows + TM - 1) / TM));
+  gemm_tc_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+}  // namespace ipc

@@ -49,6 +49,38 @@ __global__ void encode_share_kernel(const uint64_t* __restrict__ code_bits, cons
   }
 }
 
+// bf16 bit pattern of a limb (an integer in [-128, 127]: exact in bf16, so the high half of the
+// fp32 value is the bf16 value).
+__device__ __forceinline__ uint16_t bf16_of(int8_t v) {
+  return static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);
+}
+
+// A1 for the bf16 tensor-core path: 8 elements per thread, limbs written as bf16.
+__global__ void split_limbs_bf16_kernel(const uint16_t* __restrict__ x, size_t count, uint16_t* __restrict__ lo,
+                                        uint16_t* __restrict__ hi) {
+  const size_t i8 = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) * 8;
+  if (i8 >= count) return;
+  const size_t n = count - i8 < 8 ? count - i8 : 8;
+  uint16_t l8[8], h8[8];
+  for (size_t e = 0; e < n; ++e) {
+    int8_t a, b;
+    limbs(x[i8 + e], a, b);
+    l8[e] = bf16_of(a);
+    h8[e] = bf16_of(b);
+  }
+  if (n == 8) {
+    *reinterpret_cast<uint4*>(lo + i8) = make_uint4(l8[0] | (uint32_t(l8[1]) << 16), l8[2] | (uint32_t(l8[3]) << 16),
+                                                    l8[4] | (uint32_t(l8[5]) << 16), l8[6] | (uint32_t(l8[7]) << 16));
+    *reinterpret_cast<uint4*>(hi + i8) = make_uint4(h8[0] | (uint32_t(h8[1]) << 16), h8[2] | (uint32_t(h8[3]) << 16),
+                                                    h8[4] | (uint32_t(h8[5]) << 16), h8[6] | (uint32_t(h8[7]) << 16));
+  } else {
+    for (size_t e = 0; e < n; ++e) {
+      lo[i8 + e] = l8[e];
+      hi[i8 + e] = h8[e];
+    }
+  }
+}
+
 // A1: 8 elements per thread.
 __global__ void split_limbs_kernel(const uint16_t* __restrict__ x, size_t count, int8_t* __restrict__ lo,
                                    int8_t* __restrict__ hi) {
@@ -72,9 +104,11 @@ __global__ void split_limbs_kernel(const uint16_t* __restrict__ x, size_t count,
   }
 }
 
-// A2: one thread per output element of B_i (row n, position k of 2l).
+// A2: one thread per output element of B_i (row n, position k of 2l). Limb type T: int8_t, or
+// uint16_t for the bf16 bit patterns of the same limbs.
+template <typename T>
 __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint32_t Q, ipc_geom g, uint32_t party,
-                                  int8_t* __restrict__ b_lo, int8_t* __restrict__ b_hi, uint32_t n_pad) {
+                                  T* __restrict__ b_lo, T* __restrict__ b_hi, uint32_t n_pad) {
   const uint32_t l = g.rows * g.cols * g.cell;
   const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   const uint64_t total = static_cast<uint64_t>(n_pad) * 2 * l;
@@ -101,8 +135,13 @@ __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint32_t Q, ip
   }
   int8_t a, b;
   limbs(val & 0xFFFFu, a, b);
-  b_lo[tid] = a;
-  b_hi[tid] = b;
+  if constexpr (sizeof(T) == 1) {
+    b_lo[tid] = a;
+    b_hi[tid] = b;
+  } else {
+    b_lo[tid] = bf16_of(a);
+    b_hi[tid] = bf16_of(b);
+  }
 }
 
 bool geom_ok(const ipc_geom* g) {
@@ -145,17 +184,44 @@ extern "C" int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8
   return IPC_OK;
 }
 
-extern "C" int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
-                              int8_t* b_hi, uint32_t n_pad, void* stream) {
+namespace {
+template <typename T>
+int prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, T* b_lo, T* b_hi, uint32_t n_pad,
+               void* stream, const char* who) {
   if (!geom_ok(g) || party > 2 || !y || !b_lo || !b_hi || Q == 0 || static_cast<uint64_t>(Q) * g->R > n_pad) {
-    set_error("ipc_prep_query: invalid geometry, party, or n_pad < Q*R");
+    set_error(std::string(who) + ": invalid geometry, party, or n_pad < Q*R");
     return IPC_EINVAL;
   }
   const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
   const uint64_t total = static_cast<uint64_t>(n_pad) * 2 * l;
   const uint32_t bs = 256;
-  prep_query_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(y, Q, *g, party, b_lo,
-                                                                                               b_hi, n_pad);
+  prep_query_kernel<T><<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(y, Q, *g, party,
+                                                                                                  b_lo, b_hi, n_pad);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+}  // namespace
+
+extern "C" int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
+                              int8_t* b_hi, uint32_t n_pad, void* stream) {
+  return prep_query(y, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query");
+}
+
+extern "C" int ipc_prep_query_bf16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
+                                   uint16_t* b_hi, uint32_t n_pad, void* stream) {
+  return prep_query(y, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query_bf16");
+}
+
+extern "C" int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* lo, uint16_t* hi, void* stream) {
+  if (count == 0 || !x || !lo || !hi || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(lo) & 15) ||
+      (reinterpret_cast<uintptr_t>(hi) & 15)) {
+    set_error("ipc_split_limbs_bf16: count > 0, x, lo and hi 16-byte aligned");
+    return IPC_EINVAL;
+  }
+  const size_t threads = (count + 7) / 8;
+  const uint32_t bs = 256;
+  split_limbs_bf16_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(x, count, lo,
+                                                                                                      hi);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }

@@ -59,14 +59,16 @@ def test_plain_vs_precision_full_size(c2):
     rid8, sh8, dist = _run(w, "i8mma", True, c2["qc"], c2["qm"])
     rid32, sh32, _ = _run(w, "i32", False, c2["qc"], c2["qm"])
     ridx, shx, distx = _run(w, "i8mix", True, c2["qc"], c2["qm"])
-    for sh in (sh8, sh32, shx):
+    ridt, sht, distt = _run(w, "tc", True, c2["qc"], c2["qm"])
+    for sh in (sh8, sh32, shx, sht):
         assert (oracle.reconstruct_bits(sh) == c2["match"]).all()
     assert c2["match"].sum() == w.planted
-    # same request id and seeds: the three paths must agree share for share
-    assert rid8 == rid32 == ridx
-    assert (sh8 == sh32).all() and (sh8 == shx).all()
+    # same request id and seeds: the four paths must agree share for share
+    assert rid8 == rid32 == ridx == ridt
+    assert (sh8 == sh32).all() and (sh8 == shx).all() and (sh8 == sht).all()
     for k in dist:
-        assert (dist[k][0] == distx[k][0]).all() and (dist[k][1] == distx[k][1]).all()
+        for other in (distx, distt):
+            assert (dist[k][0] == other[k][0]).all() and (dist[k][1] == other[k][1]).all()
     for (q, rho), (dot, ml) in dist.items():
         assert (ml == c2["ml"][q, rho]).all()
         assert (dot == c2["ml"][q, rho] - 2 * c2["hd"][q, rho]).all()
@@ -85,7 +87,7 @@ def test_tiny_workload_share_for_share():
     dbc, dbm = oracle.encode_share(dc, dm, w.l, w.db_share_seed, 0)
     qsc, qsm = oracle.encode_share(qc, qm, w.l, w.q_share_seed, 1)
     match, ml, hd = oracle.plain_match(g, qc, qm, dc, dm, distances=True)
-    for path in ("i8mix", "i8mma", "i32"):
+    for path in ("i8mix", "i8mma", "i32", "tc"):
         ctx = make_ctx(w, path=path, keep=True)
         try:
             load_workload(ctx, w)

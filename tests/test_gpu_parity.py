@@ -52,6 +52,23 @@ def test_split_limbs_exhaustive(torch):
     assert lo_.min() >= -128 and lo_.max() <= 127 and hi_.min() >= -128 and hi_.max() <= 127
 
 
+def test_split_limbs_bf16_exhaustive(torch):
+    """The bf16 limbs of the tensor-core path are the int8 limbs, exactly, for all 65536 values."""
+    ipc = lib()
+    x = torch.arange(65536, dtype=torch.int32).to(torch.int16).cuda()
+    lo8 = torch.empty(65536, dtype=torch.int8, device="cuda")
+    hi8 = torch.empty(65536, dtype=torch.int8, device="cuda")
+    ipc.ipc_split_limbs(x, 65536, lo8, hi8)
+    lo = torch.empty(65536, dtype=torch.int16, device="cuda")
+    hi = torch.empty(65536, dtype=torch.int16, device="cuda")
+    ipc.ipc_split_limbs_bf16(x, 65536, lo, hi)
+    lof = lo.view(torch.bfloat16).float().cpu().numpy()
+    hif = hi.view(torch.bfloat16).float().cpu().numpy()
+    assert (lof == lo8.cpu().numpy().astype(np.float32)).all()
+    assert (hif == hi8.cpu().numpy().astype(np.float32)).all()
+    assert ((256 * hif.astype(np.int64) + lof.astype(np.int64)) & 0xFFFF == np.arange(65536)).all()
+
+
 def test_encode_share_matches_oracle(small):
     code, mask = encode_gpu(small["dc"], small["dm"], L, small["w"].db_share_seed, 0)
     assert (u16(code) == small["dbc"]).all()
@@ -94,15 +111,16 @@ def test_prep_query_is_rotated_aby3_operand(small, torch):
         assert (rebuilt[Q * R:] == 0).all()
 
 
-def _planes(torch, shares):
-    """[3][n][l] uint16 numpy -> per component (lo, hi) int8 device planes via the C ABI."""
+def _planes(torch, shares, bf16=False):
+    """[3][n][l] uint16 numpy -> per component (lo, hi) device limb planes via the C ABI
+    (int8, or bf16 bit patterns for the tensor-core path)."""
     ipc = lib()
     out = []
     for j in range(3):
         x = torch.from_numpy(shares[j].view(np.int16).copy()).cuda()
-        lo = torch.empty(x.shape, dtype=torch.int8, device="cuda")
-        hi = torch.empty(x.shape, dtype=torch.int8, device="cuda")
-        ipc.ipc_split_limbs(x, x.numel(), lo, hi)
+        lo = torch.empty(x.shape, dtype=torch.int16 if bf16 else torch.int8, device="cuda")
+        hi = torch.empty(x.shape, dtype=torch.int16 if bf16 else torch.int8, device="cuda")
+        (ipc.ipc_split_limbs_bf16 if bf16 else ipc.ipc_split_limbs)(x, x.numel(), lo, hi)
         out.append((lo, hi))
     return out
 
@@ -117,24 +135,30 @@ def _gemm_all(torch, small, path):
     tags = torch.from_numpy(tags_for(REQ, Q, R).view(np.int32)).cuda()
     ldz = 784
     out = []
+    tc = path == "tc"
     for vec, (db, qs) in enumerate(((small["dbc"], small["qsc"]), (small["dbm"], small["qsm"]))):
-        planes = _planes(torch, db)
+        planes = _planes(torch, db, bf16=tc)
         y = torch.from_numpy(qs.view(np.int16).copy()).cuda()
         z = torch.zeros((3, N, ldz), dtype=torch.int16, device="cuda")
         for i in range(3):
             prev = (i + 2) % 3
-            blo = torch.empty((n_pad, 2 * L), dtype=torch.int8, device="cuda")
-            bhi = torch.empty((n_pad, 2 * L), dtype=torch.int8, device="cuda")
-            ipc.ipc_prep_query(y, Q, g, i, blo, bhi, n_pad)
-            ipc.ipc_ring_gemm(path, [planes[i][0], planes[prev][0]], [planes[i][1], planes[prev][1]], s, blo, bhi,
-                              N, n_pad, L, tags, w.prf_seeds[i], w.prf_seeds[prev], vec, z[i], ldz, 0)
+            blo = torch.empty((n_pad, 2 * L), dtype=torch.int16 if tc else torch.int8, device="cuda")
+            bhi = torch.empty((n_pad, 2 * L), dtype=torch.int16 if tc else torch.int8, device="cuda")
+            (ipc.ipc_prep_query_bf16 if tc else ipc.ipc_prep_query)(y, Q, g, i, blo, bhi, n_pad)
+            xl, xh = [planes[i][0], planes[prev][0]], [planes[i][1], planes[prev][1]]
+            if tc:
+                ipc.ipc_ring_gemm_tc(xl, xh, s, blo, bhi, N, n_pad, L, tags, w.prf_seeds[i], w.prf_seeds[prev], vec,
+                                     z[i], ldz, 0)
+            else:
+                ipc.ipc_ring_gemm(path, xl, xh, s, blo, bhi, N, n_pad, L, tags, w.prf_seeds[i], w.prf_seeds[prev],
+                                  vec, z[i], ldz, 0)
         torch.cuda.synchronize()
         ipc.ipc_status()
         out.append(u16(z)[:, :, :s])
     return out
 
 
-@pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32"])
+@pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32", "tc"])
 def test_ring_gemm_matches_oracle_shares(small, torch, path):
     zc, zm = _gemm_all(torch, small, path)
     assert (zc == small["ref"]["z_code"]).all()
@@ -171,7 +195,7 @@ def test_compare_and_or_tree_match_oracle_shares(small, torch):
     assert (oracle.reconstruct_bits(small["ref"]["bits"]) == small["match"]).all()
 
 
-@pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32"])
+@pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32", "tc"])
 def test_context_end_to_end_small(small, torch, path):
     ipc = lib()
     w = small["w"]
@@ -209,7 +233,7 @@ def test_context_multi_chunk(torch):
     dbc, dbm = oracle.encode_share(dc, dm, L, w.db_share_seed, 0)
     qsc, qsm = oracle.encode_share(qc, qm, L, w.q_share_seed, 1)
     match, _, _ = oracle.plain_match(oracle.Geom(16, 200, 4, -1, 3), qc, qm, dc, dm)
-    for path in ("i8mma", "i8mix", "i32"):
+    for path in ("i8mma", "i8mix", "i32", "tc"):
         ctx = make_ctx(w, path=path, chunk_rows=1024)
         try:
             load_workload(ctx, w, chunk=700)
@@ -240,13 +264,20 @@ def test_gemm_exact_at_max_length_and_extreme_limbs(torch):
     y = torch.full((3, Q, Lm), 0x7F80, dtype=torch.int32).to(torch.int16).cuda()
     y[2] = 0  # party 0's operand is [y_0 + y_2 | y_0] = [0x7F80 | 0x7F80]: C reaches 2l * 2 * 128^2 = 2^30
     tags = torch.from_numpy(tags_for(1, Q, R).view(np.int32)).cuda()
+    lo16 = torch.empty((s, Lm), dtype=torch.int16, device="cuda")
+    hi16 = torch.empty((s, Lm), dtype=torch.int16, device="cuda")
+    ipc.ipc_split_limbs_bf16(x, x.numel(), lo16, hi16)
     res = {}
-    for path in ("i8mma", "i8mix", "i32"):
-        blo = torch.empty((128, 2 * Lm), dtype=torch.int8, device="cuda")
-        bhi = torch.empty((128, 2 * Lm), dtype=torch.int8, device="cuda")
-        ipc.ipc_prep_query(y, Q, g, 0, blo, bhi, 128)
+    for path in ("i8mma", "i8mix", "i32", "tc"):
+        tc = path == "tc"
+        blo = torch.empty((128, 2 * Lm), dtype=torch.int16 if tc else torch.int8, device="cuda")
+        bhi = torch.empty((128, 2 * Lm), dtype=torch.int16 if tc else torch.int8, device="cuda")
+        (ipc.ipc_prep_query_bf16 if tc else ipc.ipc_prep_query)(y, Q, g, 0, blo, bhi, 128)
         z = torch.zeros((Q * R, 136), dtype=torch.int16, device="cuda")
-        ipc.ipc_ring_gemm(path, [lo, lo], [hi, hi], s, blo, bhi, Q * R, 128, Lm, tags, 0, 0, 0, z, 136, 0)
+        if tc:
+            ipc.ipc_ring_gemm_tc([lo16, lo16], [hi16, hi16], s, blo, bhi, Q * R, 128, Lm, tags, 0, 0, 0, z, 136, 0)
+        else:
+            ipc.ipc_ring_gemm(path, [lo, lo], [hi, hi], s, blo, bhi, Q * R, 128, Lm, tags, 0, 0, 0, z, 136, 0)
         torch.cuda.synchronize()
         ipc.ipc_status()
         res[path] = u16(z)[:, :s]
@@ -331,3 +362,32 @@ def test_gemm_variants_and_tile_lists_match_int32(torch, variant):
             assert (z2[cols, :rows] == refc[cols, :rows]).all(), t
         else:
             assert (z2[cols] == 77).all(), t
+
+
+def _bf16(torch, t):
+    """int8 limb tensor -> the bf16 bit patterns of the same integers (test-side conversion)."""
+    return t.float().to(torch.bfloat16).view(torch.int16).contiguous()
+
+
+@pytest.mark.parametrize("rows,N,row0", [(1000, 300, 8), (128, 256, 0), (4097, 31, 65536)])
+def test_tc_gemm_matches_int32_on_random_limbs(torch, rows, N, row0):
+    """The tcgen05 path equals the int32 path on random full-range limbs: ragged row tiles, one
+    and two 256-column tiles (the second ragged), a row offset inside and past the first chunk."""
+    ipc = lib()
+    n_pad = (N + 127) // 128 * 128
+    g = torch.Generator(device="cpu").manual_seed(rows + N)
+    planes = [torch.randint(-128, 128, (rows, L), dtype=torch.int8, generator=g).cuda() for _ in range(4)]
+    blo = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    bhi = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    tags = torch.from_numpy(tags_for(3, (N + 30) // 31, 31).view(np.int32)).cuda()
+    ldz = (rows + 7) // 8 * 8
+    ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, ref, ldz, row0)
+    z = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
+    p16 = [_bf16(torch, t) for t in planes]
+    ipc.ipc_ring_gemm_tc(p16[0:2], p16[2:4], rows, _bf16(torch, blo), _bf16(torch, bhi), N, n_pad, L, tags, 5, 6, 1,
+                         z, ldz, row0)
+    torch.cuda.synchronize()
+    ipc.ipc_status()
+    assert (z.cpu()[:, :rows] == ref.cpu()[:, :rows]).all()
+    assert (z.cpu()[:, rows:] == 77).all()
