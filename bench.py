@@ -6,10 +6,12 @@ lift + threshold + MSB + in-block OR (A4-A8) per chunk, the rest of the OR tree 
 copy of the bit components. Workload (default): 100,000 database rows x 32 queries x 31
 rotations, 12,800-bit codes, synthetic (seeded), database shares resident on the device.
 
-Prints one JSON line. `value` is comparisons/s of the int8 tensor-core path with the query
-shares already on the device, timed with CUDA events on the library's control stream;
-`e2e` is the same through host (pinned) buffers with the copies inside the timed region;
-`int32_path` is the plain CUDA-core path on the same workload. --impl reference times the
+Prints one JSON line. `value` is comparisons/s of the tcgen05 path (the int8 limbs carried
+exactly as bf16, fp32 accumulators in tensor memory) with the query shares already on the
+device, timed with CUDA events on the library's control stream; `e2e` is the same through
+host (pinned) buffers with the copies inside the timed region; `int8_mix_path`,
+`int8_tensor_only_path` (mma.sync s8 with and without dp4a) and `int32_path` (plain CUDA-core
+ring GEMM) run the same workload, and each reports whether its bits equal the headline's. --impl reference times the
 CPU oracle (the 3-party simulation of Alg. 3) on bounded samples of the same workload.
 """
 from __future__ import annotations
@@ -225,7 +227,8 @@ def run_ours(args, w):
     dev = torch.cuda.current_device()
 
     # ---- setup (untimed): resident database, query shares, contexts ----
-    ctxs = {"i8mix": make_ctx(w, path="i8mix", max_queries=w.Q), "i8mma": make_ctx(w, path="i8mma", max_queries=w.Q)}
+    # headline: the tcgen05 path; beside it the two int8 mma.sync paths and the int32 path
+    ctxs = {p: make_ctx(w, path=p, max_queries=w.Q) for p in ("tc", "i8mix", "i8mma")}
     if not args.no_i32:
         ctxs["i32"] = make_ctx(w, path="i32", max_queries=w.Q)
     for c in ctxs.values():
@@ -262,11 +265,11 @@ def run_ours(args, w):
             ms = float(t.item())
         return ms / k, wall / k, bits.copy()
 
-    main = ctxs["i8mix"]
+    main = ctxs["tc"]
     run_steps(main, args.warmup, False)
     clocks = Clocks(dev)
     clocks.start()
-    ms_i8, wall_i8, bits = run_steps(main, args.steps, False)
+    ms_main, wall_main, bits = run_steps(main, args.steps, False)
     clk = clocks.stop()
     run_steps(main, 1, True)
     ms_e2e, wall_e2e, bits_e2e = run_steps(main, args.steps, True)
@@ -277,50 +280,66 @@ def run_ours(args, w):
         return {"value": w.comparisons * world / (ms * 1e-3), "ms_per_step": ms,
                 "bits_equal_to_headline_path": bool((b == bits).all())}
 
-    out_tc = other("i8mma")
+    out_mix = other("i8mix")
+    out_mma = other("i8mma")
     out_i32 = other("i32") if "i32" in ctxs else None
 
-    # ---- dominant kernel alone: one i8 GEMM launch over a 65536-row chunk ----
+    # ---- each ring-GEMM kernel alone: one launch over a 65536-row chunk, all query columns ----
     l, N = w.l, w.Q * w.R
     n_pad = (N + 127) // 128 * 128
     rows = min(65536, w.s)
-    g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
     planes = [torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda") for _ in range(4)]
     blo = torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")
     bhi = torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")
+    bf = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in planes + [blo, bhi]]
     tags = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
     z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
     st = torch.cuda.current_stream()
 
+    def launch(path):
+        if path == "tc":
+            ipc.ipc_ring_gemm_tc(bf[0:2], bf[2:4], rows, bf[4], bf[5], N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+        else:
+            ipc.ipc_ring_gemm(path, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+
     def gemm_time(path, reps):
         for _ in range(2):
-            ipc.ipc_ring_gemm(path, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+            launch(path)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         for _ in range(reps):
-            ipc.ipc_ring_gemm(path, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+            launch(path)
         e1.record(st)
         e1.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    t_mix = gemm_time("i8mix", 5)
-    t_i8 = gemm_time("i8mma", 5)
-    t_i32 = gemm_time("i32", 3) if not args.no_i32 else None
-    ops = 2.0 * 3 * N * rows * 2 * l          # 3 int8 products per ring multiply-add, 2 ops each
+    t_tc = gemm_time("tc", 10)
+    t_mix = gemm_time("i8mix", 3)
+    t_i8 = gemm_time("i8mma", 3)
+    t_i32 = gemm_time("i32", 2) if not args.no_i32 else None
+    ipc.ipc_status()
+    ops = 2.0 * 3 * N * rows * 2 * l          # 3 limb products per ring multiply-add, 2 ops each
+    peaks = measured_peaks()
+    bf16_burst, bf16_sust = peaks.get("bf16_tflops"), peaks.get("bf16_tflops_sustained")
     peak_mma = ipc.ipc_measure_peak(0)
     peak_imad = ipc.ipc_measure_peak(1)
     peak_dp4a = ipc.ipc_measure_peak(2)
-    peak_int8 = peak_mma + peak_dp4a
-    achieved = ops / (t_mix * 1e-3) / 1e12
-    traffic = ncu_traffic("gemm_i8_kernel", os.path.join(ROOT, "paper_2405_04463_gb300", "csrc", "gemm_i8.cu"))
-    roofline = {"bound": "tensor", "kernel": "gemm_i8_kernel<1> (mma.sync s8 + dp4a)", "achieved": achieved,
-                "peak": peak_int8, "unit": "TOP/s", "frac": achieved / peak_int8, "traffic": traffic,
-                "peak_source": "measured live: register-only mma.sync.m16n8k32 s8 loop + dp4a loop "
-                               "(ipc_measure_peak); MEASURED_PEAKS.json has no int8 figure",
-                "peak_mma_s8": peak_mma, "peak_dp4a": peak_dp4a, "launch_ms": t_mix, "ops_per_launch": ops,
-                "tensor_only_kernel": {"kernel": "gemm_i8_kernel<0>", "launch_ms": t_i8,
-                                       "achieved": ops / (t_i8 * 1e-3) / 1e12,
-                                       "frac_of_mma_peak": ops / (t_i8 * 1e-3) / 1e12 / peak_mma}}
+    achieved = ops / (t_tc * 1e-3) / 1e12
+    traffic = ncu_traffic("gemm_tc_kernel", os.path.join(ROOT, "paper_2405_04463_gb300", "csrc", "gemm_tc.cu"))
+    roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, bf16-carried int8 limbs)",
+                "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
+                "frac": achieved / bf16_burst if bf16_burst else None, "traffic": traffic,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the kernel is timed alone, back to back)",
+                "launch_ms": t_tc, "flops_per_launch": ops,
+                "int8_kernels": {
+                    "gemm_i8_kernel<1> (mma.sync s8 + dp4a)": {
+                        "launch_ms": t_mix, "achieved_tops": ops / (t_mix * 1e-3) / 1e12,
+                        "frac_of_measured_mma_plus_dp4a": ops / (t_mix * 1e-3) / 1e12 / (peak_mma + peak_dp4a)},
+                    "gemm_i8_kernel<0> (mma.sync s8)": {
+                        "launch_ms": t_i8, "achieved_tops": ops / (t_i8 * 1e-3) / 1e12,
+                        "frac_of_measured_mma": ops / (t_i8 * 1e-3) / 1e12 / peak_mma},
+                    "measured_int8_peaks_tops": {"mma_sync_s8": peak_mma, "dp4a": peak_dp4a,
+                                                 "source": "register-only loops (ipc_measure_peak)"}}}
     i32_kernel = None
     if t_i32:
         imads = 1.0 * N * rows * 2 * l
@@ -340,21 +359,26 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
     if rank != 0:
         return
-    value = w.comparisons * world / (ms_i8 * 1e-3)
+    value = w.comparisons * world / (ms_main * 1e-3)
     h2d = 2 * 3 * w.Q * w.l * 2
+    flops_per_cmp = 921600.0   # 3 parties x 2 vectors x 2 l x 3 limb products x 2 ops
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_i8, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": ms_main, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": w.name, "db_rows": w.s, "queries": w.Q, "rotations": w.R, "code_bits": w.l,
-                   "planted": w.planted, "path": "i8mix (TMA-fed tiles split between mma.sync s8 and dp4a)",
+                   "planted": w.planted,
+                   "path": "tc: int8 limbs as exact bf16 on tcgen05.mma, fp32 TMEM accumulators re-based every "
+                           "64 k inside [2^23, 2^24) (bit-exact; integer results)",
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: resident shares 12 B x rows x 12800 = "
-                         f"{12 * w.s * w.l / 1e9:.1f} GB"},
-        "int8_peak_frac_step": value * 921600 / (peak_int8 * 1e12),
-        "int8_tensor_only_path": out_tc,
+                   "l2": "inputs larger than L2: resident limb planes 24 B x rows x 12800 = "
+                         f"{24 * w.s * w.l / 1e9:.1f} GB"},
+        "tensor_peak_frac_step": value * flops_per_cmp / (bf16_sust * 1e12) if bf16_sust else None,
+        "int8_mix_path": out_mix,
+        "int8_tensor_only_path": out_mma,
         "int32_path": out_i32,
-        "ratio_int8_vs_int32": (value / out_i32["value"]) if out_i32 else None,
+        "ratio_vs_int32": (value / out_i32["value"]) if out_i32 else None,
+        "ratio_int8_mix_vs_int32": (out_mix["value"] / out_i32["value"]) if out_i32 else None,
         "roofline": roofline,
         "int32_kernel": i32_kernel,
         "cpu_baseline": cpu,
@@ -364,7 +388,7 @@ def run_ours(args, w):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "match_bits": int(bits.sum()),
-        "measured_peaks": {k: measured_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+        "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
     print(json.dumps(res), flush=True)
 
