@@ -19,9 +19,9 @@
 //                  query lo/hi 256 x 32, 64-byte swizzle) into a 4-stage ring.
 //   warp 1 lane 0  MMA issuer: per chunk of two k-blocks, the C products (8 MMAs of 128x256x16)
 //                  then the L products (4 MMAs), committing C-full, stage-empty and L-full.
-//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 128 columns; after
-//                  C-full it reads C, adds C << 8 to its int32 running sums and stores M back, then
-//                  the same for L. C is drained while the L products run and L while the next
+//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 128 columns, their
+//                  running sums kept mod 2^16 two to a register; after C-full it reads C, adds
+//                  C << 8 to the sums and stores M back, then the same for L. C is drained while the L products run and L while the next
 //                  chunk's C products run, so the tensor pipe does not wait for the drain.
 // TMEM: L in columns [0, 256), C in [256, 512).
 // Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
@@ -149,12 +149,17 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 8 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
 }
 
 // Stores v into 32 consecutive TMEM columns of this thread's lane.
@@ -166,9 +171,28 @@ __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
       : "memory");
 }
 
-// a += d, hidden from the compiler so that it keeps one running TMEM address instead of
-// materialising every offset of an unrolled loop in its own register
-__device__ __forceinline__ void bump(uint32_t& a, uint32_t d) { asm volatile("add.u32 %0, %0, %1;" : "+r"(a) : "r"(d)); }
+// Two 16-bit lanes added independently (mod 2^16 each).
+__device__ __forceinline__ uint32_t add16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("add.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Low 16 bits of x (lane 0) and of y (lane 1): the L contributions of two columns.
+__device__ __forceinline__ uint32_t pack_lo16(uint32_t x, uint32_t y) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(d) : "r"(x), "r"(y));
+  return d;
+}
+
+// (x << 8) mod 2^16 and (y << 8) mod 2^16 in lanes 0 and 1: the 256 C contributions of two
+// columns. Byte 0 of each goes to bit 8 of its lane; the zero bytes are the replicated sign of
+// byte 3 of x, which is 0x4B for every accumulator value in [2^23, 2^24).
+__device__ __forceinline__ uint32_t pack_c16(uint32_t x, uint32_t y) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, 0x4B0B;" : "=r"(d) : "r"(x), "r"(y));
+  return d;
+}
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -289,11 +313,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ----------------------------------- drain ----------------------------------
+    // z2[k] holds the running sums (mod 2^16) of columns 2k (low half) and 2k + 1 (high half).
     const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - 2) >> 2;
     const uint32_t tL = tmem + ((32u * q) << 16) + 128u * h, tC = tL + TMEM_C;
-    uint32_t z[128];
+    uint32_t z2[64];
 #pragma unroll
-    for (int j = 0; j < 128; ++j) z[j] = 0;
+    for (int k = 0; k < 64; ++k) z2[k] = 0;
 #pragma unroll
     for (uint32_t g = 0; g < 4; ++g) {
       tmem_fill32(tL + 32 * g, MAGIC);
@@ -310,21 +335,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t par = c & 1u;
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(c_full, par, p.status, abort))) break;
       fence_after();
-{
-        uint32_t ta = tC, tf = tC;
 #pragma unroll
-        for (uint32_t g = 0; g < 16; ++g) {
-          uint32_t r[8];
-          tmem_ld8(ta, r);
-          bump(ta, 8);
-          tmem_wait_ld();
+      for (uint32_t g = 0; g < 4; ++g) {
+        uint32_t r[32];
+        tmem_ld32(tC + 32 * g, r);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) z[8 * g + j] += r[j] << 8;
-          if ((g & 3) == 3) {
-            tmem_fill32(tf, MAGIC);
-            bump(tf, 32);
-          }
-        }
+        for (int k = 0; k < 16; ++k) z2[16 * g + k] = add16x2(z2[16 * g + k], pack_c16(r[2 * k], r[2 * k + 1]));
+        tmem_fill32(tC + 32 * g, MAGIC);
       }
       tmem_wait_st();
       fence_before();
@@ -332,21 +350,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (lane == 0) mbar_arrive(c_empty);
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(l_full, par, p.status, abort))) break;
       fence_after();
-{
-        uint32_t ta = tL, tf = tL;
 #pragma unroll
-        for (uint32_t g = 0; g < 16; ++g) {
-          uint32_t r[8];
-          tmem_ld8(ta, r);
-          bump(ta, 8);
-          tmem_wait_ld();
+      for (uint32_t g = 0; g < 4; ++g) {
+        uint32_t r[32];
+        tmem_ld32(tL + 32 * g, r);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) z[8 * g + j] += r[j];
-          if ((g & 3) == 3) {
-            tmem_fill32(tf, MAGIC);
-            bump(tf, 32);
-          }
-        }
+        for (int k = 0; k < 16; ++k) z2[16 * g + k] = add16x2(z2[16 * g + k], pack_lo16(r[2 * k], r[2 * k + 1]));
+        tmem_fill32(tL + 32 * g, MAGIC);
       }
       tmem_wait_st();
       fence_before();
@@ -362,7 +373,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint16_t* zs = reinterpret_cast<uint16_t*>(smem);  // [TN][TM]
       const uint32_t row = 32 * q + lane;
 #pragma unroll
-      for (int j = 0; j < 128; ++j) zs[(128 * h + j) * TM + row] = static_cast<uint16_t>(z[j]);
+      for (int k = 0; k < 64; ++k) {
+        zs[(128 * h + 2 * k) * TM + row] = static_cast<uint16_t>(z2[k]);
+        zs[(128 * h + 2 * k + 1) * TM + row] = static_cast<uint16_t>(z2[k] >> 16);
+      }
       named_sync(1, DRAIN_THREADS);
       const uint32_t dt = threadIdx.x - 64;
       const uint32_t grp0 = static_cast<uint32_t>((p.row0 + d0) >> 3);
