@@ -6,19 +6,20 @@
 // sm_103a has no integer tcgen05 kind, but the arithmetic stays exact on the bf16 kind:
 //   * every limb is an integer in [-128, 127], exactly a bf16 value;
 //   * every product is an integer with |p| <= 2^14, exact in fp32;
-//   * an accumulator starts each chunk of 64 k at M = 1.5 * 2^23 and receives at most 128 products
-//     (C: two per k), so every partial sum is an integer within M +- 2^21, inside [2^23, 2^24),
-//     where consecutive fp32 values are 1 apart: whatever the order or rounding of the additions,
-//     each one is exact;
-//   * in that binade the fp32 bit pattern of M + v is bits(M) + v, and bits(M) = 0x4B400000 is
+//   * an accumulator starts each chunk of 128 k at M = 1.5 * 2^23 and receives at most 256
+//     products (C: two per k), so every partial sum, in any order or grouping, is an integer
+//     within M +- 2^22, i.e. in [2^23, 2^24], where consecutive fp32 values are 1 apart (2^24
+//     included): each addition is exact whatever its rounding;
+//   * on [2^23, 2^24] the fp32 bit pattern of M + v is bits(M) + v, and bits(M) = 0x4B400000 is
 //     0 mod 2^16, so the raw bits of the two accumulators, added as integers (L + (C << 8)) over
 //     all chunks, give z - r mod 2^16 with no conversion instruction.
 //
 // Pipeline (one CTA per 128 database rows x 256 query columns, 10 warps):
 //   warp 0 lane 0  TMA producer: per k-block of 32 elements, four tiles (database lo/hi 128 x 32,
 //                  query lo/hi 256 x 32, 64-byte swizzle) into a 4-stage ring.
-//   warp 1 lane 0  MMA issuer: per chunk of two k-blocks, the C products (8 MMAs of 128x256x16)
-//                  then the L products (4 MMAs), committing C-full, stage-empty and L-full.
+//   warp 1 lane 0  MMA issuer: per chunk of four k-blocks, the C products (2 MMAs of 128x256x16
+//                  per 16 k) with the L products (1 MMA per 16 k) one k-block behind, committing
+//                  C-full after the last C k-block, stage-empty after each L k-block and L-full.
 //   warps 2-9      drain: each thread owns one TMEM lane (database row) and 128 columns, their
 //                  running sums kept mod 2^16 two to a register; after C-full it reads C, adds
 //                  C << 8 to the sums and stores M back, then the same for L. C is drained while the L products run and L while the next
@@ -41,7 +42,8 @@ constexpr int TM = 128;          // database rows per tile (MMA M = TMEM lanes)
 constexpr int TN = 256;          // query columns per tile (MMA N)
 constexpr int KB = 32;           // bf16 elements of K per stage: one 64-byte swizzled row
 constexpr int STAGES = 4;
-constexpr int KB_PER_CHUNK = 2;  // k-blocks per accumulator chunk (64 k)
+constexpr int KB_PER_CHUNK = 4;  // k-blocks per accumulator chunk (128 k)
+static_assert(KB_PER_CHUNK >= 2, "the L products lag the C products by one k-block");
 constexpr int A_BYTES = TM * KB * 2;                    // 8 KiB
 constexpr int B_BYTES = TN * KB * 2;                    // 16 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 KiB
@@ -271,6 +273,26 @@ __global__ void __launch_bounds__(THREADS, 1)
     // -------------------------------- MMA issuer --------------------------------
     if (lane == 0) {
       const uint32_t tL = tmem, tC = tmem + TMEM_C;
+      // C products of k-block j, L products of k-block j - 1, so that the C drain of a chunk
+      // overlaps its last two L k-blocks and the L drain the next chunk's first two C k-blocks:
+      //   C0 C1 L0 C2 L1 C3 [C-full] L2 L3 [L-full]
+      auto issue_c = [&](uint32_t base) {
+#pragma unroll
+        for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+          const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
+          umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o));  // lo * hi'
+          umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o));  // hi * lo'
+        }
+      };
+      auto issue_l = [&](uint32_t G) {
+        const uint32_t s = G % STAGES, base = tiles + s * STAGE_BYTES;
+#pragma unroll
+        for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+          const uint32_t o = 32u * ks;
+          umma(tL, sdesc(base + o), sdesc(base + 2 * A_BYTES + o));  // lo * lo'
+        }
+        umma_commit(empty0 + 8 * s);  // stage free once these (and all earlier) MMAs are done
+      };
       for (uint32_t c = 0; c < n_chunks; ++c) {
         const uint32_t par = c & 1u, G0 = c * KB_PER_CHUNK;
         if (!mbar_wait(c_empty, par, p.status, abort)) break;
@@ -283,28 +305,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           fence_after();
-          const uint32_t base = tiles + s * STAGE_BYTES;
-#pragma unroll
-          for (uint32_t ks = 0; ks < KB / 16; ++ks) {
-            const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
-            umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o));      // lo * hi'
-            umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o));      // hi * lo'
+          issue_c(tiles + s * STAGE_BYTES);
+          if (kb == KB_PER_CHUNK - 1) umma_commit(c_full);
+          if (kb == 1) {
+            if (!mbar_wait(l_empty, par, p.status, abort)) {
+              ok = false;
+              break;
+            }
+            fence_after();
           }
+          if (kb >= 1) issue_l(G - 1);
         }
         if (!ok) break;
-        umma_commit(c_full);
-        if (!mbar_wait(l_empty, par, p.status, abort)) break;
-        fence_after();
-        for (uint32_t kb = 0; kb < KB_PER_CHUNK; ++kb) {
-          const uint32_t s = (G0 + kb) % STAGES;
-          const uint32_t base = tiles + s * STAGE_BYTES;
-#pragma unroll
-          for (uint32_t ks = 0; ks < KB / 16; ++ks) {
-            const uint32_t o = 32u * ks;
-            umma(tL, sdesc(base + o), sdesc(base + 2 * A_BYTES + o));  // lo * lo'
-          }
-          umma_commit(empty0 + 8 * s);
-        }
+        issue_l(G0 + KB_PER_CHUNK - 1);
         umma_commit(l_full);
       }
       // every MMA issued above completes before the tensor memory is freed
