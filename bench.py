@@ -369,7 +369,7 @@ def run_ours(args, w):
         "config": {"workload": w.name, "db_rows": w.s, "queries": w.Q, "rotations": w.R, "code_bits": w.l,
                    "planted": w.planted,
                    "path": "tc: int8 limbs as exact bf16 on tcgen05.mma, fp32 TMEM accumulators re-based every "
-                           "64 k inside [2^23, 2^24) (bit-exact; integer results)",
+                           "128 k inside [2^23, 2^24] (bit-exact; integer results)",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: resident limb planes 24 B x rows x 12800 = "
                          f"{24 * w.s * w.l / 1e9:.1f} GB"},
