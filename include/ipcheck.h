@@ -188,6 +188,20 @@ int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2
                      size_t ldz, uint64_t row0, void* stream);
 
 /*
+ * IPC_PATH_TC with a tile width and an optional list of column tiles (the form the serving
+ * loop replays inside a CUDA graph). tile_cols: 256 or 128 query columns per tile.
+ * col_tiles (device, may be NULL): indices of the tiles of that width to compute, n_col_list
+ * (device) their count, read when the kernel starts; with NULL every tile of [0, n_cols) is
+ * computed, one CTA per tile. With a list the launch is persistent (one CTA per SM walking the
+ * list), so its grid does not depend on the list. Other arguments and errors as ipc_ring_gemm_tc.
+ */
+int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2],
+                           size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols,
+                           uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                           uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                           const uint32_t* col_tiles, const uint32_t* n_col_list, void* stream);
+
+/*
  * A4-A8 (per comparison, and the OR tree inside aligned row blocks).
  * z_code[j], z_mask[j]: the j-th additive components over Z_{2^16} of the
  * code dot and of ml, [n_cols][ldz] uint16 (A3 outputs of parties 0..2).

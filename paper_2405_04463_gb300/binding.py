@@ -66,6 +66,8 @@ _SIGS = {
     "ipc_split_limbs_bf16": [_vp, _sz, _vp, _vp, _vp],
     "ipc_prep_query_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_ring_gemm_tc": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
+    "ipc_ring_gemm_tc_tiles": [_u32, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
+                               _u64, _vp, _vp, _vp],
     "ipc_ring_gemm": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
     "ipc_ring_gemm_tiles": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
                             _u64, _vp, _vp, _vp],
@@ -169,6 +171,14 @@ def ipc_ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags,
     _check(lib.ipc_ring_gemm_tc(_VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
                                 ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
                                 seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
+
+
+def ipc_ring_gemm_tc_tiles(tile_cols, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+                           seed_prev, vec, z, ldz, row0, col_tiles=None, n_col_list=None, stream=None):
+    _check(lib.ipc_ring_gemm_tc_tiles(tile_cols, _VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]),
+                                      x_rows, ptr(b_lo), ptr(b_hi), n_cols, n_pad, l, ptr(col_tags),
+                                      seed_own & (2**64 - 1), seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0,
+                                      ptr(col_tiles), ptr(n_col_list), _stream(stream)))
 
 
 IPC_GEMM_MIX128, IPC_GEMM_MMA128, IPC_GEMM_MMA64, IPC_GEMM_MMA32 = 0, 1, 2, 3

@@ -26,6 +26,11 @@ int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], s
                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream);
+int ring_gemm_tc_variant(uint32_t tile_cols, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2],
+                         size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
+                         uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
+                         uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
+                         const uint32_t* n_col_list, cudaStream_t stream);
 const char* thread_last_error();
 
 namespace {
@@ -100,11 +105,10 @@ extern "C" int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], con
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
 }
 
-extern "C" int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
-                                const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
-                                uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
-                                uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, void* stream) {
-  const char* who = "ipc_ring_gemm_tc";
+namespace {
+int check_tc_args(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+                  uint32_t vec, const uint16_t* z, size_t ldz, uint64_t row0, const char* who) {
   auto fail = [&](const char* what) { return bad((std::string(who) + ": " + what).c_str()); };
   if (!x_lo || !x_hi || !b_lo || !b_hi || !col_tags || !z) return fail("null pointer");
   for (int i = 0; i < 2; ++i)
@@ -117,9 +121,37 @@ extern "C" int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* c
   if (row0 % 8 != 0) return fail("row0 must be a multiple of 8");
   if (vec > 1) return fail("vec is 0 (code) or 1 (mask)");
   if (x_rows > IPC_MAX_GEMM_ROWS) return fail("too many rows in one call");
+  return IPC_OK;
+}
+}  // namespace
+
+extern "C" int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+                                const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
+                                uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
+                                uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, void* stream) {
+  int rc = check_tc_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                         "ipc_ring_gemm_tc");
+  if (rc) return rc;
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
   return ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
                       row0, as_stream(stream));
+}
+
+extern "C" int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const x_lo[2],
+                                      const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+                                      const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                                      const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
+                                      uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
+                                      const uint32_t* n_col_list, void* stream) {
+  int rc = check_tc_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                         "ipc_ring_gemm_tc_tiles");
+  if (rc) return rc;
+  if (tile_cols != 128 && tile_cols != 256) return bad("ipc_ring_gemm_tc_tiles: tile_cols must be 128 or 256");
+  if ((col_tiles == nullptr) != (n_col_list == nullptr))
+    return bad("ipc_ring_gemm_tc_tiles: col_tiles and n_col_list go together");
+  if (x_rows == 0 || n_cols == 0) return IPC_OK;
+  return ring_gemm_tc_variant(tile_cols, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+                              seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
 }
 
 extern "C" int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,

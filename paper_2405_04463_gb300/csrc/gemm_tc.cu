@@ -39,34 +39,44 @@ namespace ipc {
 namespace {
 
 constexpr int TM = 128;          // database rows per tile (MMA M = TMEM lanes)
-constexpr int TN = 256;          // query columns per tile (MMA N)
 constexpr int KB = 32;           // bf16 elements of K per stage: one 64-byte swizzled row
 constexpr int STAGES = 4;
 constexpr int KB_PER_CHUNK = 4;  // k-blocks per accumulator chunk (128 k)
 static_assert(KB_PER_CHUNK >= 2, "the L products lag the C products by one k-block");
-constexpr int A_BYTES = TM * KB * 2;                    // 8 KiB
-constexpr int B_BYTES = TN * KB * 2;                    // 16 KiB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 KiB
+constexpr int A_BYTES = TM * KB * 2;  // 8 KiB
 constexpr int THREADS = 10 * 32;
 constexpr int DRAIN_THREADS = 8 * 32;
-constexpr int NUM_BARS = 2 * STAGES + 5;  // full[S], empty[S], c_full, c_empty, l_full, l_empty, done
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NUM_BARS;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t TMEM_C = 256;          // column offset of the C accumulator
-constexpr uint32_t MAGIC = 0x4B400000u;   // fp32 bits of 1.5 * 2^23
-// z of one tile, [TN][TM] uint16, staged in the (then idle) stage ring
-static_assert(TN * TM * 2 <= STAGES * STAGE_BYTES, "z tile must fit the stage ring");
+// full[S], empty[S], c_full, c_empty, l_full, l_empty, done, epi_done
+constexpr int NUM_BARS = 2 * STAGES + 6;
+constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
 
-// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1), B bf16
-// (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
-                           (static_cast<uint32_t>(TM >> 4) << 24);
+// Tile shape: TN query columns per tile (MMA N = 256 or 128).
+template <int TN>
+struct Shape {
+  static_assert(TN == 256 || TN == 128, "tile width");
+  static constexpr int B_BYTES = TN * KB * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 or 32 KiB
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NUM_BARS;
+  static constexpr uint32_t TMEM_COLS = 2 * TN;  // L in [0, TN), C in [TN, 2 TN)
+  static constexpr uint32_t TMEM_C = TN;
+  static constexpr int DCOLS = TN / 2;       // columns per drain thread (two drain warps per lane quarter)
+  static constexpr int GROUPS = DCOLS / 32;  // 32-column TMEM loads per accumulator and drain
+  // Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1), B bf16
+  // (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
+                                    (static_cast<uint32_t>(TM >> 4) << 24);
+  // z of one tile, [TN][TM] uint16, staged in the (then idle) stage ring
+  static_assert(TN * TM * 2 <= STAGES * STAGE_BYTES, "z tile must fit the stage ring");
+};
 
 struct TcParams {
   uint32_t n_cols;
   uint32_t x_rows;
   uint32_t kb_total;  // 2l / KB
   uint32_t kb_half;   // l / KB
+  uint32_t n_row_tiles;
+  const uint32_t* col_tiles;   // list mode: the column tiles to compute (device)
+  const uint32_t* n_col_list;  // list mode: their count (device), read when the kernel starts
   const uint32_t* col_tags;
   uint64_t seed_own, seed_prev;
   uint32_t vec;
@@ -135,11 +145,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          (1ull << 46) | (4ull << 61);
 }
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b) {
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           d_tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(1u)
+      "l"(a), "l"(b), "r"(idesc), "r"(1u)
       : "memory");
 }
 
@@ -203,23 +213,46 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// Without a list (LIST false) the grid is (column tiles, row tiles), one tile per CTA. With a list,
+// gridDim.x persistent CTAs walk items w = blockIdx.x + i * gridDim.x: column tile
+// list[w % n_ct], row tile w / n_ct; k-block and chunk counters run on across items, and the
+// producer starts an item's copies once the previous item's epilogue has left the stage ring.
+template <int TN, bool LIST>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tb_lo, const __grid_constant__ CUtensorMap tb_hi,
                    const __grid_constant__ CUtensorMap ta0_lo, const __grid_constant__ CUtensorMap ta0_hi,
                    const __grid_constant__ CUtensorMap ta1_lo, const __grid_constant__ CUtensorMap ta1_hi,
                    const TcParams p) {
+  using S = Shape<TN>;
+  constexpr int B_BYTES = S::B_BYTES, STAGE_BYTES = S::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ uint32_t s_abort;
+  uint32_t n_ct = 0, my_items = 1;
+  if (LIST) {
+    n_ct = *p.n_col_list;
+    const uint32_t n_items = n_ct * p.n_row_tiles;
+    my_items = n_items > blockIdx.x ? (n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (my_items == 0) return;  // uniform for the CTA, before any barrier or allocation
+  }
+  auto coords = [&](uint32_t i, uint32_t& q0, uint32_t& d0) {
+    if (LIST) {
+      const uint32_t w = blockIdx.x + i * gridDim.x;
+      q0 = p.col_tiles[w % n_ct] * TN;
+      d0 = (w / n_ct) * TM;
+    } else {
+      q0 = blockIdx.x * TN;
+      d0 = blockIdx.y * TM;
+    }
+  };
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t tiles = smem_addr(smem);
   const uint32_t bars = tiles + STAGES * STAGE_BYTES;
   const uint32_t full0 = bars, empty0 = bars + 8 * STAGES;
   const uint32_t c_full = bars + 16 * STAGES, c_empty = c_full + 8, l_full = c_full + 16, l_empty = c_full + 24,
-                 done_bar = c_full + 32;
+                 done_bar = c_full + 32, epi_done = c_full + 40;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t q0 = blockIdx.x * TN, d0 = blockIdx.y * TM;
   const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;
 
   if (threadIdx.x == 0) {
@@ -232,12 +265,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     mbar_init(l_full, 1);
     mbar_init(l_empty, DRAIN_THREADS / 32);
     mbar_init(done_bar, 1);
+    mbar_init(epi_done, DRAIN_THREADS / 32);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                 "r"(TMEM_COLS)
+                 "r"(S::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -250,18 +284,27 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------- TMA producer -------------------------------
     if (lane == 0) {
       uint32_t issued = 0;
-      for (uint32_t G = 0; G < p.kb_total; ++G) {
-        const uint32_t s = G % STAGES;
-        if (!mbar_wait(empty0 + 8 * s, ((G / STAGES) & 1u) ^ 1u, p.status, abort)) break;
-        const uint32_t full = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
-        mbar_expect_tx(full, STAGE_BYTES);
-        const bool first = G < p.kb_half;
-        const int32_t kx = static_cast<int32_t>((first ? G : G - p.kb_half) * KB);
-        tma_load(base, first ? &ta0_lo : &ta1_lo, kx, static_cast<int32_t>(d0), full);
-        tma_load(base + A_BYTES, first ? &ta0_hi : &ta1_hi, kx, static_cast<int32_t>(d0), full);
-        tma_load(base + 2 * A_BYTES, &tb_lo, static_cast<int32_t>(G * KB), static_cast<int32_t>(q0), full);
-        tma_load(base + 2 * A_BYTES + B_BYTES, &tb_hi, static_cast<int32_t>(G * KB), static_cast<int32_t>(q0), full);
-        issued = G + 1;
+      bool ok = true;
+      for (uint32_t i = 0; i < my_items && ok; ++i) {
+        uint32_t q0, d0;
+        coords(i, q0, d0);
+        if (i > 0 && !mbar_wait(epi_done, (i - 1) & 1u, p.status, abort)) break;
+        for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
+          const uint32_t G = i * p.kb_total + kb, s = G % STAGES;
+          if (!mbar_wait(empty0 + 8 * s, ((G / STAGES) & 1u) ^ 1u, p.status, abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t full = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
+          mbar_expect_tx(full, STAGE_BYTES);
+          const bool first = kb < p.kb_half;
+          const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
+          tma_load(base, first ? &ta0_lo : &ta1_lo, kx, static_cast<int32_t>(d0), full);
+          tma_load(base + A_BYTES, first ? &ta0_hi : &ta1_hi, kx, static_cast<int32_t>(d0), full);
+          tma_load(base + 2 * A_BYTES, &tb_lo, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+          tma_load(base + 2 * A_BYTES + B_BYTES, &tb_hi, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+          issued = G + 1;
+        }
       }
       if (*abort) {
         // copies that may still be in flight land before the CTA leaves (bounded, no abort)
@@ -272,7 +315,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // -------------------------------- MMA issuer --------------------------------
     if (lane == 0) {
-      const uint32_t tL = tmem, tC = tmem + TMEM_C;
+      const uint32_t tL = tmem, tC = tmem + S::TMEM_C;
       // C products of k-block j, L products of k-block j - 1, so that the C drain of a chunk
       // overlaps its last two L k-blocks and the L drain the next chunk's first two C k-blocks:
       //   C0 C1 L0 C2 L1 C3 [C-full] L2 L3 [L-full]
@@ -280,8 +323,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (uint32_t ks = 0; ks < KB / 16; ++ks) {
           const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
-          umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o));  // lo * hi'
-          umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o));  // hi * lo'
+          umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o), S::IDESC);  // lo * hi'
+          umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o), S::IDESC);  // hi * lo'
         }
       };
       auto issue_l = [&](uint32_t G) {
@@ -289,11 +332,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (uint32_t ks = 0; ks < KB / 16; ++ks) {
           const uint32_t o = 32u * ks;
-          umma(tL, sdesc(base + o), sdesc(base + 2 * A_BYTES + o));  // lo * lo'
+          umma(tL, sdesc(base + o), sdesc(base + 2 * A_BYTES + o), S::IDESC);  // lo * lo'
         }
         umma_commit(empty0 + 8 * s);  // stage free once these (and all earlier) MMAs are done
       };
-      for (uint32_t c = 0; c < n_chunks; ++c) {
+      const uint32_t total_chunks = my_items * n_chunks;
+      for (uint32_t c = 0; c < total_chunks; ++c) {
         const uint32_t par = c & 1u, G0 = c * KB_PER_CHUNK;
         if (!mbar_wait(c_empty, par, p.status, abort)) break;
         fence_after();
@@ -326,14 +370,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ----------------------------------- drain ----------------------------------
-    // z2[k] holds the running sums (mod 2^16) of columns 2k (low half) and 2k + 1 (high half).
+    // z2[k] holds the running sums (mod 2^16) of columns 2k (low half) and 2k + 1 (high half)
+    // of this thread's DCOLS columns.
+    constexpr int DCOLS = S::DCOLS, GROUPS = S::GROUPS;
     const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - 2) >> 2;
-    const uint32_t tL = tmem + ((32u * q) << 16) + 128u * h, tC = tL + TMEM_C;
-    uint32_t z2[64];
+    const uint32_t tL = tmem + ((32u * q) << 16) + DCOLS * h, tC = tL + S::TMEM_C;
 #pragma unroll
-    for (int k = 0; k < 64; ++k) z2[k] = 0;
-#pragma unroll
-    for (uint32_t g = 0; g < 4; ++g) {
+    for (uint32_t g = 0; g < GROUPS; ++g) {
       tmem_fill32(tL + 32 * g, MAGIC);
       tmem_fill32(tC + 32 * g, MAGIC);
     }
@@ -344,51 +387,65 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_arrive(c_empty);
       mbar_arrive(l_empty);
     }
-    for (uint32_t c = 0; c < n_chunks; ++c) {
-      const uint32_t par = c & 1u;
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(c_full, par, p.status, abort))) break;
-      fence_after();
+    bool ok = true;
+    for (uint32_t i = 0; i < my_items && ok; ++i) {
+      uint32_t z2[DCOLS / 2];
 #pragma unroll
-      for (uint32_t g = 0; g < 4; ++g) {
-        uint32_t r[32];
-        tmem_ld32(tC + 32 * g, r);
-        tmem_wait_ld();
+      for (int k = 0; k < DCOLS / 2; ++k) z2[k] = 0;
+      for (uint32_t cc = 0; cc < n_chunks; ++cc) {
+        const uint32_t par = (i * n_chunks + cc) & 1u;
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(c_full, par, p.status, abort))) {
+          ok = false;
+          break;
+        }
+        fence_after();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) z2[16 * g + k] = add16x2(z2[16 * g + k], pack_c16(r[2 * k], r[2 * k + 1]));
-        tmem_fill32(tC + 32 * g, MAGIC);
+        for (uint32_t g = 0; g < GROUPS; ++g) {
+          uint32_t r[32];
+          tmem_ld32(tC + 32 * g, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 16; ++k) z2[16 * g + k] = add16x2(z2[16 * g + k], pack_c16(r[2 * k], r[2 * k + 1]));
+          tmem_fill32(tC + 32 * g, MAGIC);
+        }
+        tmem_wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(c_empty);
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(l_full, par, p.status, abort))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+#pragma unroll
+        for (uint32_t g = 0; g < GROUPS; ++g) {
+          uint32_t r[32];
+          tmem_ld32(tL + 32 * g, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 16; ++k) z2[16 * g + k] = add16x2(z2[16 * g + k], pack_lo16(r[2 * k], r[2 * k + 1]));
+          tmem_fill32(tL + 32 * g, MAGIC);
+        }
+        tmem_wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(l_empty);
       }
-      tmem_wait_st();
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(c_empty);
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(l_full, par, p.status, abort))) break;
-      fence_after();
-#pragma unroll
-      for (uint32_t g = 0; g < 4; ++g) {
-        uint32_t r[32];
-        tmem_ld32(tL + 32 * g, r);
-        tmem_wait_ld();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) z2[16 * g + k] = add16x2(z2[16 * g + k], pack_lo16(r[2 * k], r[2 * k + 1]));
-        tmem_fill32(tL + 32 * g, MAGIC);
-      }
-      tmem_wait_st();
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(l_empty);
-    }
-    // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) (App. C) ----
-    // The running sums go to shared memory (the stage ring is idle once every drainer has seen
-    // the last L-full), then each (column, 8-row group) item adds its zero shares, which one
-    // Philox block per seed gives for all 8 rows, and writes 16 bytes of z.
-    named_sync(1, DRAIN_THREADS);
-    if (!*abort) {
+      // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) (App. C) ----
+      // The running sums go to shared memory (the stage ring is idle once every drainer has seen
+      // the item's last L-full and before the producer sees epi-done), then each (column, 8-row
+      // group) item adds its zero shares, which one Philox block per seed gives for all 8 rows,
+      // and writes 16 bytes of z.
+      named_sync(1, DRAIN_THREADS);
+      if (*abort) break;  // uniform: read after the barrier that every drainer reaches
+      uint32_t q0, d0;
+      coords(i, q0, d0);
       uint16_t* zs = reinterpret_cast<uint16_t*>(smem);  // [TN][TM]
       const uint32_t row = 32 * q + lane;
 #pragma unroll
-      for (int k = 0; k < 64; ++k) {
-        zs[(128 * h + 2 * k) * TM + row] = static_cast<uint16_t>(z2[k]);
-        zs[(128 * h + 2 * k + 1) * TM + row] = static_cast<uint16_t>(z2[k] >> 16);
+      for (int k = 0; k < DCOLS / 2; ++k) {
+        zs[(DCOLS * h + 2 * k) * TM + row] = static_cast<uint16_t>(z2[k]);
+        zs[(DCOLS * h + 2 * k + 1) * TM + row] = static_cast<uint16_t>(z2[k] >> 16);
       }
       named_sync(1, DRAIN_THREADS);
       const uint32_t dt = threadIdx.x - 64;
@@ -417,13 +474,15 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (uint32_t e = 0; e < p.x_rows - r0; ++e) dst[e] = static_cast<uint16_t>(w[e >> 1] >> (16 * (e & 1)));
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(epi_done);  // this warp is done with the stage ring
     }
   }
   fence_before();
   __syncthreads();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
   }
 }
 
@@ -462,29 +521,60 @@ int make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t ro
   return IPC_OK;
 }
 
-}  // namespace
+int sm_count_tc() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
 
-int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
-                 const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
-                 uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
-                 cudaStream_t stream) {
-  CUtensorMap m[6];
-  int rc;
-  if ((rc = make_map_bf16(&m[0], b_lo, 2ull * l, n_pad, TN)) || (rc = make_map_bf16(&m[1], b_hi, 2ull * l, n_pad, TN)) ||
-      (rc = make_map_bf16(&m[2], x_lo[0], l, x_rows, TM)) || (rc = make_map_bf16(&m[3], x_hi[0], l, x_rows, TM)) ||
-      (rc = make_map_bf16(&m[4], x_lo[1], l, x_rows, TM)) || (rc = make_map_bf16(&m[5], x_hi[1], l, x_rows, TM)))
-    return rc;
+template <int TN, bool LIST>
+int launch_tc(const CUtensorMap* m, const TcParams& p, dim3 grid, cudaStream_t stream) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = cudaFuncSetAttribute(gemm_tc_kernel<TN, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Shape<TN>::SMEM_BYTES);
   });
   IPC_CUDA_TRY(attr);
+  gemm_tc_kernel<TN, LIST><<<grid, THREADS, Shape<TN>::SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+}  // namespace
+
+// tile_cols: 256 or 128 query columns per tile. With col_tiles set, only the listed tiles of
+// that width are computed (n_col_list, on the device, holds their count) by one persistent CTA
+// per SM; otherwise every tile of [0, n_cols), one CTA each.
+int ring_gemm_tc_variant(uint32_t tile_cols, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2],
+                         size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
+                         uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
+                         uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
+                         const uint32_t* n_col_list, cudaStream_t stream) {
+  if (tile_cols != 256 && tile_cols != 128) {
+    set_error("tcgen05 ring GEMM: tile width must be 128 or 256");
+    return IPC_EINVAL;
+  }
+  CUtensorMap m[6];
+  int rc;
+  if ((rc = make_map_bf16(&m[0], b_lo, 2ull * l, n_pad, tile_cols)) ||
+      (rc = make_map_bf16(&m[1], b_hi, 2ull * l, n_pad, tile_cols)) ||
+      (rc = make_map_bf16(&m[2], x_lo[0], l, x_rows, TM)) || (rc = make_map_bf16(&m[3], x_hi[0], l, x_rows, TM)) ||
+      (rc = make_map_bf16(&m[4], x_lo[1], l, x_rows, TM)) || (rc = make_map_bf16(&m[5], x_hi[1], l, x_rows, TM)))
+    return rc;
   TcParams p;
   p.n_cols = n_cols;
   p.x_rows = static_cast<uint32_t>(x_rows);
   p.kb_total = 2 * l / KB;
   p.kb_half = l / KB;
+  p.n_row_tiles = static_cast<uint32_t>((x_rows + TM - 1) / TM);
+  p.col_tiles = col_tiles;
+  p.n_col_list = n_col_list;
   p.col_tags = col_tags;
   p.seed_own = seed_own;
   p.seed_prev = seed_prev;
@@ -493,10 +583,20 @@ int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], s
   p.ldz = ldz;
   p.row0 = row0;
   p.status = status_ptr();
-  const dim3 grid((n_cols + TN - 1) / TN, static_cast<unsigned>((x_rows + TM - 1) / TM));
-  gemm_tc_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
-  IPC_CUDA_TRY(cudaGetLastError());
-  return IPC_OK;
+  if (col_tiles) {
+    const dim3 grid(static_cast<unsigned>(sm_count_tc()));
+    return tile_cols == 256 ? launch_tc<256, true>(m, p, grid, stream) : launch_tc<128, true>(m, p, grid, stream);
+  }
+  const dim3 grid((n_cols + tile_cols - 1) / tile_cols, p.n_row_tiles);
+  return tile_cols == 256 ? launch_tc<256, false>(m, p, grid, stream) : launch_tc<128, false>(m, p, grid, stream);
+}
+
+int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+                 const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+                 uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                 cudaStream_t stream) {
+  return ring_gemm_tc_variant(256, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev,
+                              vec, z, ldz, row0, nullptr, nullptr, stream);
 }
 
 }  // namespace ipc

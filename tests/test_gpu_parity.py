@@ -391,3 +391,51 @@ def test_tc_gemm_matches_int32_on_random_limbs(torch, rows, N, row0):
     ipc.ipc_status()
     assert (z.cpu()[:, :rows] == ref.cpu()[:, :rows]).all()
     assert (z.cpu()[:, rows:] == 77).all()
+
+
+@pytest.mark.parametrize("tile_cols", [256, 128])
+def test_tc_tile_lists_match_int32(torch, tile_cols):
+    """tcgen05 path with 256- and 128-column tiles: all tiles, then a sparse device-side list of
+    column tiles walked by persistent CTAs (unlisted columns untouched)."""
+    ipc = lib()
+    rows, N, n_pad = 1000, 700, 768
+    g = torch.Generator(device="cpu").manual_seed(tile_cols)
+    planes = [torch.randint(-128, 128, (rows, L), dtype=torch.int8, generator=g).cuda() for _ in range(4)]
+    blo = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    bhi = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    tags = torch.from_numpy(tags_for(4, 23, 31).view(np.int32)).cuda()
+    ldz = 1000
+    ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 0, ref, ldz, 16)
+    p16 = [_bf16(torch, t) for t in planes]
+    b16 = [_bf16(torch, blo), _bf16(torch, bhi)]
+    z = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tc_tiles(tile_cols, p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 0, z,
+                               ldz, 16)
+    torch.cuda.synchronize()
+    ipc.ipc_status()
+    refc = ref.cpu()
+    assert (z.cpu()[:, :rows] == refc[:, :rows]).all()
+    ntile = (N + tile_cols - 1) // tile_cols
+    chosen = [t for t in range(ntile) if t != 1] if ntile > 2 else [ntile - 1]
+    lst = torch.tensor(chosen, dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([len(chosen)], dtype=torch.int32, device="cuda")
+    z2 = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tc_tiles(tile_cols, p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 0, z2,
+                               ldz, 16, lst, cnt)
+    torch.cuda.synchronize()
+    ipc.ipc_status()
+    z2 = z2.cpu()
+    for t in range(ntile):
+        cols = slice(t * tile_cols, min(N, (t + 1) * tile_cols))
+        if t in chosen:
+            assert (z2[cols, :rows] == refc[cols, :rows]).all(), t
+        else:
+            assert (z2[cols] == 77).all(), t
+    # an empty list launches nothing that writes
+    cnt0 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    z3 = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tc_tiles(tile_cols, p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 0, z3,
+                               ldz, 16, lst, cnt0)
+    torch.cuda.synchronize()
+    assert (z3.cpu() == 77).all()
