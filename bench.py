@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--kernel", default=None, help="time one ring-GEMM path alone (i8mix | i8mma | i32 | tc), for profiling")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--serving", action="store_true",
+                    help="serving run: Poisson arrivals of 1..256-query batches at 3 rates (workload c4)")
+    ap.add_argument("--requests-per-rate", type=int, default=40)
+    ap.add_argument("--rates", default="0.3,0.6,0.9", help="arrival rates as fractions of the measured capacity")
+    ap.add_argument("--pool", type=int, default=0, help="serving pool in query slots (0 = library default)")
+    ap.add_argument("--capacity-requests", type=int, default=8)
     return ap.parse_args()
 
 
@@ -393,8 +399,117 @@ def run_ours(args, w):
     print(json.dumps(res), flush=True)
 
 
+def run_serving(args):
+    """Continuous batching on the serving workload: 250,000 resident rows, batches of U{1..256}
+    queries x 31 rotations arriving by a seeded Poisson process at fractions of the measured
+    capacity (requests/s of a burst of batches of 128 and 129 queries, mean 128.5). Latency =
+    completion - submission per request, both taken by the library's own clock."""
+
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    from paper_2405_04463_gb300.workload import encode_gpu, load_workload, make_ctx
+
+    w = synth.workload("c4")
+    torch.cuda.set_device(0)
+    ctx = make_ctx(w, path="tc", max_queries=256)
+    t_load = time.perf_counter()
+    load_workload(ctx, w, chunk=32768)
+    t_load = time.perf_counter() - t_load
+    # 512 query shares on the host; request k takes a window of its batch size
+    rng = np.random.default_rng(0x5E7E)
+    qc = rng.integers(0, 2**63, size=(512, w.nwords), dtype=np.int64).view(np.uint64)
+    qm = rng.integers(0, 2**63, size=(512, w.nwords), dtype=np.int64).view(np.uint64)
+    qcode, qmask = encode_gpu(qc, qm, w.l, w.q_share_seed, 1)
+    hcode = [qcode[j].cpu().numpy() for j in range(3)]
+    hmask = [qmask[j].cpu().numpy() for j in range(3)]
+    del qcode, qmask
+    ipc.ipc_serve_start(ctx, pool_queries=args.pool, variant=ipc.IPC_SERVE_AUTOTUNE)
+    tuning = ipc.ipc_serve_tuning(ctx)
+    clocks = Clocks(0)
+    clocks.start()
+
+    def submit(q, off):
+        code = [np.ascontiguousarray(hcode[j][off:off + q]) for j in range(3)]
+        mask = [np.ascontiguousarray(hmask[j][off:off + q]) for j in range(3)]
+        while True:
+            try:
+                return ipc.ipc_serve_submit(ctx, code, mask, q)
+            except ipc.IpcError as e:
+                if e.rc != ipc.IPC_EAGAIN:
+                    raise
+                time.sleep(0.001)
+
+    def collect(rids, sizes):
+        times = []
+        for rid, q in zip(rids, sizes):
+            sh = np.zeros((3, q), np.uint8)
+            ipc.fetch_bit_shares(ctx, rid, sh, q, -1)
+            times.append(ipc.ipc_serve_times(ctx, rid))
+            ipc.ipc_release(ctx, rid)
+        return np.array(times)
+
+    # capacity: a burst of batches of 128 and 129 queries
+    st0 = ipc.ipc_serve_stats(ctx)
+    sizes = [128 + (k & 1) for k in range(args.capacity_requests)]
+    rids = [submit(q, k % 128) for k, q in enumerate(sizes)]
+    t = collect(rids, sizes)
+    span = t[:, 2].max() - t[:, 0].min()
+    capacity = len(sizes) / span
+    st1 = ipc.ipc_serve_stats(ctx)
+    cap_cmp = (st1["comparisons"] - st0["comparisons"]) / span
+    out_rates = []
+    for k, frac in enumerate(float(x) for x in args.rates.split(",")):
+        lam = frac * capacity
+        r = np.random.default_rng(0xA441 + k)
+        gaps = r.exponential(1.0 / lam, size=args.requests_per_rate)
+        qs = r.integers(1, 257, size=args.requests_per_rate)
+        offs = r.integers(0, 256, size=args.requests_per_rate)
+        rids = []
+        s0 = ipc.ipc_serve_stats(ctx)
+        t0 = time.perf_counter()
+        at = 0.0
+        for g, q, o in zip(gaps, qs, offs):
+            at += g
+            d = t0 + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            rids.append(submit(int(q), int(o)))
+        t = collect(rids, [int(q) for q in qs])
+        s1 = ipc.ipc_serve_stats(ctx)
+        lat = t[:, 2] - t[:, 0]
+        wait = t[:, 1] - t[:, 0]
+        span = t[:, 2].max() - t[:, 0].min()
+        out_rates.append({
+            "fraction_of_capacity": frac, "offered_req_per_s": lam, "requests": len(rids),
+            "achieved_req_per_s": len(rids) / span, "mean_batch": float(qs.mean()),
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "admission_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+            "comparisons_per_s": (s1["comparisons"] - s0["comparisons"]) / span,
+            "steps": s1["steps"] - s0["steps"],
+            "variant_steps": [a - b for a, b in zip(s1["variant_steps"], s0["variant_steps"])],
+        })
+    clk = clocks.stop()
+    stats = ipc.ipc_serve_stats(ctx)
+    ipc.ipc_serve_stop(ctx)
+    ipc.ipc_destroy(ctx)
+    print(json.dumps({
+        "metric": "serving: latency p50/p99 and comparisons/s under Poisson arrivals", "unit": "s / comparisons/s",
+        "config": {"workload": w.name, "db_rows": w.s, "rotations": w.R, "batch": "U{1..256} queries",
+                   "arrivals": "Poisson, seeded", "path": "tc", "pool_query_slots": stats["pool_queries"],
+                   "pool_cols": stats["pool_cols"], "chunks": stats["n_chunks"],
+                   "requests_per_rate": args.requests_per_rate},
+        "load_s": t_load, "capacity_req_per_s": capacity, "capacity_comparisons_per_s": cap_cmp,
+        "rates": out_rates, "tuning": json.loads(tuning) if tuning else None, "clocks": clk,
+        "data": "synthetic"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.serving:
+        run_serving(args)
+        return
     w = synth.workload(args.workload)
     if args.kernel:
         run_kernel(args, w)

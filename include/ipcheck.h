@@ -364,6 +364,65 @@ const char* ipc_last_error(const ipc_ctx* ctx);
  * instruction). Synchronous; allocates a small buffer. */
 int ipc_measure_peak(int what, void* stream, double* out);
 
+/* ======================================================================== */
+/* Serving (A9): continuous batching over the resident database.           */
+/* ======================================================================== */
+/*
+ * ipc_serve_start turns a context (database loaded, path IPC_PATH_TC, I8MMA or I8MIX) into a
+ * request loop on its own host thread. Requests (ipc_serve_submit) wait in FIFO order until
+ * Q consecutive query slots of a column pool are free (admission by device memory: the pool
+ * is allocated once, sized by pool_queries or from free device memory). One loop step runs
+ * one resident chunk for every admitted column: the six GEMMs (A3) as one persistent launch
+ * per party and vector over a device-side list of the column tiles in use, and the comparison
+ * phase (A4-A8) over the same list, replayed from a CUDA graph per (chunk, GEMM variant). A
+ * request visits every chunk once, starting wherever the loop is when it is admitted, then
+ * its OR tree is finished (A8) and its slots freed. Its result does not depend on the other
+ * requests: each PRF counter depends on its request id, query, rotation and row only.
+ * fetch_bit_shares / fetch_match_bits / ipc_release take serving request ids. While serving,
+ * ipc_serve_* and fetch_* may be called from any host thread; submit_queries and
+ * load_db_shares are refused. ipc_serve_stop (or ipc_destroy) finishes every submitted
+ * request and stops the loop.
+ */
+#define IPC_SERVE_AUTOTUNE -1
+typedef struct {
+  uint32_t pool_queries;   /* query slots (R columns each); 0 = 2 x max_queries, or less if memory is short */
+  uint32_t max_pending;    /* submitted, not yet admitted requests before IPC_EAGAIN; 0 = 1024 */
+  int32_t variant;         /* GEMM variant for every step, or IPC_SERVE_AUTOTUNE. IPC_PATH_TC:
+                              0 = 256-column tcgen05 tiles, 1 = 128-column; int8 paths: the
+                              IPC_GEMM_* variants */
+  const char* tune_cache;  /* autotuner table (JSON) read if it matches this device and shape,
+                              else measured and written; NULL = measure, keep in memory */
+} ipc_serve_config;
+
+typedef struct {
+  uint64_t steps, admitted, completed, pending;
+  double comparisons;       /* database rows x active columns over all steps so far */
+  double elapsed_s;         /* since ipc_serve_start */
+  uint32_t pool_queries, pool_cols, n_chunks;
+  uint64_t variant_steps[4];  /* steps run with each GEMM variant */
+} ipc_serve_counters;
+
+/* Errors: IPC_EINVAL (already serving, no rows, int32 path, bad variant), IPC_ENOMEM (pool). */
+int ipc_serve_start(ipc_ctx* ctx, const ipc_serve_config* cfg);
+/* code[j], mask[j]: HOST [n_queries][l] uint16, copied before return. Returns IPC_EAGAIN when
+ * max_pending requests are waiting; IPC_EINVAL if n_queries exceeds max_queries or the pool. */
+int ipc_serve_submit(ipc_ctx* ctx, const uint16_t* const code[3], const uint16_t* const mask[3], size_t n_queries,
+                     uint64_t* req_id);
+int ipc_serve_stop(ipc_ctx* ctx);
+int ipc_serve_stats(ipc_ctx* ctx, ipc_serve_counters* out);
+/* out: submit, admit and completion times of a request in seconds since ipc_serve_start
+ * (-1 while not reached). The completion time is taken on the host when the request's bit
+ * components have arrived in host memory. */
+int ipc_serve_times(ipc_ctx* ctx, uint64_t req_id, double out[3]);
+/* The autotuner's table as JSON (empty if a fixed variant was given). */
+int ipc_serve_tuning(ipc_ctx* ctx, char* buf, size_t len);
+/* Host-only helpers of the loop, exported for tests: the sorted distinct tiles of width
+ * tile_cols covering column ranges [col0[i], col0[i] + ncols[i]) (returns the count; at most
+ * max_tiles written), and the first run of `want` free slots (-1 if none). */
+int ipc_serve_tile_list(const uint32_t* col0, const uint32_t* ncols, uint32_t n_ranges, uint32_t tile_cols,
+                        uint32_t* tiles_out, uint32_t max_tiles);
+int64_t ipc_serve_first_fit(const uint8_t* used, uint32_t n_slots, uint32_t want);
+
 #ifdef __cplusplus
 }
 #endif

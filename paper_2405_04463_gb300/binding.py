@@ -48,6 +48,22 @@ class ipc_config(ctypes.Structure):
                 ("seeds", ctypes.c_uint64 * 3), ("keep_distances", ctypes.c_uint32), ("device", ctypes.c_int32)]
 
 
+IPC_SERVE_AUTOTUNE = -1
+SERVE_VARIANTS = {"tc256": 0, "tc128": 1, "mix128": 0, "mma128": 1, "mma64": 2, "mma32": 3}
+
+
+class ipc_serve_config(ctypes.Structure):
+    _fields_ = [("pool_queries", ctypes.c_uint32), ("max_pending", ctypes.c_uint32), ("variant", ctypes.c_int32),
+                ("tune_cache", ctypes.c_char_p)]
+
+
+class ipc_serve_counters(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("comparisons", ctypes.c_double), ("elapsed_s", ctypes.c_double),
+                ("pool_queries", ctypes.c_uint32), ("pool_cols", ctypes.c_uint32), ("n_chunks", ctypes.c_uint32),
+                ("variant_steps", ctypes.c_uint64 * 4)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build()); "
                       "there is no CPU fallback")
@@ -88,6 +104,14 @@ _SIGS = {
     "ipc_ctx_stream": [_vp],
     "ipc_set_input_stream": [_vp, _vp],
     "ipc_measure_peak": [_int, _vp, ctypes.POINTER(ctypes.c_double)],
+    "ipc_serve_start": [_vp, ctypes.POINTER(ipc_serve_config)],
+    "ipc_serve_submit": [_vp, _VP3, _VP3, _sz, ctypes.POINTER(_u64)],
+    "ipc_serve_stop": [_vp],
+    "ipc_serve_stats": [_vp, ctypes.POINTER(ipc_serve_counters)],
+    "ipc_serve_times": [_vp, _u64, ctypes.POINTER(ctypes.c_double)],
+    "ipc_serve_tuning": [_vp, ctypes.c_char_p, _sz],
+    "ipc_serve_tile_list": [_vp, _vp, _u32, _u32, _vp, _u32],
+    "ipc_serve_first_fit": [_vp, _u32, _u32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -97,6 +121,7 @@ lib.ipc_destroy.restype = None
 lib.ipc_db_rows.restype = _sz
 lib.ipc_last_error.restype = ctypes.c_char_p
 lib.ipc_ctx_stream.restype = _vp
+lib.ipc_serve_first_fit.restype = ctypes.c_int64
 
 
 def ptr(x) -> int | None:
@@ -293,3 +318,64 @@ def ipc_measure_peak(what: int, stream=None) -> float:
 def ipc_last_error(ctx=None) -> str:
     m = lib.ipc_last_error(ctx)
     return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------------------------
+# Serving (continuous batching)
+# ---------------------------------------------------------------------------------------------
+
+def ipc_serve_start(ctx, pool_queries: int = 0, max_pending: int = 0, variant=IPC_SERVE_AUTOTUNE,
+                    tune_cache: str | None = None):
+    v = SERVE_VARIANTS.get(variant, variant)
+    cfg = ipc_serve_config(pool_queries, max_pending, v, tune_cache.encode() if tune_cache else None)
+    _check(lib.ipc_serve_start(ctx, ctypes.byref(cfg)), ctx)
+
+
+def ipc_serve_submit(ctx, code, mask, n_queries) -> int:
+    """code[j], mask[j]: host arrays (numpy or pinned CPU tensors) [n_queries][l] uint16/int16."""
+    rid = _u64(0)
+    _check(lib.ipc_serve_submit(ctx, _VP3(*[ptr(a) for a in code]), _VP3(*[ptr(a) for a in mask]), n_queries,
+                                ctypes.byref(rid)), ctx)
+    return rid.value
+
+
+def ipc_serve_stop(ctx):
+    _check(lib.ipc_serve_stop(ctx), ctx)
+
+
+def ipc_serve_stats(ctx) -> dict:
+    out = ipc_serve_counters()
+    _check(lib.ipc_serve_stats(ctx, ctypes.byref(out)), ctx)
+    return {"steps": out.steps, "admitted": out.admitted, "completed": out.completed, "pending": out.pending,
+            "comparisons": out.comparisons, "elapsed_s": out.elapsed_s, "pool_queries": out.pool_queries,
+            "pool_cols": out.pool_cols, "n_chunks": out.n_chunks, "variant_steps": list(out.variant_steps)}
+
+
+def ipc_serve_times(ctx, req_id) -> tuple:
+    out = (ctypes.c_double * 3)()
+    _check(lib.ipc_serve_times(ctx, req_id, out), ctx)
+    return tuple(out)
+
+
+def ipc_serve_tuning(ctx) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib.ipc_serve_tuning(ctx, buf, len(buf)), ctx)
+    return buf.value.decode()
+
+
+def ipc_serve_tile_list(col0, ncols, tile_cols):
+    import numpy as np
+    col0 = np.ascontiguousarray(col0, dtype=np.uint32)
+    ncols = np.ascontiguousarray(ncols, dtype=np.uint32)
+    cap = int(sum((c + n + tile_cols - 1) // tile_cols - c // tile_cols for c, n in zip(col0, ncols))) + 1
+    out = np.zeros(cap, np.uint32)
+    n = lib.ipc_serve_tile_list(ptr(col0), ptr(ncols), len(col0), tile_cols, ptr(out), cap)
+    if n < 0:
+        _check(n)
+    return out[:n]
+
+
+def ipc_serve_first_fit(used, want) -> int:
+    import numpy as np
+    used = np.ascontiguousarray(used, dtype=np.uint8)
+    return int(lib.ipc_serve_first_fit(ptr(used), len(used), want))

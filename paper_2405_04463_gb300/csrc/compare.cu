@@ -6,6 +6,8 @@
 // ripple-carry BinAdd; App. D) then run 32 comparisons per logic instruction.
 // Party p only ever combines its own pair of components (c_p, c_{p-1}) and the
 // PRF outputs of its two seeds, as in the App. C product.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ipc {
@@ -122,6 +124,9 @@ struct CmpParams {
   uint64_t ld_roots;
   uint8_t* msb_out;
   uint64_t ld_msb;
+  const uint32_t* col_tiles;   // optional device list of tile_cols-wide column tiles
+  const uint32_t* n_col_list;  // its length (device)
+  uint32_t tile_cols;
 };
 
 // Shared memory per thread (index [slot][threadIdx.x], conflict-free):
@@ -143,8 +148,15 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
   auto S = [&](int slot) -> uint32_t& { return sm[slot * CT + tid]; };
   const uint64_t gtid = blockIdx.x * static_cast<uint64_t>(CT) + tid;
   if (gtid >= static_cast<uint64_t>(P.n_cols) * P.n_blocks) return;
-  const uint32_t n = static_cast<uint32_t>(gtid % P.n_cols);
+  uint32_t n = static_cast<uint32_t>(gtid % P.n_cols);
   const uint32_t blk = static_cast<uint32_t>(gtid / P.n_cols);
+  if (P.col_tiles) {
+    // the first (listed tiles x tile_cols) threads of each block row take the listed columns
+    const uint32_t active = *P.n_col_list * P.tile_cols;
+    if (n >= active) return;
+    n = P.col_tiles[n / P.tile_cols] * P.tile_cols + n % P.tile_cols;
+    if (n >= P.n_cols) return;
+  }
   const uint32_t req = P.col_tags[2 * n], tag = P.col_tags[2 * n + 1];
   const uint32_t words_per_block = 1u << P.p;
   const uint64_t blk_row = static_cast<uint64_t>(blk) << (5 + P.p);  // local first row of this block
@@ -321,12 +333,11 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
 }
 
 // Rows stage of the OR tree above the block roots: per column, pairwise levels p+1, p+2, ...
-__global__ void or_rows_kernel(uint32_t* roots, uint64_t ld_roots, uint32_t n_cols, uint32_t n_blocks, uint32_t p,
-                               const uint32_t* col_tags, Seeds sd) {
+__global__ void or_rows_kernel(uint32_t* roots, uint64_t ld_roots, uint64_t plane, uint32_t n_cols, uint32_t n_blocks,
+                               uint32_t p, const uint32_t* col_tags, Seeds sd) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_cols) return;
   const uint32_t req = col_tags[2 * n], tag = col_tags[2 * n + 1];
-  const uint64_t plane = static_cast<uint64_t>(n_cols) * ld_roots;
   uint32_t* r0 = roots + static_cast<uint64_t>(n) * ld_roots;
   uint32_t cnt = n_blocks, level = p + 1;
   while (cnt > 1) {
@@ -350,11 +361,10 @@ __global__ void or_rows_kernel(uint32_t* roots, uint64_t ld_roots, uint32_t n_co
 }
 
 // Rotation stage and lane fold, per query.
-__global__ void or_queries_kernel(const uint32_t* roots, uint64_t ld_roots, uint32_t n_cols, uint32_t Q, uint32_t R,
+__global__ void or_queries_kernel(const uint32_t* roots, uint64_t ld_roots, uint64_t plane, uint32_t Q, uint32_t R,
                                   const uint32_t* col_tags, Seeds sd, uint8_t* bit_shares) {
   const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= Q) return;
-  const uint64_t plane = static_cast<uint64_t>(n_cols) * ld_roots;
   const uint32_t req = col_tags[2 * (q * R)], tag = col_tags[2 * (q * R) + 1] & ~31u;
   B3 w[32];
   for (uint32_t rho = 0; rho < R; ++rho) {
@@ -385,9 +395,11 @@ __global__ void or_queries_kernel(const uint32_t* roots, uint64_t ld_roots, uint
 
 }  // namespace
 
-int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz, uint32_t n_cols,
-                   size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
-                   uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, cudaStream_t st) {
+int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
+                         uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
+                         const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
+                         uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
+                         uint32_t tile_cols, cudaStream_t st) {
   CmpParams P;
   for (int j = 0; j < 3; ++j) {
     P.zc[j] = z_code[j];
@@ -406,28 +418,48 @@ int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask
   P.ld_roots = ld_roots;
   P.msb_out = msb_out;
   P.ld_msb = ld_msb;
+  P.col_tiles = col_tiles;
+  P.n_col_list = n_col_list;
+  P.tile_cols = tile_cols;
   const uint64_t threads = static_cast<uint64_t>(n_cols) * P.n_blocks;
   const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
-  static bool attr = false;
-  if (!attr) {
-    IPC_CUDA_TRY(cudaFuncSetAttribute(compare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(compare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  });
+  IPC_CUDA_TRY(attr);
   compare_kernel<<<static_cast<unsigned>((threads + CT - 1) / CT), CT, smem, st>>>(P);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz, uint32_t n_cols,
+                   size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
+                   uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, cudaStream_t st) {
+  return compare_launch_tiles(z_code, z_mask, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, p, roots, ld_roots,
+                              msb_out, ld_msb, nullptr, nullptr, 0, st);
+}
+
+// plane: words between the three components' root planes (n_cols * ld_roots for a stand-alone
+// request; the pool's column count * ld_roots for a request occupying a range of a column pool).
+int or_finalize_strided(uint32_t* roots, size_t ld_roots, size_t plane, uint32_t n_blocks, uint32_t p, uint32_t Q,
+                        uint32_t R, const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares,
+                        cudaStream_t st) {
+  Seeds sd;
+  for (int j = 0; j < 3; ++j) sd.s[j] = seeds[j];
+  const uint32_t n_cols = Q * R;
+  or_rows_kernel<<<(n_cols + 127) / 128, 128, 0, st>>>(roots, ld_roots, plane, n_cols, n_blocks, p, col_tags, sd);
+  IPC_CUDA_TRY(cudaGetLastError());
+  or_queries_kernel<<<(Q + 63) / 64, 64, 0, st>>>(roots, ld_roots, plane, Q, R, col_tags, sd, bit_shares);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
 
 int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t p, uint32_t Q, uint32_t R,
                        const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares, cudaStream_t st) {
-  Seeds sd;
-  for (int j = 0; j < 3; ++j) sd.s[j] = seeds[j];
-  const uint32_t n_cols = Q * R;
-  or_rows_kernel<<<(n_cols + 127) / 128, 128, 0, st>>>(roots, ld_roots, n_cols, n_blocks, p, col_tags, sd);
-  IPC_CUDA_TRY(cudaGetLastError());
-  or_queries_kernel<<<(Q + 63) / 64, 64, 0, st>>>(roots, ld_roots, n_cols, Q, R, col_tags, sd, bit_shares);
-  IPC_CUDA_TRY(cudaGetLastError());
-  return IPC_OK;
+  return or_finalize_strided(roots, ld_roots, static_cast<size_t>(Q) * R * ld_roots, n_blocks, p, Q, R, col_tags, seeds,
+                             bit_shares, st);
 }
 
 }  // namespace ipc

@@ -6,68 +6,9 @@
 //   compare stream     : wait(all three parties), A4-A8 per comparison + in-block OR -> roots
 // then A8 (rest of the OR tree) and the copy of the three bit components to pinned host memory.
 // Queries are prepared once per request on the party streams (A2).
-#include <algorithm>
-#include <chrono>
-#include <cstring>
-#include <map>
-#include <string>
-#include <thread>
-#include <vector>
-
-#include "common.cuh"
-
-namespace ipc {
-const char* thread_last_error();
-}
+#include "context.cuh"
 
 using namespace ipc;
-
-namespace {
-
-constexpr uint32_t kLog2BlockWords = 5;  // 1024-row OR blocks inside ipc_compare
-
-struct Chunk {
-  uint8_t* planes = nullptr;  // 12 planes [cap][l] of limbs: ((component * 2 + vec) * 2 + limb)
-  size_t cap = 0;
-  size_t rows = 0;
-  uint64_t row0 = 0;
-};
-
-struct Request {
-  uint64_t id = 0;
-  uint32_t Q = 0, N = 0, n_pad = 0;
-  uint8_t* bq = nullptr;        // [party][vec][limb][n_pad][2l] limbs
-  uint16_t* qstage = nullptr;   // [vec][3][Q][l] query shares
-  uint32_t* tags = nullptr;     // [N][2]
-  uint32_t* roots = nullptr;    // [3][N][ld_roots]
-  size_t ld_roots = 0;
-  uint8_t* shares_dev = nullptr;  // [3][Q]
-  uint8_t* shares_host = nullptr; // pinned [3][Q]
-  uint16_t* zkeep = nullptr;      // [vec][party][N][rows] when distances are kept
-  size_t zkeep_rows = 0;
-  cudaEvent_t done = nullptr;
-};
-
-}  // namespace
-
-struct ipc_ctx {
-  ipc_config cfg{};
-  uint32_t l = 0;
-  uint32_t esz = 1;  // bytes per limb: int8, or bf16 for IPC_PATH_TC
-  cudaStream_t sp[3] = {nullptr, nullptr, nullptr};
-  cudaStream_t sc = nullptr;
-  cudaEvent_t ev_setup = nullptr, ev_gemm[3][2] = {}, ev_cmp[2] = {};
-  cudaEvent_t ev_input = nullptr;        // recorded on input_stream before reading caller device buffers
-  cudaStream_t input_stream = nullptr;   // stream whose earlier work produces device inputs (NULL = legacy)
-  std::vector<Chunk> chunks;
-  size_t rows = 0;
-  uint16_t* zbuf = nullptr;  // [2 sets][vec][party][zbuf_cols][chunk_rows]
-  size_t zbuf_cols = 0;
-  uint16_t* stage = nullptr;  // load staging [chunk_rows][l] u16
-  std::map<uint64_t, Request> reqs;
-  uint64_t next_id = 1;
-  std::string err;
-};
 
 namespace {
 
@@ -171,6 +112,15 @@ int check_device_status(ipc_ctx* c) {
 
 }  // namespace
 
+namespace ipc {
+int ctx_fail(ipc_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+int ctx_cfail(ipc_ctx* c, cudaError_t e, const char* what) { return cfail(c, e, what); }
+uint8_t* ctx_plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
+  return plane(c, ch, comp, vec, limb);
+}
+int ctx_check_device_status(ipc_ctx* c) { return check_device_status(c); }
+}  // namespace ipc
+
 extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   if (!cfg || !out) return fail(nullptr, IPC_EINVAL, "ipc_create: null argument");
   const ipc_geom& g = cfg->geom;
@@ -211,6 +161,7 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
 
 extern "C" void ipc_destroy(ipc_ctx* c) {
   if (!c) return;
+  serve_shutdown(c);
   cudaSetDevice(c->cfg.device);
   cudaDeviceSynchronize();
   for (auto& kv : c->reqs) free_request(c, kv.second);
@@ -245,6 +196,7 @@ extern "C" int ipc_set_input_stream(ipc_ctx* c, void* stream) {
 extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const mask[3],
                               size_t n_rows, int src_is_device) {
   if (!c || !code || !mask) return fail(c, IPC_EINVAL, "load_db_shares: null argument");
+  if (c->srv) return fail(c, IPC_EINVAL, "load_db_shares: the context is serving");
   for (int j = 0; j < 3; ++j)
     if (!code[j] || !mask[j]) return fail(c, IPC_EINVAL, "load_db_shares: null component");
   if (n_rows == 0) return IPC_OK;
@@ -315,6 +267,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   if (!c || !code || !mask || !req_id) return fail(c, IPC_EINVAL, "submit_queries: null argument");
   if (n_queries == 0 || n_queries > c->cfg.max_queries)
     return fail(c, IPC_EINVAL, "submit_queries: n_queries must be in 1..max_queries");
+  if (c->srv) return fail(c, IPC_EINVAL, "submit_queries: the context is serving; use ipc_serve_submit");
   if (c->rows == 0) return fail(c, IPC_EINVAL, "submit_queries: no database rows loaded");
   CTX_TRY(c, cudaSetDevice(c->cfg.device));
   const ipc_geom& g = c->cfg.geom;
@@ -324,7 +277,10 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   if (rc) return rc;
 
   Request r;
-  r.id = c->next_id;
+  {
+    std::lock_guard<std::mutex> lock(c->id_mu);
+    r.id = c->next_id++;
+  }
   r.Q = Q;
   r.N = N;
   r.n_pad = n_pad;
@@ -439,14 +395,16 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   CTX_TRY(c, cudaEventSynchronize(c->ev_setup));  // the tag vector above is a host temporary
   c->reqs[r.id] = r;
   *req_id = r.id;
-  ++c->next_id;
   return IPC_OK;
 }
 
 extern "C" int fetch_bit_shares(ipc_ctx* c, uint64_t req_id, uint8_t* shares_out, size_t n_queries, int timeout_ms) {
   if (!c || !shares_out) return fail(c, IPC_EINVAL, "fetch_bit_shares: null argument");
   auto it = c->reqs.find(req_id);
-  if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
+  if (it == c->reqs.end()) {
+    const int rc = serve_fetch_shares(c, req_id, shares_out, n_queries, timeout_ms);
+    return rc == IPC_ENOTFOUND ? fail(c, IPC_ENOTFOUND, "unknown request id") : rc;
+  }
   Request& r = it->second;
   if (n_queries != r.Q) return fail(c, IPC_EINVAL, "n_queries does not match the request");
   int rc = wait_event(c, r.done, timeout_ms);
@@ -497,7 +455,10 @@ extern "C" int fetch_distances(ipc_ctx* c, uint64_t req_id, uint32_t q, uint32_t
 extern "C" int ipc_release(ipc_ctx* c, uint64_t req_id) {
   if (!c) return fail(c, IPC_EINVAL, "ipc_release: null context");
   auto it = c->reqs.find(req_id);
-  if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
+  if (it == c->reqs.end()) {
+    const int rc = serve_release(c, req_id);
+    return rc == IPC_ENOTFOUND ? fail(c, IPC_ENOTFOUND, "unknown request id") : rc;
+  }
   cudaEventSynchronize(it->second.done);
   free_request(c, it->second);
   c->reqs.erase(it);

@@ -1,0 +1,77 @@
+// Internal state of a context, shared by context.cu (load, submit, fetch) and serve.cu (the
+// continuous-batching request loop).
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ipc {
+const char* thread_last_error();
+
+constexpr uint32_t kLog2BlockWords = 5;  // 1024-row OR blocks inside ipc_compare
+
+struct Chunk {
+  uint8_t* planes = nullptr;  // 12 planes [cap][l] of limbs: ((component * 2 + vec) * 2 + limb)
+  size_t cap = 0;
+  size_t rows = 0;
+  uint64_t row0 = 0;
+};
+
+struct Request {
+  uint64_t id = 0;
+  uint32_t Q = 0, N = 0, n_pad = 0;
+  uint8_t* bq = nullptr;        // [party][vec][limb][n_pad][2l] limbs
+  uint16_t* qstage = nullptr;   // [vec][3][Q][l] query shares
+  uint32_t* tags = nullptr;     // [N][2]
+  uint32_t* roots = nullptr;    // [3][N][ld_roots]
+  size_t ld_roots = 0;
+  uint8_t* shares_dev = nullptr;  // [3][Q]
+  uint8_t* shares_host = nullptr; // pinned [3][Q]
+  uint16_t* zkeep = nullptr;      // [vec][party][N][rows] when distances are kept
+  size_t zkeep_rows = 0;
+  cudaEvent_t done = nullptr;
+};
+
+struct Server;  // serve.cu
+
+// Context helpers defined in context.cu.
+int ctx_fail(ipc_ctx* c, int code, const std::string& msg);
+int ctx_cfail(ipc_ctx* c, cudaError_t e, const char* what);
+uint8_t* ctx_plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb);
+int ctx_check_device_status(ipc_ctx* c);
+
+// Serving hooks defined in serve.cu. serve_fetch_shares and serve_release return IPC_ENOTFOUND
+// for ids that are not serving requests.
+int serve_fetch_shares(ipc_ctx* c, uint64_t id, uint8_t* out, size_t n, int timeout_ms);
+int serve_release(ipc_ctx* c, uint64_t id);
+void serve_shutdown(ipc_ctx* c);
+}  // namespace ipc
+
+struct ipc_ctx {
+  ipc_config cfg{};
+  uint32_t l = 0;
+  uint32_t esz = 1;  // bytes per limb: int8, or bf16 for IPC_PATH_TC
+  cudaStream_t sp[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t sc = nullptr;
+  cudaEvent_t ev_setup = nullptr, ev_gemm[3][2] = {}, ev_cmp[2] = {};
+  cudaEvent_t ev_input = nullptr;        // recorded on input_stream before reading caller device buffers
+  cudaStream_t input_stream = nullptr;   // stream whose earlier work produces device inputs (NULL = legacy)
+  std::vector<ipc::Chunk> chunks;
+  size_t rows = 0;
+  uint16_t* zbuf = nullptr;  // [2 sets][vec][party][zbuf_cols][chunk_rows]
+  size_t zbuf_cols = 0;
+  uint16_t* stage = nullptr;  // load staging [chunk_rows][l] u16
+  std::map<uint64_t, ipc::Request> reqs;
+  uint64_t next_id = 1;
+  std::mutex id_mu;            // next_id, when the serving loop runs
+  ipc::Server* srv = nullptr;  // the serving loop, while one runs
+  std::string err;
+};

@@ -107,8 +107,8 @@ __global__ void split_limbs_kernel(const uint16_t* __restrict__ x, size_t count,
 // A2: one thread per output element of B_i (row n, position k of 2l). Limb type T: int8_t, or
 // uint16_t for the bf16 bit patterns of the same limbs.
 template <typename T>
-__global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint32_t Q, ipc_geom g, uint32_t party,
-                                  T* __restrict__ b_lo, T* __restrict__ b_hi, uint32_t n_pad) {
+__global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint64_t plane, uint32_t Q, ipc_geom g,
+                                  uint32_t party, T* __restrict__ b_lo, T* __restrict__ b_hi, uint32_t n_pad) {
   const uint32_t l = g.rows * g.cols * g.cell;
   const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   const uint64_t total = static_cast<uint64_t>(n_pad) * 2 * l;
@@ -124,7 +124,6 @@ __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint32_t Q, ip
     int32_t js = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
     if (js < 0) js += g.cols;
     const uint32_t src = (r * g.cols + static_cast<uint32_t>(js)) * g.cell + c;
-    const uint64_t plane = static_cast<uint64_t>(Q) * l;
     const uint32_t prev = (party + 2) % 3;
     const uint32_t yi = y[party * plane + static_cast<uint64_t>(q) * l + src];
     if (k < l) {
@@ -184,10 +183,11 @@ extern "C" int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8
   return IPC_OK;
 }
 
-namespace {
+namespace ipc {
+// y_plane: elements between the three components of y (Q * l when they are packed).
 template <typename T>
-int prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, T* b_lo, T* b_hi, uint32_t n_pad,
-               void* stream, const char* who) {
+int prep_query_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party, T* b_lo,
+                       T* b_hi, uint32_t n_pad, void* stream, const char* who) {
   if (!geom_ok(g) || party > 2 || !y || !b_lo || !b_hi || Q == 0 || static_cast<uint64_t>(Q) * g->R > n_pad) {
     set_error(std::string(who) + ": invalid geometry, party, or n_pad < Q*R");
     return IPC_EINVAL;
@@ -195,21 +195,31 @@ int prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party,
   const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
   const uint64_t total = static_cast<uint64_t>(n_pad) * 2 * l;
   const uint32_t bs = 256;
-  prep_query_kernel<T><<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(y, Q, *g, party,
-                                                                                                  b_lo, b_hi, n_pad);
+  if (y_plane < static_cast<uint64_t>(Q) * l) {
+    set_error(std::string(who) + ": component stride shorter than Q * l");
+    return IPC_EINVAL;
+  }
+  prep_query_kernel<T><<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+      y, y_plane, Q, *g, party, b_lo, b_hi, n_pad);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
-}  // namespace
+template int prep_query_strided<int8_t>(const uint16_t*, uint64_t, uint32_t, const ipc_geom*, uint32_t, int8_t*,
+                                        int8_t*, uint32_t, void*, const char*);
+template int prep_query_strided<uint16_t>(const uint16_t*, uint64_t, uint32_t, const ipc_geom*, uint32_t, uint16_t*,
+                                          uint16_t*, uint32_t, void*, const char*);
+}  // namespace ipc
 
 extern "C" int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
                               int8_t* b_hi, uint32_t n_pad, void* stream) {
-  return prep_query(y, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query");
+  const uint64_t l = g ? static_cast<uint64_t>(g->rows) * g->cols * g->cell : 0;
+  return prep_query_strided(y, Q * l, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query");
 }
 
 extern "C" int ipc_prep_query_bf16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
                                    uint16_t* b_hi, uint32_t n_pad, void* stream) {
-  return prep_query(y, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query_bf16");
+  const uint64_t l = g ? static_cast<uint64_t>(g->rows) * g->cols * g->cell : 0;
+  return prep_query_strided(y, Q * l, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query_bf16");
 }
 
 extern "C" int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* lo, uint16_t* hi, void* stream) {
