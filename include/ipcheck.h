@@ -177,9 +177,10 @@ int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], const int8_t* 
  * z as ipc_ring_gemm, with operands from ipc_split_limbs_bf16 and
  * ipc_prep_query_bf16 (bf16 bit patterns of the int8 limbs; x planes
  * [x_rows][l], b planes [n_pad][2l]). The products run as bf16 MMAs with fp32
- * accumulators in tensor memory; each accumulator restarts every 128 k at
- * 1.5 * 2^23, so all partial sums stay integers inside [2^23, 2^24] where fp32
- * addition is exact, and the result is bit-identical to the integer paths.
+ * accumulators in tensor memory; each accumulator is drained and restarts at
+ * 1.5 * 2^23 after at most 256 products, so all partial sums stay integers
+ * inside [2^23, 2^24], where fp32 addition is exact, and the result is
+ * bit-identical to the integer paths.
  * Arguments, alignment rules and errors as ipc_ring_gemm.
  */
 int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,

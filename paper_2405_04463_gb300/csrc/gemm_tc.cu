@@ -6,25 +6,28 @@
 // sm_103a has no integer tcgen05 kind, but the arithmetic stays exact on the bf16 kind:
 //   * every limb is an integer in [-128, 127], exactly a bf16 value;
 //   * every product is an integer with |p| <= 2^14, exact in fp32;
-//   * an accumulator starts each chunk of 128 k at M = 1.5 * 2^23 and receives at most 256
-//     products (C: two per k), so every partial sum, in any order or grouping, is an integer
-//     within M +- 2^22, i.e. in [2^23, 2^24], where consecutive fp32 values are 1 apart (2^24
-//     included): each addition is exact whatever its rounding;
+//   * an accumulator starts at M = 1.5 * 2^23 and is drained and reset to M after at most 256
+//     products (C every 128 k: two per k; L every 256 k), so every partial sum, in any order or
+//     grouping, is an integer within M +- 2^22, i.e. in [2^23, 2^24], where consecutive fp32
+//     values are 1 apart (2^24 included): each addition is exact whatever its rounding;
 //   * on [2^23, 2^24] the fp32 bit pattern of M + v is bits(M) + v, and bits(M) = 0x4B400000 is
 //     0 mod 2^16, so the raw bits of the two accumulators, added as integers (L + (C << 8)) over
 //     all chunks, give z - r mod 2^16 with no conversion instruction.
 //
-// Pipeline (one CTA per 128 database rows x 256 query columns, 10 warps):
+// Pipeline (one CTA per tile of 128 database rows x TN query columns, 10 warps):
 //   warp 0 lane 0  TMA producer: per k-block of 32 elements, four tiles (database lo/hi 128 x 32,
 //                  query lo/hi 256 x 32, 64-byte swizzle) into a 4-stage ring.
 //   warp 1 lane 0  MMA issuer: per chunk of four k-blocks, the C products (2 MMAs of 128x256x16
 //                  per 16 k) with the L products (1 MMA per 16 k) one k-block behind, committing
-//                  C-full after the last C k-block, stage-empty after each L k-block and L-full.
-//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 128 columns, their
+//                  C-full after the last C k-block, stage-empty after each L k-block, and L-full
+//                  after every second chunk.
+//   warps 2-9      drain: each thread owns one TMEM lane (database row) and TN/2 columns, their
 //                  running sums kept mod 2^16 two to a register; after C-full it reads C, adds
-//                  C << 8 to the sums and stores M back, then the same for L. C is drained while the L products run and L while the next
-//                  chunk's C products run, so the tensor pipe does not wait for the drain.
-// TMEM: L in columns [0, 256), C in [256, 512).
+//                  C << 8 to the sums and stores M back, and likewise for L after L-full. C is
+//                  drained while the chunk's last L products run, L while the next chunk's first
+//                  C products run, so the tensor pipe does not wait for the drain.
+// TMEM: L in columns [0, TN), C in [TN, 2 TN).
+// Tile widths TN = 256 (the fixed-shape launch) and 128; see gemm_tc_kernel for the list mode.
 // Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
 // status word, lets its copies and MMAs finish, frees its tensor memory and stores nothing.
 #include <cuda.h>
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                  done_bar = c_full + 32, epi_done = c_full + 40;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;
+  const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;  // even: l is a multiple of 128
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -336,9 +339,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         umma_commit(empty0 + 8 * s);  // stage free once these (and all earlier) MMAs are done
       };
+      // C restarts every chunk (128 k), L every other chunk (256 k): L gains at most 2^14 per
+      // k, C twice that, so both stay within 2^22 of the base between drains.
       const uint32_t total_chunks = my_items * n_chunks;
       for (uint32_t c = 0; c < total_chunks; ++c) {
         const uint32_t par = c & 1u, G0 = c * KB_PER_CHUNK;
+        const bool l_opens = (c & 1u) == 0, l_closes = (c & 1u) == 1;
         if (!mbar_wait(c_empty, par, p.status, abort)) break;
         fence_after();
         bool ok = true;
@@ -351,8 +357,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           fence_after();
           issue_c(tiles + s * STAGE_BYTES);
           if (kb == KB_PER_CHUNK - 1) umma_commit(c_full);
-          if (kb == 1) {
-            if (!mbar_wait(l_empty, par, p.status, abort)) {
+          if (kb == 1 && l_opens) {
+            if (!mbar_wait(l_empty, (c >> 1) & 1u, p.status, abort)) {
               ok = false;
               break;
             }
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!ok) break;
         issue_l(G0 + KB_PER_CHUNK - 1);
-        umma_commit(l_full);
+        if (l_closes) umma_commit(l_full);
       }
       // every MMA issued above completes before the tensor memory is freed
       umma_commit(done_bar);
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int k = 0; k < DCOLS / 2; ++k) z2[k] = 0;
       for (uint32_t cc = 0; cc < n_chunks; ++cc) {
-        const uint32_t par = (i * n_chunks + cc) & 1u;
+        const uint32_t gc = i * n_chunks + cc, par = gc & 1u;
         if (!__all_sync(0xFFFFFFFFu, mbar_wait(c_full, par, p.status, abort))) {
           ok = false;
           break;
@@ -412,7 +418,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(c_empty);
-        if (!__all_sync(0xFFFFFFFFu, mbar_wait(l_full, par, p.status, abort))) {
+        if ((gc & 1u) == 0) continue;  // L closes every other chunk
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(l_full, (gc >> 1) & 1u, p.status, abort))) {
           ok = false;
           break;
         }
