@@ -115,6 +115,15 @@ def _declare(L):
     L.orc_mpc_compare.argtypes = [C, _p(u16), _p(u16), u32, u32, u32, _p(u8), _p(u32), _p(u32), S]
     L.orc_bit_extract.argtypes = [C, _p(u32), u32, u32, u32, u32, u32, _p(u8), _p(u8), S]
     L.orc_or_tree.argtypes = [C, _p(u8), u32, u32, u32, _p(u8), S]
+    L.orc_gr_mul.argtypes = [_p(u16), _p(u16), _p(u16)]
+    L.orc_gr_inv.argtypes = [_p(u16), _p(u16)]
+    L.orc_gr_inv.restype = ctypes.c_int
+    L.orc_gr_points.argtypes = [_p(u16)]
+    L.orc_gr_lagrange.argtypes = [_p(u16)]
+    L.orc_encode_share_galois.argtypes = [_p(u64), _p(u64), u32, u32, u64, u32, u32, _p(u16), _p(u16)]
+    L.orc_mpc_dot_galois.argtypes = [C, _p(u16), u64, _p(u16), u64, u32, u32, u32, u32, u32, _p(u16), S]
+    L.orc_mpc_match_galois.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
+                                       _p(u16), _p(u16), _p(u8), _p(u8), S]
     L.orc_mpc_match.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
                                 _p(u16), _p(u16), _p(u8), _p(u8), S]
     for f in ("orc_philox4x32_10", "orc_rotate_u16", "orc_rotate_bits", "orc_encode_share", "orc_plain_pair",
@@ -248,6 +257,10 @@ def mpc_match(cfg: MpcCfg, g: Geom, db_code, db_mask, q_code, q_mask, want_z: bo
               want_msb: bool = False):
     """Alg. 3 for all queries. Shares are [3][n][l] u16. Returns a dict with bits[3][Q]
     (and z_code/z_mask [3][Q*R][s], msb [3][Q*R][s] when asked) plus stats."""
+    return _mpc_match(lib().orc_mpc_match, cfg, g, db_code, db_mask, q_code, q_mask, want_z, want_msb)
+
+
+def _mpc_match(fn, cfg, g, db_code, db_mask, q_code, q_mask, want_z, want_msb):
     db_code = np.ascontiguousarray(db_code, dtype=np.uint16)
     db_mask = np.ascontiguousarray(db_mask, dtype=np.uint16)
     q_code = np.ascontiguousarray(q_code, dtype=np.uint16)
@@ -260,11 +273,72 @@ def mpc_match(cfg: MpcCfg, g: Geom, db_code, db_mask, q_code, q_mask, want_z: bo
     msb = np.zeros((3, n, s), np.uint8) if want_msb else None
     bits = np.zeros((3, Q), np.uint8)
     st = Stats()
-    lib().orc_mpc_match(ctypes.byref(cfg), ctypes.byref(g), _ptr(db_code, ctypes.c_uint16),
-                        _ptr(db_mask, ctypes.c_uint16), s, _ptr(q_code, ctypes.c_uint16),
-                        _ptr(q_mask, ctypes.c_uint16), Q, _ptr(zc, ctypes.c_uint16), _ptr(zm, ctypes.c_uint16),
-                        _ptr(msb, ctypes.c_uint8), _ptr(bits, ctypes.c_uint8), ctypes.byref(st))
+    fn(ctypes.byref(cfg), ctypes.byref(g), _ptr(db_code, ctypes.c_uint16), _ptr(db_mask, ctypes.c_uint16), s,
+       _ptr(q_code, ctypes.c_uint16), _ptr(q_mask, ctypes.c_uint16), Q, _ptr(zc, ctypes.c_uint16),
+       _ptr(zm, ctypes.c_uint16), _ptr(msb, ctypes.c_uint8), _ptr(bits, ctypes.c_uint8), ctypes.byref(st))
     return {"bits": bits, "z_code": zc, "z_mask": zm, "msb": msb, "stats": st.as_dict()}
+
+
+# ---- Galois-ring Shamir dot products (Sec. 4.3.2): GR = Z_{2^16}[X]/(X^2 - X - 1) ----
+
+def gr_mul(a, b) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    b = np.ascontiguousarray(b, dtype=np.uint16)
+    out = np.zeros(2, np.uint16)
+    lib().orc_gr_mul(_ptr(a, ctypes.c_uint16), _ptr(b, ctypes.c_uint16), _ptr(out, ctypes.c_uint16))
+    return out
+
+
+def gr_inv(a):
+    """a^-1, or None if a is not a unit of GR."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    out = np.zeros(2, np.uint16)
+    ok = lib().orc_gr_inv(_ptr(a, ctypes.c_uint16), _ptr(out, ctypes.c_uint16))
+    return out if ok else None
+
+
+def gr_points() -> np.ndarray:
+    out = np.zeros(6, np.uint16)
+    lib().orc_gr_points(_ptr(out, ctypes.c_uint16))
+    return out.reshape(3, 2)
+
+
+def gr_lagrange() -> np.ndarray:
+    out = np.zeros(6, np.uint16)
+    lib().orc_gr_lagrange(_ptr(out, ctypes.c_uint16))
+    return out.reshape(3, 2)
+
+
+def encode_share_galois(code_bits, mask_bits, l: int, client_seed: int, side: int, idx0: int = 0):
+    """Masked-bit encoding and Galois-ring Shamir sharing (degree 1) of packed rows; returns the
+    three parties' code and mask shares [3][n][l] u16 (element e's coefficients at 2e, 2e+1)."""
+    cb = np.ascontiguousarray(code_bits, dtype=np.uint64)
+    mb = np.ascontiguousarray(mask_bits, dtype=np.uint64)
+    n = cb.shape[0]
+    code = np.empty((3, n, l), np.uint16)
+    mask = np.empty((3, n, l), np.uint16)
+    lib().orc_encode_share_galois(_ptr(cb, ctypes.c_uint64), _ptr(mb, ctypes.c_uint64), n, l,
+                                  client_seed & 0xFFFFFFFFFFFFFFFF, side, idx0,
+                                  _ptr(code, ctypes.c_uint16), _ptr(mask, ctypes.c_uint16))
+    return code, mask
+
+
+def mpc_dot_galois(cfg: MpcCfg, x, y, q: int, rho: int, i: int, vec: int, stats: Stats | None = None):
+    """Galois-ring Shamir dot of DB shares x[3][l] with rotated query shares y[3][l] -> z[3]."""
+    x = np.ascontiguousarray(x, dtype=np.uint16)
+    y = np.ascontiguousarray(y, dtype=np.uint16)
+    l = x.shape[-1]
+    z = np.zeros(3, np.uint16)
+    st = stats if stats is not None else Stats()
+    lib().orc_mpc_dot_galois(ctypes.byref(cfg), _ptr(x, ctypes.c_uint16), l, _ptr(y, ctypes.c_uint16), l, l,
+                             q, rho, i, vec, _ptr(z, ctypes.c_uint16), ctypes.byref(st))
+    return z
+
+
+def mpc_match_galois(cfg: MpcCfg, g: Geom, db_code, db_mask, q_code, q_mask, want_z: bool = False,
+                     want_msb: bool = False):
+    """mpc_match with the dot products on Galois-ring Shamir shares (encode_share_galois)."""
+    return _mpc_match(lib().orc_mpc_match_galois, cfg, g, db_code, db_mask, q_code, q_mask, want_z, want_msb)
 
 
 def reconstruct_u16(shares) -> np.ndarray:

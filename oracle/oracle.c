@@ -572,11 +572,14 @@ void orc_or_tree(const orc_mpc_cfg* cfg, const uint8_t* msb, uint32_t R, uint32_
   free(rot);
 }
 
-void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
-                   const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
-                   const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
-                   uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
-                   orc_stats* st) {
+typedef void (*dot_fn)(const orc_mpc_cfg*, const uint16_t*, uint64_t, const uint16_t*, uint64_t, uint32_t,
+                       uint32_t, uint32_t, uint32_t, uint32_t, uint16_t[3], orc_stats*);
+
+static void mpc_match_with(dot_fn dot, const orc_mpc_cfg* cfg, const orc_geom* g,
+                           const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
+                           const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
+                           uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
+                           orc_stats* st) {
   uint32_t l = g->rows * g->cols * g->cell;
   uint32_t R = g->R;
   uint64_t db_plane = (uint64_t)s * l, q_plane = (uint64_t)Q * l;
@@ -595,8 +598,8 @@ void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
       size_t n = (size_t)q * R + rho;
       for (uint32_t i = 0; i < s; i++) {
         uint16_t zc[3], zm[3];
-        orc_mpc_dot(cfg, db_code + (size_t)i * l, db_plane, ry, l, l, q, rho, i, 0, zc, st);
-        orc_mpc_dot(cfg, db_mask + (size_t)i * l, db_plane, ry + (size_t)3 * l, l, l, q, rho, i, 1, zm, st);
+        dot(cfg, db_code + (size_t)i * l, db_plane, ry, l, l, q, rho, i, 0, zc, st);
+        dot(cfg, db_mask + (size_t)i * l, db_plane, ry + (size_t)3 * l, l, l, q, rho, i, 1, zm, st);
         if (z_code)
           for (int p = 0; p < 3; p++) z_code[p * zplane + n * s + i] = zc[p];
         if (z_mask)
@@ -616,4 +619,141 @@ void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
   }
   free(ry);
   free(msb);
+}
+
+void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
+                   const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
+                   const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
+                   uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
+                   orc_stats* st) {
+  mpc_match_with(orc_mpc_dot, cfg, g, db_code, db_mask, s, q_code, q_mask, Q, z_code, z_mask, msb_out, bits, st);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Galois-ring Shamir dot products (Sec. 4.3.2). GR = Z_{2^16}[X]/(X^2-X-1):  */
+/* X^2 = X + 1, so                                                            */
+/*   (a0 + a1 X)(b0 + b1 X) = (a0 b0 + a1 b1) + (a0 b1 + a1 b0 + a1 b1) X.   */
+/* ------------------------------------------------------------------------ */
+void orc_gr_mul(const uint16_t a[2], const uint16_t b[2], uint16_t out[2]) {
+  uint32_t a0 = a[0], a1 = a[1], b0 = b[0], b1 = b[1];
+  uint32_t x2 = a1 * b1; /* the X^2 term, folded into both coefficients */
+  out[0] = (uint16_t)(a0 * b0 + x2);
+  out[1] = (uint16_t)(a0 * b1 + a1 * b0 + x2);
+}
+
+/* Inverse of an odd n modulo 2^16 by Newton's iteration x <- x (2 - n x), which doubles the
+ * number of correct low bits; x = n is right to 3 bits since n^2 = 1 (mod 8) for odd n. */
+static uint16_t inv_odd16(uint16_t n) {
+  uint32_t x = n;
+  for (int it = 0; it < 4; it++) x = x * (2u - n * x);
+  return (uint16_t)x;
+}
+
+/* The conjugate maps X to the other root 1 - X of X^2 - X - 1; a * conj(a) is the norm
+ * N = a0^2 + a0 a1 - a1^2 in Z_{2^16}, and a is a unit iff N is (i.e. N odd). */
+int orc_gr_inv(const uint16_t a[2], uint16_t out[2]) {
+  uint16_t conj[2] = {(uint16_t)(a[0] + a[1]), (uint16_t)(0u - a[1])};
+  uint16_t nrm[2];
+  orc_gr_mul(a, conj, nrm);
+  if (nrm[1] != 0 || (nrm[0] & 1u) == 0) return 0;
+  uint16_t ninv[2] = {inv_odd16(nrm[0]), 0};
+  orc_gr_mul(conj, ninv, out);
+  return 1;
+}
+
+static void gr_sub(const uint16_t a[2], const uint16_t b[2], uint16_t out[2]) {
+  out[0] = (uint16_t)(a[0] - b[0]);
+  out[1] = (uint16_t)(a[1] - b[1]);
+}
+
+void orc_gr_points(uint16_t alpha[6]) {
+  alpha[0] = 1; alpha[1] = 0; /* 1     */
+  alpha[2] = 0; alpha[3] = 1; /* X     */
+  alpha[4] = 1; alpha[5] = 1; /* 1 + X */
+}
+
+/* lambda_p = prod_{j != p} alpha_j / (alpha_j - alpha_p) */
+void orc_gr_lagrange(uint16_t lambda[6]) {
+  uint16_t alpha[6];
+  orc_gr_points(alpha);
+  for (int p = 0; p < 3; p++) {
+    uint16_t acc[2] = {1, 0};
+    for (int j = 0; j < 3; j++) {
+      if (j == p) continue;
+      uint16_t diff[2], inv[2], t[2];
+      gr_sub(alpha + 2 * j, alpha + 2 * p, diff);
+      if (!orc_gr_inv(diff, inv)) abort(); /* the points are exceptional: differences are units */
+      orc_gr_mul(alpha + 2 * j, inv, t);
+      orc_gr_mul(acc, t, acc);
+    }
+    lambda[2 * p] = acc[0];
+    lambda[2 * p + 1] = acc[1];
+  }
+}
+
+void orc_encode_share_galois(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                             uint64_t client_seed, uint32_t side, uint32_t idx0,
+                             uint16_t* code_sh, uint16_t* mask_sh) {
+  uint32_t nw = (l + 63) / 64;
+  size_t plane = (size_t)n * l;
+  uint16_t alpha[6];
+  orc_gr_points(alpha);
+  for (uint32_t r = 0; r < n; r++) {
+    const uint64_t* c = code_bits + (size_t)r * nw;
+    const uint64_t* m = mask_bits + (size_t)r * nw;
+    uint32_t w[2][4];
+    for (uint32_t e = 0; 2 * e < l; e++) {
+      uint16_t val[2][2]; /* [vec][coefficient]: bits 2e and 2e+1 */
+      for (uint32_t t = 0; t < 2; t++) {
+        int cb = get_bit(c, 2 * e + t), mb = get_bit(m, 2 * e + t);
+        val[0][t] = (uint16_t)(mb - 2 * (cb & mb)); /* masked bit (Sec. 4.1.1) */
+        val[1][t] = (uint16_t)mb;
+      }
+      if ((e & 3u) == 0)
+        for (uint32_t vec = 0; vec < 2; vec++)
+          prf(client_seed, e >> 2, idx0 + r, (side << 8) | vec, ORC_D_GSHARE << 24, w[vec]);
+      for (uint32_t vec = 0; vec < 2; vec++) {
+        uint16_t rnd[2] = {(uint16_t)(w[vec][e & 3] & 0xFFFFu), (uint16_t)(w[vec][e & 3] >> 16)};
+        uint16_t* dst = vec == 0 ? code_sh : mask_sh;
+        for (int p = 0; p < 3; p++) {
+          uint16_t ra[2]; /* share_p = g + r alpha_p */
+          orc_gr_mul(rnd, alpha + 2 * p, ra);
+          size_t at = (size_t)p * plane + (size_t)r * l + 2 * e;
+          dst[at] = (uint16_t)(val[vec][0] + ra[0]);
+          dst[at + 1] = (uint16_t)(val[vec][1] + ra[1]);
+        }
+      }
+    }
+  }
+}
+
+void orc_mpc_dot_galois(const orc_mpc_cfg* cfg, const uint16_t* x, uint64_t x_stride,
+                        const uint16_t* y, uint64_t y_stride, uint32_t l,
+                        uint32_t q, uint32_t rho, uint32_t i, uint32_t vec, uint16_t z[3], orc_stats* st) {
+  uint16_t lambda[6];
+  orc_gr_lagrange(lambda);
+  for (int p = 0; p < 3; p++) {
+    const uint16_t* xp = x + (size_t)p * x_stride;
+    const uint16_t* yp = y + (size_t)p * y_stride;
+    uint32_t acc = 0;
+    for (uint32_t e = 0; 2 * e < l; e++) {
+      uint16_t a[2], prod[2];
+      orc_gr_mul(lambda + 2 * p, yp + 2 * e, a); /* the query share times lambda_p */
+      orc_gr_mul(a, xp + 2 * e, prod);           /* its product with the DB share: keep the constant term */
+      acc += prod[0];
+    }
+    uint32_t r = za_value(cfg->seeds[p], cfg->req, q, rho, i, vec) - za_value(cfg->seeds[P(p - 1)], cfg->req, q, rho, i, vec);
+    z[p] = (uint16_t)(acc + r);
+    if (st) st->bits_sent[p] += 16; /* resharing: z_p to party p+1 */
+  }
+}
+
+void orc_mpc_match_galois(const orc_mpc_cfg* cfg, const orc_geom* g,
+                          const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
+                          const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
+                          uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
+                          orc_stats* st) {
+  if (g->cell % 2 != 0) abort(); /* element pairs must not straddle rotated cells */
+  mpc_match_with(orc_mpc_dot_galois, cfg, g, db_code, db_mask, s, q_code, q_mask, Q, z_code, z_mask, msb_out, bits,
+                 st);
 }

@@ -34,6 +34,7 @@ extern "C" {
 #define ORC_D_INJ0  4u /* BitInject c_0 (seed_0)                                       */
 #define ORC_D_INJ2  5u /* BitInject c_2, w_0, w_1 (seed_2)                             */
 #define ORC_D_OR    6u /* boolean zero shares of the OR-tree AND gates                 */
+#define ORC_D_GSHARE 7u /* client randomness of the Galois-ring Shamir sharing        */
 
 /* Gate numbering of the comparison circuit (D_AND counter). */
 #define ORC_LIFT_GATE0 0u  /* 33 gates of BitExtract(.,{17,16}) inside Lift      */
@@ -126,6 +127,39 @@ void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
                    const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
                    uint16_t* z_code, uint16_t* z_mask, uint8_t* msb, uint8_t* bits,
                    orc_stats* st);
+
+/* ---- Galois-ring Shamir dot products (Sec. 4.3.2, Shamir sharing over Galois rings) ----
+ * GR = Z_{2^16}[X]/(X^2 - X - 1); an element c0 + c1 X is stored as uint16_t[2] = {c0, c1}.
+ * Two consecutive code (or mask) bits 2e, 2e+1 form one element, so a share vector of l
+ * coefficients keeps the bit layout: coefficient t of element e sits at index 2e + t. */
+void orc_gr_mul(const uint16_t a[2], const uint16_t b[2], uint16_t out[2]);
+/* Returns 1 and writes a^-1 if a is a unit of GR, else returns 0. */
+int orc_gr_inv(const uint16_t a[2], uint16_t out[2]);
+/* Evaluation points of parties 0, 1, 2 (reading: the non-zero elements of the exceptional
+ * set {0, 1, X, 1+X}; the secret sits at 0): alpha = [3][2]. */
+void orc_gr_points(uint16_t alpha[6]);
+/* Lagrange coefficients at 0 for the three points, degree <= 2: lambda = [3][2]. */
+void orc_gr_lagrange(uint16_t lambda[6]);
+/* Client sharing: each element g is shared with the degree-1 polynomial g + r Y, party p
+ * holding g + r alpha_p; r from Philox(client_seed, (e >> 2, idx0 + row, side<<8 | vec,
+ * D_GSHARE << 24)), word e & 3 (c0 = low half, c1 = high half). Output [3][n][l] u16, the
+ * three parties' shares, for the masked code bits and for the mask bits. */
+void orc_encode_share_galois(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                             uint64_t client_seed, uint32_t side, uint32_t idx0,
+                             uint16_t* code_sh, uint16_t* mask_sh);
+/* Party p's share of the dot product of DB row x (party shares [3][l]) with the rotated
+ * query y (party shares [3][l]): the constant term of sum_e (lambda_p y_p[e]) x_p[e], then the
+ * D_ZA zero share of (q, rho, i, vec) as in orc_mpc_dot. z: the three additive components. */
+void orc_mpc_dot_galois(const orc_mpc_cfg* cfg, const uint16_t* x, uint64_t x_stride,
+                        const uint16_t* y, uint64_t y_stride, uint32_t l,
+                        uint32_t q, uint32_t rho, uint32_t i, uint32_t vec, uint16_t z[3], orc_stats* st);
+/* orc_mpc_match with the dot products on Galois-ring Shamir shares (inputs from
+ * orc_encode_share_galois); the comparison phase and OR tree are unchanged. */
+void orc_mpc_match_galois(const orc_mpc_cfg* cfg, const orc_geom* g,
+                          const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
+                          const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
+                          uint16_t* z_code, uint16_t* z_mask, uint8_t* msb, uint8_t* bits,
+                          orc_stats* st);
 
 #ifdef __cplusplus
 }
