@@ -58,6 +58,7 @@ extern "C" {
 #define IPC_PATH_I32 1    /* plain int32 CUDA-core ring GEMM (IMAD) */
 #define IPC_PATH_I8MIX 2  /* int8 limb GEMM split between mma.sync s8 and dp4a in every tile */
 #define IPC_PATH_TC 3     /* the same limbs as bf16 on tcgen05 (TMEM accumulators, exact) */
+#define IPC_PATH_TCG 4    /* tcgen05, dot products on Galois-ring Shamir shares (Sec. 4.3.2) */
 
 /* PRF domains: high byte of Philox counter word 3. */
 #define IPC_D_SHARE 1u
@@ -66,6 +67,7 @@ extern "C" {
 #define IPC_D_INJ0 4u
 #define IPC_D_INJ2 5u
 #define IPC_D_OR 6u
+#define IPC_D_GSHARE 7u /* client randomness of the Galois-ring Shamir sharing */
 
 typedef struct {
   uint32_t rows, cols, cell; /* code geometry; l = rows*cols*cell, a multiple of 128 */
@@ -125,6 +127,32 @@ int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t pa
 /* A2 for IPC_PATH_TC: as ipc_prep_query, limbs written as bf16 bit patterns. */
 int ipc_prep_query_bf16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
                         uint16_t* b_hi, uint32_t n_pad, void* stream);
+
+/*
+ * A0 and A2 for Galois-ring Shamir dot products (Sec. 4.3.2; IPC_PATH_TCG).
+ * GR = Z_{2^16}[X]/(X^2 - X - 1). Bits 2e, 2e+1 of a code (or mask) form the element
+ * g_e = v_{2e} + v_{2e+1} X (v the masked bit or mask bit as in ipc_encode_share), shared
+ * with the degree-1 polynomial g_e + r_e Y: party p receives g_e + r_e alpha_p with
+ * alpha = (1, X, 1 + X); r_e = (low, high half of word e & 3 of Philox(client_seed,
+ * (e >> 2, idx0 + row, side<<8 | vec, IPC_D_GSHARE<<24))). Shares are stored with element e's
+ * coefficients at indices 2e, 2e+1, so a share vector has the bit layout; code_sh, mask_sh:
+ * [3][n][l] uint16, party-major. l must be a multiple of 8.
+ */
+int ipc_encode_share_galois(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                            uint64_t client_seed, uint32_t side, uint32_t idx0, uint16_t* code_sh,
+                            uint16_t* mask_sh, void* stream);
+
+/*
+ * Party p's query operand for Galois-ring shares: B[n][k] (K = l, bf16 limbs as in
+ * ipc_prep_query_bf16) holds coefficient k & 1 of lambda_p * y_p[e] for the element e that
+ * rotation rho = n % R brings to position k / 2, lambda_p the Lagrange coefficient at 0 of
+ * party p's point for polynomials of degree <= 2. Then the constant term of the product with
+ * party p's database share, summed over elements, is sum_k B[n][k] * x_p[k]: a plain dot
+ * product of length l, whose three party components add up to the masked dot product.
+ * y: [3][Q][l] the parties' query shares. Errors as ipc_prep_query; the cell size must be even.
+ */
+int ipc_prep_query_galois(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
+                          uint16_t* b_hi, uint32_t n_pad, void* stream);
 
 /*
  * A3 -- share-domain dot products of one party for one vector (App. C), as a
@@ -201,6 +229,19 @@ int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const x_lo[2], co
                            uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
                            uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                            const uint32_t* col_tiles, const uint32_t* n_col_list, void* stream);
+
+/*
+ * A3 for Galois-ring Shamir shares (IPC_PATH_TCG): party p's GEMM over its own database
+ * share only, K = l: z[n][r] = sum_k B[n][k] x_p[r][k] + r_p(n, r) (mod 2^16), with B from
+ * ipc_prep_query_galois and r_p the zero share of ipc_ring_gemm. x_lo, x_hi: bf16 limb planes
+ * [x_rows][l] of party p's share. l must be a multiple of 256. tile_cols, col_tiles and
+ * n_col_list as in ipc_ring_gemm_tc_tiles. Other arguments and errors as ipc_ring_gemm_tc.
+ */
+int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const uint16_t* x_lo, const uint16_t* x_hi, size_t x_rows,
+                            const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                            const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
+                            uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
+                            const uint32_t* n_col_list, void* stream);
 
 /*
  * A4-A8 (per comparison, and the OR tree inside aligned row blocks).
@@ -283,7 +324,9 @@ typedef struct ipc_ctx ipc_ctx;
 typedef struct {
   ipc_geom geom;            /* {16, 200, 4, -15, 31} for the deployed system */
   uint32_t thr_a;           /* a of the threshold a/b with b = 2^16; 16384 for MATCH_RATIO 0.375 */
-  int32_t path;             /* IPC_PATH_I8MMA, IPC_PATH_I8MIX, IPC_PATH_I32 or IPC_PATH_TC */
+  int32_t path;             /* IPC_PATH_I8MMA, IPC_PATH_I8MIX, IPC_PATH_I32, IPC_PATH_TC or IPC_PATH_TCG
+                               (TCG: load_db_shares and submit_queries take the three parties'
+                               Galois-ring Shamir shares from ipc_encode_share_galois) */
   uint32_t db_chunk_rows;   /* rows per resident chunk and pipeline step; multiple of 1024; 0 = 65536 */
   uint32_t max_queries;     /* largest request accepted by submit_queries; 0 = 256 */
   uint64_t seeds[3];        /* pairwise PRF seeds; seeds[j] shared by parties j and j+1 */

@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_PKG, "libipcheck.so")
 
 IPC_OK, IPC_EINVAL, IPC_ENOMEM, IPC_ECUDA, IPC_ETIMEOUT = 0, -1, -2, -3, -4
 IPC_EAGAIN, IPC_ENOTFOUND, IPC_EDEVICE, IPC_ENOSYS = -5, -6, -7, -8
-IPC_PATH_I8MMA, IPC_PATH_I32, IPC_PATH_I8MIX, IPC_PATH_TC = 0, 1, 2, 3
-PATHS = {"i8mma": IPC_PATH_I8MMA, "i32": IPC_PATH_I32, "i8mix": IPC_PATH_I8MIX, "tc": IPC_PATH_TC}
+IPC_PATH_I8MMA, IPC_PATH_I32, IPC_PATH_I8MIX, IPC_PATH_TC, IPC_PATH_TCG = 0, 1, 2, 3, 4
+PATHS = {"i8mma": IPC_PATH_I8MMA, "i32": IPC_PATH_I32, "i8mix": IPC_PATH_I8MIX, "tc": IPC_PATH_TC,
+         "tcg": IPC_PATH_TCG}
 
 
 class IpcError(RuntimeError):
@@ -80,6 +81,10 @@ _SIGS = {
     "ipc_split_limbs": [_vp, _sz, _vp, _vp, _vp],
     "ipc_prep_query": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_split_limbs_bf16": [_vp, _sz, _vp, _vp, _vp],
+    "ipc_encode_share_galois": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
+    "ipc_prep_query_galois": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
+    "ipc_ring_gemm_tc_galois": [_u32, _vp, _vp, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
+                                _u64, _vp, _vp, _vp],
     "ipc_prep_query_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_ring_gemm_tc": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
     "ipc_ring_gemm_tc_tiles": [_u32, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
@@ -189,6 +194,23 @@ def ipc_split_limbs_bf16(x, count, lo, hi, stream=None):
 def ipc_prep_query_bf16(y, Q, geom: ipc_geom, party, b_lo, b_hi, n_pad, stream=None):
     _check(lib.ipc_prep_query_bf16(ptr(y), Q, ctypes.byref(geom), party, ptr(b_lo), ptr(b_hi), n_pad,
                                    _stream(stream)))
+
+
+def ipc_encode_share_galois(code_bits, mask_bits, n, l, client_seed, side, idx0, code_sh, mask_sh, stream=None):
+    _check(lib.ipc_encode_share_galois(ptr(code_bits), ptr(mask_bits), n, l, client_seed & (2**64 - 1), side, idx0,
+                                       ptr(code_sh), ptr(mask_sh), _stream(stream)))
+
+
+def ipc_prep_query_galois(y, Q, geom: ipc_geom, party, b_lo, b_hi, n_pad, stream=None):
+    _check(lib.ipc_prep_query_galois(ptr(y), Q, ctypes.byref(geom), party, ptr(b_lo), ptr(b_hi), n_pad,
+                                     _stream(stream)))
+
+
+def ipc_ring_gemm_tc_galois(tile_cols, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+                            seed_prev, vec, z, ldz, row0, col_tiles=None, n_col_list=None, stream=None):
+    _check(lib.ipc_ring_gemm_tc_galois(tile_cols, ptr(x_lo), ptr(x_hi), x_rows, ptr(b_lo), ptr(b_hi), n_cols, n_pad, l,
+                                       ptr(col_tags), seed_own & (2**64 - 1), seed_prev & (2**64 - 1), vec, ptr(z),
+                                       ldz, row0, ptr(col_tiles), ptr(n_col_list), _stream(stream)))
 
 
 def ipc_ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,

@@ -26,11 +26,11 @@ int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], s
                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream);
-int ring_gemm_tc_variant(uint32_t tile_cols, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2],
-                         size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
-                         uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
-                         uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
-                         const uint32_t* n_col_list, cudaStream_t stream);
+int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* const x_lo[2],
+                         const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
+                         uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                         uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                         const uint32_t* col_tiles, const uint32_t* n_col_list, cudaStream_t stream);
 const char* thread_last_error();
 
 namespace {
@@ -150,7 +150,26 @@ extern "C" int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const 
   if ((col_tiles == nullptr) != (n_col_list == nullptr))
     return bad("ipc_ring_gemm_tc_tiles: col_tiles and n_col_list go together");
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
-  return ring_gemm_tc_variant(tile_cols, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+  return ring_gemm_tc_variant(tile_cols, 2, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+                              seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
+}
+
+extern "C" int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const uint16_t* x_lo, const uint16_t* x_hi, size_t x_rows,
+                                       const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
+                                       uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
+                                       uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                                       const uint32_t* col_tiles, const uint32_t* n_col_list, void* stream) {
+  const uint16_t* xl[2] = {x_lo, x_lo};
+  const uint16_t* xh[2] = {x_hi, x_hi};
+  int rc = check_tc_args(xl, xh, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                         "ipc_ring_gemm_tc_galois");
+  if (rc) return rc;
+  if (l % 256 != 0) return bad("ipc_ring_gemm_tc_galois: l must be a multiple of 256");
+  if (tile_cols != 128 && tile_cols != 256) return bad("ipc_ring_gemm_tc_galois: tile_cols must be 128 or 256");
+  if ((col_tiles == nullptr) != (n_col_list == nullptr))
+    return bad("ipc_ring_gemm_tc_galois: col_tiles and n_col_list go together");
+  if (x_rows == 0 || n_cols == 0) return IPC_OK;
+  return ring_gemm_tc_variant(tile_cols, 1, xl, xh, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
 }
 

@@ -128,15 +128,18 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   if (l == 0 || l % 128 != 0 || l > 16384 || g.R == 0 || g.R > 31)
     return fail(nullptr, IPC_EINVAL, "ipc_create: l must be a multiple of 128 up to 16384 and 1 <= R <= 31");
   if (cfg->path != IPC_PATH_I8MMA && cfg->path != IPC_PATH_I32 && cfg->path != IPC_PATH_I8MIX &&
-      cfg->path != IPC_PATH_TC)
+      cfg->path != IPC_PATH_TC && cfg->path != IPC_PATH_TCG)
     return fail(nullptr, IPC_EINVAL, "ipc_create: path");
+  if (cfg->path == IPC_PATH_TCG && (l % 256 != 0 || g.cell % 2 != 0))
+    return fail(nullptr, IPC_EINVAL, "ipc_create: Galois-ring shares need l % 256 == 0 and an even cell size");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
   ipc_ctx* c = new ipc_ctx();
   c->cfg = *cfg;
   if (c->cfg.db_chunk_rows == 0) c->cfg.db_chunk_rows = 65536;
   if (c->cfg.max_queries == 0) c->cfg.max_queries = 256;
   c->l = static_cast<uint32_t>(l);
-  c->esz = cfg->path == IPC_PATH_TC ? 2 : 1;
+  c->esz = (cfg->path == IPC_PATH_TC || cfg->path == IPC_PATH_TCG) ? 2 : 1;
+  c->kq = cfg->path == IPC_PATH_TCG ? c->l : 2 * c->l;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete c;
@@ -286,7 +289,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   r.n_pad = n_pad;
   const size_t total_blocks = (c->chunks.size() * c->cfg.db_chunk_rows) >> (5 + kLog2BlockWords);
   r.ld_roots = total_blocks;
-  bool ok = cudaMalloc(&r.bq, 12ull * n_pad * 2 * l * c->esz) == cudaSuccess &&
+  bool ok = cudaMalloc(&r.bq, 12ull * n_pad * c->kq * c->esz) == cudaSuccess &&
             cudaMalloc(&r.qstage, 2ull * 3 * Q * l * sizeof(uint16_t)) == cudaSuccess &&
             cudaMalloc(&r.tags, 2ull * N * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&r.roots, 3ull * N * r.ld_roots * sizeof(uint32_t)) == cudaSuccess &&
@@ -324,13 +327,17 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
                                  static_cast<size_t>(Q) * l * sizeof(uint16_t), kind, c->sc));
   CTX_TRY(c, cudaEventRecord(c->ev_setup, c->sc));
   // the host tags vector dies at return: make the copy complete before that
-  const size_t qplane = static_cast<size_t>(n_pad) * 2 * l * c->esz;
+  const size_t qplane = static_cast<size_t>(n_pad) * c->kq * c->esz;
   auto bq = [&](int party, int vec, int limb) { return r.bq + ((party * 2 + vec) * 2 + limb) * qplane; };
   for (int i = 0; i < 3; ++i) {
     CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
     for (int vec = 0; vec < 2; ++vec) {
       const uint16_t* y = r.qstage + static_cast<size_t>(vec) * 3 * Q * l;
-      if (c->esz == 2)
+      if (c->cfg.path == IPC_PATH_TCG)
+        CTX_RC(c, prep_query_galois_strided(y, static_cast<uint64_t>(Q) * l, Q, &g, i,
+                                            reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
+                                            reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
+      else if (c->esz == 2)
         CTX_RC(c, ipc_prep_query_bf16(y, Q, &g, i, reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
                                       reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
       else
@@ -361,7 +368,15 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
       for (int vec = 0; vec < 2; ++vec) {
         uint16_t* zo = vec == 0 ? zc[i] : zm[i];
-        if (c->cfg.path == IPC_PATH_TC) {
+        if (c->cfg.path == IPC_PATH_TCG) {
+          // Galois-ring Shamir: party i's own share only, K = l
+          auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
+          const uint16_t* xl[2] = {p16(plane(c, ch, i, vec, 0)), p16(plane(c, ch, i, vec, 0))};
+          const uint16_t* xh[2] = {p16(plane(c, ch, i, vec, 1)), p16(plane(c, ch, i, vec, 1))};
+          CTX_RC(c, ring_gemm_tc_variant(256, 1, xl, xh, ch.rows, p16(bq(i, vec, 0)), p16(bq(i, vec, 1)), N, n_pad, l,
+                                         r.tags, c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo,
+                                         ldz, ch.row0, nullptr, nullptr, c->sp[i]));
+        } else if (c->cfg.path == IPC_PATH_TC) {
           auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
           const uint16_t* xl[2] = {p16(plane(c, ch, i, vec, 0)), p16(plane(c, ch, prev, vec, 0))};
           const uint16_t* xh[2] = {p16(plane(c, ch, i, vec, 1)), p16(plane(c, ch, prev, vec, 1))};

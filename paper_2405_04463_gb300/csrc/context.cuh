@@ -28,7 +28,7 @@ struct Chunk {
 struct Request {
   uint64_t id = 0;
   uint32_t Q = 0, N = 0, n_pad = 0;
-  uint8_t* bq = nullptr;        // [party][vec][limb][n_pad][2l] limbs
+  uint8_t* bq = nullptr;        // [party][vec][limb][n_pad][kq] limbs
   uint16_t* qstage = nullptr;   // [vec][3][Q][l] query shares
   uint32_t* tags = nullptr;     // [N][2]
   uint32_t* roots = nullptr;    // [3][N][ld_roots]
@@ -47,6 +47,13 @@ int ctx_fail(ipc_ctx* c, int code, const std::string& msg);
 int ctx_cfail(ipc_ctx* c, cudaError_t e, const char* what);
 uint8_t* ctx_plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb);
 int ctx_check_device_status(ipc_ctx* c);
+int prep_query_galois_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party,
+                              uint16_t* b_lo, uint16_t* b_hi, uint32_t n_pad, void* stream);
+int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* const x_lo[2],
+                         const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
+                         uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                         uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                         const uint32_t* col_tiles, const uint32_t* n_col_list, cudaStream_t stream);
 
 // Serving hooks defined in serve.cu. serve_fetch_shares and serve_release return IPC_ENOTFOUND
 // for ids that are not serving requests.
@@ -58,7 +65,8 @@ void serve_shutdown(ipc_ctx* c);
 struct ipc_ctx {
   ipc_config cfg{};
   uint32_t l = 0;
-  uint32_t esz = 1;  // bytes per limb: int8, or bf16 for IPC_PATH_TC
+  uint32_t esz = 1;  // bytes per limb: int8, or bf16 for IPC_PATH_TC / IPC_PATH_TCG
+  uint32_t kq = 0;   // K of the query operand: 2l (replicated sharing) or l (Galois-ring Shamir)
   cudaStream_t sp[3] = {nullptr, nullptr, nullptr};
   cudaStream_t sc = nullptr;
   cudaEvent_t ev_setup = nullptr, ev_gemm[3][2] = {}, ev_cmp[2] = {};

@@ -75,8 +75,8 @@ struct Shape {
 struct TcParams {
   uint32_t n_cols;
   uint32_t x_rows;
-  uint32_t kb_total;  // 2l / KB
-  uint32_t kb_half;   // l / KB
+  uint32_t kb_total;  // K / KB (K = 2l, or l for Galois-ring shares)
+  uint32_t kb_half;   // l / KB: k-blocks below it read the first database plane pair
   uint32_t n_row_tiles;
   const uint32_t* col_tiles;   // list mode: the column tiles to compute (device)
   const uint32_t* n_col_list;  // list mode: their count (device), read when the kernel starts
@@ -557,28 +557,38 @@ int launch_tc(const CUtensorMap* m, const TcParams& p, dim3 grid, cudaStream_t s
 
 // tile_cols: 256 or 128 query columns per tile. With col_tiles set, only the listed tiles of
 // that width are computed (n_col_list, on the device, holds their count) by one persistent CTA
-// per SM; otherwise every tile of [0, n_cols), one CTA each.
-int ring_gemm_tc_variant(uint32_t tile_cols, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2],
-                         size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
-                         uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
-                         uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
-                         const uint32_t* n_col_list, cudaStream_t stream) {
+// per SM; otherwise every tile of [0, n_cols), one CTA each. segments: 2 for K = 2l over the
+// planes [x_lo[0] | x_lo[1]] (replicated sharing), 1 for K = l over x_lo[0] alone (Galois-ring
+// Shamir shares; l a multiple of 256 so that L's 256-k drains tile K).
+int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* const x_lo[2],
+                         const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
+                         uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                         uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                         const uint32_t* col_tiles, const uint32_t* n_col_list, cudaStream_t stream) {
   if (tile_cols != 256 && tile_cols != 128) {
     set_error("tcgen05 ring GEMM: tile width must be 128 or 256");
     return IPC_EINVAL;
   }
+  if (segments != 1 && segments != 2) {
+    set_error("tcgen05 ring GEMM: one or two K segments");
+    return IPC_EINVAL;
+  }
+  if ((segments * l) % (2 * KB_PER_CHUNK * KB) != 0) {
+    set_error("tcgen05 ring GEMM: K must be a multiple of 256");
+    return IPC_EINVAL;
+  }
   CUtensorMap m[6];
   int rc;
-  if ((rc = make_map_bf16(&m[0], b_lo, 2ull * l, n_pad, tile_cols)) ||
-      (rc = make_map_bf16(&m[1], b_hi, 2ull * l, n_pad, tile_cols)) ||
+  if ((rc = make_map_bf16(&m[0], b_lo, static_cast<uint64_t>(segments) * l, n_pad, tile_cols)) ||
+      (rc = make_map_bf16(&m[1], b_hi, static_cast<uint64_t>(segments) * l, n_pad, tile_cols)) ||
       (rc = make_map_bf16(&m[2], x_lo[0], l, x_rows, TM)) || (rc = make_map_bf16(&m[3], x_hi[0], l, x_rows, TM)) ||
       (rc = make_map_bf16(&m[4], x_lo[1], l, x_rows, TM)) || (rc = make_map_bf16(&m[5], x_hi[1], l, x_rows, TM)))
     return rc;
   TcParams p;
   p.n_cols = n_cols;
   p.x_rows = static_cast<uint32_t>(x_rows);
-  p.kb_total = 2 * l / KB;
-  p.kb_half = l / KB;
+  p.kb_total = segments * l / KB;
+  p.kb_half = l / KB;  // with one segment every k-block reads x_lo[0] / x_hi[0]
   p.n_row_tiles = static_cast<uint32_t>((x_rows + TM - 1) / TM);
   p.col_tiles = col_tiles;
   p.n_col_list = n_col_list;
@@ -602,8 +612,8 @@ int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], s
                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream) {
-  return ring_gemm_tc_variant(256, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev,
-                              vec, z, ldz, row0, nullptr, nullptr, stream);
+  return ring_gemm_tc_variant(256, 2, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
+                              seed_prev, vec, z, ldz, row0, nullptr, nullptr, stream);
 }
 
 }  // namespace ipc

@@ -143,6 +143,99 @@ __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint64_t plane
   }
 }
 
+// ---- Galois-ring Shamir sharing (Sec. 4.3.2): GR = Z_{2^16}[X]/(X^2 - X - 1) ----
+// An element c0 + c1 X holds two consecutive code bits 2e, 2e+1; in a share vector its
+// coefficients sit at indices 2e, 2e+1, so share vectors keep the bit layout (and a rotation
+// of whole 4-bit cells moves whole elements).
+struct Gr {
+  uint32_t c0, c1;  // taken mod 2^16 where stored
+};
+
+// (a0 + a1 X)(b0 + b1 X) with X^2 = X + 1: the a1 b1 X^2 term adds to both coefficients.
+__host__ __device__ __forceinline__ Gr gr_mul(Gr a, Gr b) {
+  const uint32_t t = a.c1 * b.c1;
+  return {(a.c0 * b.c0 + t) & 0xFFFFu, (a.c0 * b.c1 + a.c1 * b.c0 + t) & 0xFFFFu};
+}
+
+// Party p's evaluation point: 1, X, 1 + X (the non-zero elements of the exceptional set
+// {0, 1, X, 1 + X}; the secret is the value at 0).
+__host__ __device__ __forceinline__ Gr gr_point(uint32_t p) {
+  return p == 0 ? Gr{1, 0} : (p == 1 ? Gr{0, 1} : Gr{1, 1});
+}
+
+// A0, Galois-ring Shamir: one thread per (row, 4 elements = 8 bits); one Philox call per
+// vector gives the 4 elements' random slopes r (word e & 3: c0 low half, c1 high half); party
+// p's share of element g is g + r * alpha_p.
+__global__ void encode_share_galois_kernel(const uint64_t* __restrict__ code_bits,
+                                           const uint64_t* __restrict__ mask_bits, uint32_t n, uint32_t l,
+                                           uint64_t seed, uint32_t side, uint32_t idx0,
+                                           uint16_t* __restrict__ code_sh, uint16_t* __restrict__ mask_sh) {
+  const uint32_t groups = l >> 3;
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (tid >= static_cast<uint64_t>(n) * groups) return;
+  const uint32_t r = static_cast<uint32_t>(tid / groups), t = static_cast<uint32_t>(tid % groups);
+  const uint32_t nw = (l + 63) >> 6;
+  const uint32_t b0 = t << 3;  // first bit of the 4 elements
+  const uint32_t cw = static_cast<uint32_t>(code_bits[static_cast<uint64_t>(r) * nw + (b0 >> 6)] >> (b0 & 63)) & 0xFFu;
+  const uint32_t mw = static_cast<uint32_t>(mask_bits[static_cast<uint64_t>(r) * nw + (b0 >> 6)] >> (b0 & 63)) & 0xFFu;
+  const uint64_t plane = static_cast<uint64_t>(n) * l;
+  const uint64_t at = static_cast<uint64_t>(r) * l + b0;
+#pragma unroll
+  for (uint32_t vec = 0; vec < 2; ++vec) {
+    const uint4 w = philox(t, idx0 + r, (side << 8) | vec, IPC_D_GSHARE << 24, seed);
+    uint32_t out[3][4];  // [party][element]: c0 | c1 << 16
+#pragma unroll
+    for (uint32_t e = 0; e < 4; ++e) {
+      uint32_t v[2];
+#pragma unroll
+      for (uint32_t k = 0; k < 2; ++k) {
+        const uint32_t cb = (cw >> (2 * e + k)) & 1u, mb = (mw >> (2 * e + k)) & 1u;
+        v[k] = vec == 0 ? (mb - 2u * (cb & mb)) : mb;
+      }
+      const uint32_t word = word_of(w, e);
+      const Gr slope = {word & 0xFFFFu, word >> 16};
+#pragma unroll
+      for (uint32_t p = 0; p < 3; ++p) {
+        const Gr ra = gr_mul(slope, gr_point(p));
+        out[p][e] = ((v[0] + ra.c0) & 0xFFFFu) | (((v[1] + ra.c1) & 0xFFFFu) << 16);
+      }
+    }
+    uint16_t* dst = vec == 0 ? code_sh : mask_sh;
+#pragma unroll
+    for (uint32_t p = 0; p < 3; ++p)
+      *reinterpret_cast<uint4*>(dst + p * plane + at) = make_uint4(out[p][0], out[p][1], out[p][2], out[p][3]);
+  }
+}
+
+// A2 for Galois-ring shares: B_p[n][k] = coefficient k & 1 of lambda_p * y_p[e'] where e' is the
+// element of the unrotated query that rotation rho brings to position k / 2. K = l.
+__global__ void prep_query_galois_kernel(const uint16_t* __restrict__ y, uint64_t plane, uint32_t Q, ipc_geom g,
+                                         uint32_t party, Gr lambda, uint16_t* __restrict__ b_lo,
+                                         uint16_t* __restrict__ b_hi, uint32_t n_pad) {
+  const uint32_t l = g.rows * g.cols * g.cell;
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  const uint64_t total = static_cast<uint64_t>(n_pad) * l;
+  if (tid >= total) return;
+  const uint32_t n = static_cast<uint32_t>(tid / l);
+  const uint32_t k = static_cast<uint32_t>(tid % l);
+  uint32_t val = 0;
+  if (n < Q * g.R) {
+    const uint32_t q = n / g.R, rho = n % g.R;
+    const int32_t shift = g.rot_lo + static_cast<int32_t>(rho);
+    const uint32_t c = k % g.cell, j = (k / g.cell) % g.cols, r = k / (g.cell * g.cols);
+    int32_t js = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
+    if (js < 0) js += g.cols;
+    const uint32_t src = (r * g.cols + static_cast<uint32_t>(js)) * g.cell + c;  // same parity as k
+    const uint16_t* yp = y + party * plane + static_cast<uint64_t>(q) * l + (src & ~1u);
+    const Gr a = gr_mul(lambda, Gr{yp[0], yp[1]});
+    val = (k & 1u) ? a.c1 : a.c0;
+  }
+  int8_t lo, hi;
+  limbs(val, lo, hi);
+  b_lo[tid] = bf16_of(lo);
+  b_hi[tid] = bf16_of(hi);
+}
+
 bool geom_ok(const ipc_geom* g) {
   if (!g || g->rows == 0 || g->cols == 0 || g->cell == 0 || g->R == 0 || g->R > 31) return false;
   const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
@@ -234,4 +327,85 @@ extern "C" int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* l
                                                                                                       hi);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
+}
+
+namespace {
+// Host-side GR arithmetic for the Lagrange coefficients (the library's own, computed once).
+struct HGr {
+  uint16_t c0, c1;
+};
+HGr hmul(HGr a, HGr b) {
+  const uint32_t t = static_cast<uint32_t>(a.c1) * b.c1;
+  return {static_cast<uint16_t>(static_cast<uint32_t>(a.c0) * b.c0 + t),
+          static_cast<uint16_t>(static_cast<uint32_t>(a.c0) * b.c1 + static_cast<uint32_t>(a.c1) * b.c0 + t)};
+}
+// a^-1 = conj(a) / N(a) with conj(X) = 1 - X and N(a) = a conj(a) in Z_{2^16}, inverted by
+// Hensel lifting (each step x <- x (2 - N x) doubles the correct low bits; x = N is right mod 8).
+bool hinv(HGr a, HGr* out) {
+  const HGr conj = {static_cast<uint16_t>(a.c0 + a.c1), static_cast<uint16_t>(-a.c1)};
+  const HGr nrm = hmul(a, conj);
+  if (nrm.c1 != 0 || (nrm.c0 & 1u) == 0) return false;
+  uint32_t x = nrm.c0;
+  for (int i = 0; i < 4; ++i) x = x * (2u - nrm.c0 * x);
+  *out = hmul(conj, HGr{static_cast<uint16_t>(x), 0});
+  return true;
+}
+// lambda_p = prod_{j != p} alpha_j (alpha_j - alpha_p)^-1
+Gr lagrange_at_zero(uint32_t p) {
+  const HGr alpha[3] = {{1, 0}, {0, 1}, {1, 1}};
+  HGr acc = {1, 0};
+  for (uint32_t j = 0; j < 3; ++j) {
+    if (j == p) continue;
+    HGr inv;
+    const HGr d = {static_cast<uint16_t>(alpha[j].c0 - alpha[p].c0), static_cast<uint16_t>(alpha[j].c1 - alpha[p].c1)};
+    if (!hinv(d, &inv)) return {0, 0};  // unreachable: the points' differences are units
+    acc = hmul(acc, hmul(alpha[j], inv));
+  }
+  return {acc.c0, acc.c1};
+}
+}  // namespace
+
+extern "C" int ipc_encode_share_galois(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                                       uint64_t client_seed, uint32_t side, uint32_t idx0, uint16_t* code_sh,
+                                       uint16_t* mask_sh, void* stream) {
+  if (l == 0 || l % 8 != 0 || !code_bits || !mask_bits || !code_sh || !mask_sh ||
+      (reinterpret_cast<uintptr_t>(code_sh) & 15) || (reinterpret_cast<uintptr_t>(mask_sh) & 15)) {
+    set_error("ipc_encode_share_galois: l must be a positive multiple of 8, outputs 16-byte aligned");
+    return IPC_EINVAL;
+  }
+  if (n == 0) return IPC_OK;
+  const uint64_t threads = static_cast<uint64_t>(n) * (l / 8);
+  const uint32_t bs = 256;
+  encode_share_galois_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+      code_bits, mask_bits, n, l, client_seed, side, idx0, code_sh, mask_sh);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+namespace ipc {
+int prep_query_galois_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party,
+                              uint16_t* b_lo, uint16_t* b_hi, uint32_t n_pad, void* stream) {
+  if (!geom_ok(g) || g->cell % 2 != 0 || party > 2 || !y || !b_lo || !b_hi || Q == 0 ||
+      static_cast<uint64_t>(Q) * g->R > n_pad) {
+    set_error("ipc_prep_query_galois: invalid geometry (even cell), party, or n_pad < Q*R");
+    return IPC_EINVAL;
+  }
+  const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
+  if (y_plane < static_cast<uint64_t>(Q) * l) {
+    set_error("ipc_prep_query_galois: component stride shorter than Q * l");
+    return IPC_EINVAL;
+  }
+  const uint64_t total = static_cast<uint64_t>(n_pad) * l;
+  const uint32_t bs = 256;
+  prep_query_galois_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+      y, y_plane, Q, *g, party, lagrange_at_zero(party), b_lo, b_hi, n_pad);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+}  // namespace ipc
+
+extern "C" int ipc_prep_query_galois(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party,
+                                     uint16_t* b_lo, uint16_t* b_hi, uint32_t n_pad, void* stream) {
+  const uint64_t l = g ? static_cast<uint64_t>(g->rows) * g->cols * g->cell : 0;
+  return prep_query_galois_strided(y, Q * l, Q, g, party, b_lo, b_hi, n_pad, stream);
 }

@@ -25,8 +25,14 @@ def dev_u64(a):
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
 
 
-def encode_gpu(code_bits, mask_bits, l, seed, side, idx0=0):
-    """A0 on the device through the C ABI; returns torch int16 [3][n][l] code and mask shares."""
+def galois(path) -> bool:
+    """Whether a path takes Galois-ring Shamir shares (else replicated-sharing components)."""
+    return path in ("tcg", 4)
+
+
+def encode_gpu(code_bits, mask_bits, l, seed, side, idx0=0, galois_shares=False):
+    """A0 on the device through the C ABI; returns torch int16 [3][n][l] code and mask shares
+    (additive components, or the parties' Galois-ring Shamir shares)."""
     torch = torch_mod()
     ipc = lib()
     cb = code_bits if hasattr(code_bits, "data_ptr") else dev_u64(code_bits)
@@ -34,7 +40,8 @@ def encode_gpu(code_bits, mask_bits, l, seed, side, idx0=0):
     n = cb.shape[0]
     code = torch.empty((3, n, l), dtype=torch.int16, device="cuda")
     mask = torch.empty((3, n, l), dtype=torch.int16, device="cuda")
-    ipc.ipc_encode_share(cb, mb, n, l, seed, side, idx0, code, mask)
+    fn = ipc.ipc_encode_share_galois if galois_shares else ipc.ipc_encode_share
+    fn(cb, mb, n, l, seed, side, idx0, code, mask)
     return code, mask
 
 
@@ -61,23 +68,23 @@ def db_bits_device(w: synth.Workload, row0: int, n: int):
     return code, mask
 
 
-def load_workload(ctx, w: synth.Workload, chunk: int = 16384):
+def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=False):
     """Generate the workload's database on the device, share it (A0) and load it (A1)."""
     torch = torch_mod()
     ipc = lib()
     for r0 in range(0, w.s, chunk):
         n = min(chunk, w.s - r0)
         cb, mb = db_bits_device(w, r0, n)
-        code, mask = encode_gpu(cb, mb, w.l, w.db_share_seed, 0, idx0=r0)
+        code, mask = encode_gpu(cb, mb, w.l, w.db_share_seed, 0, idx0=r0, galois_shares=galois_shares)
         ipc.load_db_shares(ctx, [code[j] for j in range(3)], [mask[j] for j in range(3)], n, 1)
         del code, mask
     torch.cuda.synchronize()
 
 
-def query_shares_gpu(w: synth.Workload, qc=None, qm=None):
+def query_shares_gpu(w: synth.Workload, qc=None, qm=None, galois_shares=False):
     if qc is None:
         qc, qm = w.query_bits()
-    return encode_gpu(qc, qm, w.l, w.q_share_seed, 1)
+    return encode_gpu(qc, qm, w.l, w.q_share_seed, 1, galois_shares=galois_shares)
 
 
 def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0):

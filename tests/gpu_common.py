@@ -1,3 +1,3 @@
 """GPU-test helpers: the package's workload loader plus torch/numpy glue."""
-from paper_2405_04463_gb300.workload import (db_bits_device, dev_u64, encode_gpu, lib, load_workload,  # noqa: F401
+from paper_2405_04463_gb300.workload import (db_bits_device, dev_u64, encode_gpu, galois, lib, load_workload,  # noqa: F401
                                              make_ctx, query_shares_gpu, tags_for, torch_mod, u16)

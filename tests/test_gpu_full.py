@@ -1,7 +1,8 @@
 """Full-size parity at the benchmark's workload and launch configuration.
 
 100,000 database rows x 32 queries x 31 rotations (99.2 M comparisons), database generated
-on the device, resident chunks of 65,536 rows. The plaintext oracle (Alg. 1) runs over every
+on the device, resident chunks of 65,536 rows; the planted and largest workloads run on the
+tcgen05 path the benchmark times. The plaintext oracle (Alg. 1) runs over every
 comparison on the host cores; the 3-party simulation is too slow at this size, so share-level
 agreement is checked between the two GPU paths (same request id, same PRF counters) and
 distances are checked row by row for sampled columns.
@@ -13,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import db_bits_device, lib, load_workload, make_ctx, query_shares_gpu
+from gpu_common import db_bits_device, galois, lib, load_workload, make_ctx, query_shares_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -37,8 +38,8 @@ def _run(w, path, keep, qc, qm):
     ipc = lib()
     ctx = make_ctx(w, path=path, keep=keep, max_queries=w.Q)
     try:
-        load_workload(ctx, w, chunk=8192)   # many loads racing the encode kernel if unordered
-        qcode, qmask = query_shares_gpu(w, qc, qm)
+        load_workload(ctx, w, chunk=8192, galois_shares=galois(path))   # many loads racing the encode if unordered
+        qcode, qmask = query_shares_gpu(w, qc, qm, galois_shares=galois(path))
         rid = ipc.submit_queries(ctx, [qcode[j] for j in range(3)], [qmask[j] for j in range(3)], w.Q, 1)
         shares = np.zeros((3, w.Q), np.uint8)
         ipc.fetch_bit_shares(ctx, rid, shares, w.Q, 600000)
@@ -69,6 +70,11 @@ def test_plain_vs_precision_full_size(c2):
     for k in dist:
         for other in (distx, distt):
             assert (dist[k][0] == other[k][0]).all() and (dist[k][1] == other[k][1]).all()
+    # Galois-ring Shamir dots: other shares (another sharing), the same opened bits and distances
+    _, shg, distg = _run(w, "tcg", True, c2["qc"], c2["qm"])
+    assert (oracle.reconstruct_bits(shg) == c2["match"]).all()
+    for k in dist:
+        assert (dist[k][0] == distg[k][0]).all() and (dist[k][1] == distg[k][1]).all()
     for (q, rho), (dot, ml) in dist.items():
         assert (ml == c2["ml"][q, rho]).all()
         assert (dot == c2["ml"][q, rho] - 2 * c2["hd"][q, rho]).all()
@@ -119,7 +125,7 @@ def _full_size(name, keep):
     del cb, mb
     qc, qm = w.query_bits()
     match, _, _ = oracle.plain_match(oracle.iris_geom(), qc, qm, dc, dm, threads=os.cpu_count() or 1)
-    ctx = make_ctx(w, path="i8mix", keep=keep, max_queries=w.Q)
+    ctx = make_ctx(w, path="tc", keep=keep, max_queries=w.Q)   # the benchmark's path
     try:
         load_workload(ctx, w, chunk=32768)
         assert ipc.ipc_db_rows(ctx) == w.s
@@ -159,6 +165,6 @@ def test_planted_workload_full_size():
 
 
 def test_largest_workload_full_size():
-    """600,000 rows (about 92 GB of resident shares) x 256 queries x 31 rotations (4.76 G
+    """600,000 rows (184 GB of resident bf16 limb planes) x 256 queries x 31 rotations (4.76 G
     comparisons), 13 planted near-duplicates at 5-15% flipped bits."""
     _full_size("c5", keep=False)

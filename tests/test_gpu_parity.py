@@ -439,3 +439,108 @@ def test_tc_tile_lists_match_int32(torch, tile_cols):
                                ldz, 16, lst, cnt0)
     torch.cuda.synchronize()
     assert (z3.cpu() == 77).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# Galois-ring Shamir dot products (Sec. 4.3.2): IPC_PATH_TCG
+# ---------------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_galois(small):
+    w = small["w"]
+    dbc, dbm = oracle.encode_share_galois(small["dc"], small["dm"], L, w.db_share_seed, 0)
+    qsc, qsm = oracle.encode_share_galois(small["qc"], small["qm"], L, w.q_share_seed, 1)
+    ref = oracle.mpc_match_galois(oracle.mpc_cfg(w.prf_seeds, req=REQ), oracle.iris_geom(), dbc, dbm, qsc, qsm,
+                                  want_z=True)
+    return dict(dbc=dbc, dbm=dbm, qsc=qsc, qsm=qsm, ref=ref)
+
+
+def test_encode_share_galois_matches_oracle(small, small_galois):
+    w = small["w"]
+    code, mask = encode_gpu(small["dc"], small["dm"], L, w.db_share_seed, 0, galois_shares=True)
+    assert (u16(code) == small_galois["dbc"]).all()
+    assert (u16(mask) == small_galois["dbm"]).all()
+    qcode, qmask = encode_gpu(small["qc"], small["qm"], L, w.q_share_seed, 1, galois_shares=True)
+    assert (u16(qcode) == small_galois["qsc"]).all() and (u16(qmask) == small_galois["qsm"]).all()
+
+
+def test_prep_query_galois_is_lambda_times_rotated_share(small, small_galois, torch):
+    """B_p = lambda_p * (rotated party-p share), elementwise in GR; multiplication by a0 + a1 X
+    taken as the matrix a0 I + a1 [[0, 1], [1, 1]] on the coefficient pair."""
+    ipc = lib()
+    g = ipc.iris_geom()
+    og = oracle.iris_geom()
+    Q, R = 5, 31
+    lam = oracle.gr_lagrange().astype(np.int64)
+    y = torch.from_numpy(small_galois["qsc"].view(np.int16).copy()).cuda()
+    n_pad = 256
+    for party in range(3):
+        lo = torch.empty((n_pad, L), dtype=torch.int16, device="cuda")
+        hi = torch.empty((n_pad, L), dtype=torch.int16, device="cuda")
+        ipc.ipc_prep_query_galois(y, Q, g, party, lo, hi, n_pad)
+        lof = lo.view(torch.bfloat16).float().cpu().numpy().astype(np.int64)
+        hif = hi.view(torch.bfloat16).float().cpu().numpy().astype(np.int64)
+        rebuilt = (256 * hif + lof) & 0xFFFF
+        l0, l1 = lam[party]
+        for q in (0, 4):
+            for rho in (0, 15, 30):
+                v = oracle.rotate_u16(og, small_galois["qsc"][party, q], -15 + rho).astype(np.int64)
+                y0, y1 = v[0::2], v[1::2]
+                expect = np.empty(L, np.int64)
+                expect[0::2] = (l0 * y0 + l1 * y1) & 0xFFFF
+                expect[1::2] = (l0 * y1 + l1 * (y0 + y1)) & 0xFFFF
+                assert (rebuilt[q * R + rho] == expect).all(), (party, q, rho)
+        assert (rebuilt[Q * R:] == 0).all()
+
+
+def test_ring_gemm_galois_matches_oracle_shares(small, small_galois, torch):
+    ipc = lib()
+    g = ipc.iris_geom()
+    w = small["w"]
+    Q, R, s = w.Q, w.R, w.s
+    N, n_pad, ldz = Q * R, 256, 784
+    tags = torch.from_numpy(tags_for(REQ, Q, R).view(np.int32)).cuda()
+    for vec, (db, qs, key) in enumerate(((small_galois["dbc"], small_galois["qsc"], "z_code"),
+                                         (small_galois["dbm"], small_galois["qsm"], "z_mask"))):
+        planes = _planes(torch, db, bf16=True)
+        y = torch.from_numpy(qs.view(np.int16).copy()).cuda()
+        z = torch.zeros((3, N, ldz), dtype=torch.int16, device="cuda")
+        for i in range(3):
+            prev = (i + 2) % 3
+            blo = torch.empty((n_pad, L), dtype=torch.int16, device="cuda")
+            bhi = torch.empty((n_pad, L), dtype=torch.int16, device="cuda")
+            ipc.ipc_prep_query_galois(y, Q, g, i, blo, bhi, n_pad)
+            ipc.ipc_ring_gemm_tc_galois(256, planes[i][0], planes[i][1], s, blo, bhi, N, n_pad, L, tags,
+                                        w.prf_seeds[i], w.prf_seeds[prev], vec, z[i], ldz, 0)
+        torch.cuda.synchronize()
+        ipc.ipc_status()
+        assert (u16(z)[:, :, :s] == small_galois["ref"][key]).all(), key
+    n = Q * R
+    assert (oracle.reconstruct_u16(small_galois["ref"]["z_mask"]) == small["ml"].reshape(n, -1)).all()
+
+
+@pytest.mark.parametrize("chunk_rows", [0, 1024])
+def test_context_galois_end_to_end(small, small_galois, torch, chunk_rows):
+    ipc = lib()
+    w = small["w"]
+    ctx = make_ctx(w, path="tcg", keep=True, chunk_rows=chunk_rows)
+    try:
+        load_workload(ctx, w, chunk=300, galois_shares=True)
+        qcode, qmask = query_shares_gpu(w, small["qc"], small["qm"], galois_shares=True)
+        rid = ipc.submit_queries(ctx, [qcode[j] for j in range(3)], [qmask[j] for j in range(3)], w.Q, 1)
+        sh = np.zeros((3, w.Q), np.uint8)
+        ipc.fetch_bit_shares(ctx, rid, sh, w.Q, 60000)
+        ref = oracle.mpc_match_galois(oracle.mpc_cfg(w.prf_seeds, req=rid), oracle.iris_geom(), small_galois["dbc"],
+                                      small_galois["dbm"], small_galois["qsc"], small_galois["qsm"])
+        assert (sh == ref["bits"]).all()
+        for q, rho in ((0, 0), (1, 15), (4, 30)):
+            dot = np.zeros(w.s, np.int16)
+            ml = np.zeros(w.s, np.uint16)
+            ipc.fetch_distances(ctx, rid, q, rho, 0, w.s, dot, ml)
+            assert (ml == small["ml"][q, rho]).all()
+            assert (dot == small["ml"][q, rho] - 2 * small["hd"][q, rho]).all()
+        bits = np.zeros(w.Q, np.uint8)
+        ipc.fetch_match_bits(ctx, rid, bits, w.Q, 60000)
+        assert (bits == small["match"]).all()
+    finally:
+        ipc.ipc_destroy(ctx)

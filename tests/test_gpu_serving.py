@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import lib, load_workload, make_ctx
+from gpu_common import galois, lib, load_workload, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -34,15 +34,24 @@ def wl():
     dbc, dbm = oracle.encode_share(dc, dm, L, w.db_share_seed, 0)
     qsc, qsm = oracle.encode_share(qc, qm, L, w.q_share_seed, 1)
     match, _, _ = oracle.plain_match(g, qc, qm, dc, dm, threads=os.cpu_count() or 1)
-    return dict(w=w, g=g, dbc=dbc, dbm=dbm, qsc=qsc, qsm=qsm, match=match, ref={})
+    gdbc, gdbm = oracle.encode_share_galois(dc, dm, L, w.db_share_seed, 0)
+    gqsc, gqsm = oracle.encode_share_galois(qc, qm, L, w.q_share_seed, 1)
+    return dict(w=w, g=g, dbc=dbc, dbm=dbm, qsc=qsc, qsm=qsm, match=match, ref={},
+                galois=dict(dbc=gdbc, dbm=gdbm, qsc=gqsc, qsm=gqsm))
 
 
-def _oracle_bits(wl, rid, q0, n):
-    key = (rid, q0, n)
+def _shares(wl, path):
+    return wl["galois"] if galois(path) else wl
+
+
+def _oracle_bits(wl, rid, q0, n, path="tc"):
+    key = (rid, q0, n, galois(path))
     if key not in wl["ref"]:
         w = wl["w"]
-        ref = oracle.mpc_match(oracle.mpc_cfg(w.prf_seeds, req=rid), wl["g"], wl["dbc"], wl["dbm"],
-                               wl["qsc"][:, q0:q0 + n], wl["qsm"][:, q0:q0 + n])
+        sh = _shares(wl, path)
+        fn = oracle.mpc_match_galois if galois(path) else oracle.mpc_match
+        ref = fn(oracle.mpc_cfg(w.prf_seeds, req=rid), wl["g"], sh["dbc"], sh["dbm"], sh["qsc"][:, q0:q0 + n],
+                 sh["qsm"][:, q0:q0 + n])
         wl["ref"][key] = ref["bits"]
     return wl["ref"][key]
 
@@ -51,20 +60,21 @@ def _serve(wl, path, variant, pool, batches, tune_cache=None):
     ipc = lib()
     w = wl["w"]
     ctx = make_ctx(w, path=path, chunk_rows=1024, max_queries=4)
+    sh = _shares(wl, path)
     try:
-        load_workload(ctx, w, chunk=700)
+        load_workload(ctx, w, chunk=700, galois_shares=galois(path))
         ipc.ipc_serve_start(ctx, pool_queries=pool, variant=variant, tune_cache=tune_cache)
         tuning = ipc.ipc_serve_tuning(ctx)
         rids = []
         for q0, n in batches:
-            code = [np.ascontiguousarray(wl["qsc"][j, q0:q0 + n]) for j in range(3)]
-            mask = [np.ascontiguousarray(wl["qsm"][j, q0:q0 + n]) for j in range(3)]
+            code = [np.ascontiguousarray(sh["qsc"][j, q0:q0 + n]) for j in range(3)]
+            mask = [np.ascontiguousarray(sh["qsm"][j, q0:q0 + n]) for j in range(3)]
             rids.append(ipc.ipc_serve_submit(ctx, code, mask, n))
         out = []
         for rid, (q0, n) in zip(rids, batches):
-            sh = np.zeros((3, n), np.uint8)
-            ipc.fetch_bit_shares(ctx, rid, sh, n, 120000)
-            out.append((rid, q0, n, sh, ipc.ipc_serve_times(ctx, rid)))
+            got = np.zeros((3, n), np.uint8)
+            ipc.fetch_bit_shares(ctx, rid, got, n, 120000)
+            out.append((rid, q0, n, got, ipc.ipc_serve_times(ctx, rid)))
         stats = ipc.ipc_serve_stats(ctx)
         for rid, _, n, _, _ in out:
             bits = np.zeros(n, np.uint8)
@@ -75,9 +85,9 @@ def _serve(wl, path, variant, pool, batches, tune_cache=None):
     return out, stats, tuning
 
 
-def _check(wl, out):
+def _check(wl, out, path="tc"):
     for rid, q0, n, sh, _ in out:
-        assert (sh == _oracle_bits(wl, rid, q0, n)).all(), (rid, q0, n)
+        assert (sh == _oracle_bits(wl, rid, q0, n, path)).all(), (rid, q0, n)
         assert (oracle.reconstruct_bits(sh) == wl["match"][q0:q0 + n]).all(), (rid, q0, n)
 
 
@@ -112,6 +122,13 @@ def test_autotune_table_is_cached_and_reused(wl, tmp_path):
     _check(wl, out2)
     assert tuning2.strip() == tuning.strip()   # read back, not measured again
     assert sum(stats["variant_steps"]) == stats["steps"]
+
+
+def test_galois_path_serving(wl):
+    """Galois-ring Shamir dot products in the serving loop: shares equal to the oracle's."""
+    out, stats, _ = _serve(wl, "tcg", "tc256", 6, BATCHES)
+    _check(wl, out, "tcg")
+    assert stats["completed"] == len(BATCHES)
 
 
 def test_int8_path_serving(wl):
