@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--rates", default="0.3,0.6,0.9", help="arrival rates as fractions of the measured capacity")
     ap.add_argument("--pool", type=int, default=0, help="serving pool in query slots (0 = library default)")
     ap.add_argument("--capacity-requests", type=int, default=8)
+    ap.add_argument("--serving-path", default="tc", choices=["tc", "tcg"],
+                    help="tc: replicated-sharing dots; tcg: Galois-ring Shamir dots")
     return ap.parse_args()
 
 
@@ -417,19 +419,20 @@ def run_serving(args):
     import torch
 
     import paper_2405_04463_gb300 as ipc
-    from paper_2405_04463_gb300.workload import encode_gpu, load_workload, make_ctx
+    from paper_2405_04463_gb300.workload import encode_gpu, galois, load_workload, make_ctx
 
     w = synth.workload("c4")
     torch.cuda.set_device(0)
-    ctx = make_ctx(w, path="tc", max_queries=256)
+    path = args.serving_path
+    ctx = make_ctx(w, path=path, max_queries=256)
     t_load = time.perf_counter()
-    load_workload(ctx, w, chunk=32768)
+    load_workload(ctx, w, chunk=32768, galois_shares=galois(path))
     t_load = time.perf_counter() - t_load
     # 512 query shares on the host; request k takes a window of its batch size
     rng = np.random.default_rng(0x5E7E)
     qc = rng.integers(0, 2**63, size=(512, w.nwords), dtype=np.int64).view(np.uint64)
     qm = rng.integers(0, 2**63, size=(512, w.nwords), dtype=np.int64).view(np.uint64)
-    qcode, qmask = encode_gpu(qc, qm, w.l, w.q_share_seed, 1)
+    qcode, qmask = encode_gpu(qc, qm, w.l, w.q_share_seed, 1, galois_shares=galois(path))
     hcode = [qcode[j].cpu().numpy() for j in range(3)]
     hmask = [qmask[j].cpu().numpy() for j in range(3)]
     del qcode, qmask
@@ -506,7 +509,7 @@ def run_serving(args):
     print(json.dumps({
         "metric": "serving: latency p50/p99 and comparisons/s under Poisson arrivals", "unit": "s / comparisons/s",
         "config": {"workload": w.name, "db_rows": w.s, "rotations": w.R, "batch": "U{1..256} queries",
-                   "arrivals": "Poisson, seeded", "path": "tc", "pool_query_slots": stats["pool_queries"],
+                   "arrivals": "Poisson, seeded", "path": path, "pool_query_slots": stats["pool_queries"],
                    "pool_cols": stats["pool_cols"], "chunks": stats["n_chunks"],
                    "requests_per_rate": args.requests_per_rate},
         "load_s": t_load, "capacity_req_per_s": capacity, "capacity_comparisons_per_s": cap_cmp,
