@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
-    ap.add_argument("--kernel", default=None, help="time one ring-GEMM path alone (i8mix | i8mma | i32 | tc), for profiling")
+    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc) or compare")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--serving", action="store_true",
@@ -62,12 +62,47 @@ def parse():
     return ap.parse_args()
 
 
+def run_compare_kernel(args, w):
+    """The comparison phase (A4-A8 with the in-block OR) of one chunk alone: all query columns
+    x --rows rows of random dot-product shares, timed with CUDA events."""
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    N, rows = w.Q * w.R, args.rows
+    g = torch.Generator(device="cpu").manual_seed(7)
+    zc = [torch.randint(-32768, 32768, (N, rows), dtype=torch.int16, generator=g).cuda() for _ in range(3)]
+    zm = [torch.randint(0, 12801, (N, rows), dtype=torch.int16, generator=g).cuda() for _ in range(3)]
+    tags = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
+    nb = (rows + 1023) // 1024
+    roots = torch.zeros((3, N, nb), dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def launch():
+        ipc.ipc_compare(zc, zm, rows, N, rows, 0, tags, w.prf_seeds, w.thr_a, 5, roots, nb)
+
+    launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.reps):
+        launch()
+    e1.record(st)
+    e1.synchronize()
+    ipc.ipc_status()
+    ms = e0.elapsed_time(e1) / args.reps
+    bytes_read = 12.0 * N * rows   # 3 parties x (dot, ml) x 2 B per comparison
+    print(json.dumps({"kernel": "compare", "rows": rows, "cols": N, "ms_per_launch": ms,
+                      "comparisons_per_s": N * rows / (ms * 1e-3), "algorithmic_bytes_per_launch": bytes_read,
+                      "achieved_gbs": bytes_read / (ms * 1e-3) / 1e9}))
+
+
 def run_kernel(args, w):
     """One ring-GEMM launch shape of the workload (all its query columns x --rows rows), random
     operands, timed alone with CUDA events; used for ncu captures on a small case."""
     import torch
 
     import paper_2405_04463_gb300 as ipc
+    if args.kernel == "compare":
+        return run_compare_kernel(args, w)
     l, N = w.l, w.Q * w.R
     n_pad = (N + 127) // 128 * 128
     rows = args.rows
