@@ -124,6 +124,8 @@ def _declare(L):
     L.orc_mpc_dot_galois.argtypes = [C, _p(u16), u64, _p(u16), u64, u32, u32, u32, u32, u32, _p(u16), S]
     L.orc_mpc_match_galois.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
                                        _p(u16), _p(u16), _p(u8), _p(u8), S]
+    L.orc_mpc_match_batch.argtypes = [C, G, ctypes.c_int, _p(u16), _p(u16), u32, _p(u8), S]
+    L.orc_or_combine.argtypes = [C, _p(u8), u32, _p(u8), S]
     L.orc_mpc_match.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
                                 _p(u16), _p(u16), _p(u8), _p(u8), S]
     for f in ("orc_philox4x32_10", "orc_rotate_u16", "orc_rotate_bits", "orc_encode_share", "orc_plain_pair",
@@ -339,6 +341,32 @@ def mpc_match_galois(cfg: MpcCfg, g: Geom, db_code, db_mask, q_code, q_mask, wan
                      want_msb: bool = False):
     """mpc_match with the dot products on Galois-ring Shamir shares (encode_share_galois)."""
     return _mpc_match(lib().orc_mpc_match_galois, cfg, g, db_code, db_mask, q_code, q_mask, want_z, want_msb)
+
+
+# ---- both eyes and inner-batch matching (Sec. 5.4) ----
+
+def mpc_match_batch(cfg: MpcCfg, g: Geom, q_code, q_mask, galois: bool = False):
+    """Inner-batch part of one eye: query q against the unrotated codes of persons p' < q of the
+    same batch (shares [3][P][l]); returns bits [3][P]."""
+    q_code = np.ascontiguousarray(q_code, dtype=np.uint16)
+    q_mask = np.ascontiguousarray(q_mask, dtype=np.uint16)
+    P = q_code.shape[1]
+    bits = np.zeros((3, P), np.uint8)
+    st = Stats()
+    lib().orc_mpc_match_batch(ctypes.byref(cfg), ctypes.byref(g), int(galois), _ptr(q_code, ctypes.c_uint16),
+                              _ptr(q_mask, ctypes.c_uint16), P, _ptr(bits, ctypes.c_uint8), ctypes.byref(st))
+    return bits
+
+
+def or_combine(cfg: MpcCfg, bits4) -> np.ndarray:
+    """(b0 OR b1) OR (b2 OR b3) per person on boolean sharings bits4 [4][3][P] -> [3][P]."""
+    bits4 = np.ascontiguousarray(bits4, dtype=np.uint8)
+    P = bits4.shape[2]
+    out = np.zeros((3, P), np.uint8)
+    st = Stats()
+    lib().orc_or_combine(ctypes.byref(cfg), _ptr(bits4, ctypes.c_uint8), P, _ptr(out, ctypes.c_uint8),
+                         ctypes.byref(st))
+    return out
 
 
 def reconstruct_u16(shares) -> np.ndarray:

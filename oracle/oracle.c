@@ -575,9 +575,12 @@ void orc_or_tree(const orc_mpc_cfg* cfg, const uint8_t* msb, uint32_t R, uint32_
 typedef void (*dot_fn)(const orc_mpc_cfg*, const uint16_t*, uint64_t, const uint16_t*, uint64_t, uint32_t,
                        uint32_t, uint32_t, uint32_t, uint32_t, uint16_t[3], orc_stats*);
 
+/* valid_rows (may be NULL): for query q, rows i >= valid_rows[q] enter q's OR tree as the
+ * public 0 (all three components 0) instead of their comparison bit. */
 static void mpc_match_with(dot_fn dot, const orc_mpc_cfg* cfg, const orc_geom* g,
                            const uint16_t* db_code, const uint16_t* db_mask, uint32_t s,
                            const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
+                           const uint32_t* valid_rows,
                            uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
                            orc_stats* st) {
   uint32_t l = g->rows * g->cols * g->cell;
@@ -606,6 +609,7 @@ static void mpc_match_with(dot_fn dot, const orc_mpc_cfg* cfg, const orc_geom* g
           for (int p = 0; p < 3; p++) z_mask[p * zplane + n * s + i] = zm[p];
         uint8_t b[3];
         orc_mpc_compare(cfg, zc, zm, q, rho, i, b, NULL, NULL, st);
+        if (valid_rows && i >= valid_rows[q]) b[0] = b[1] = b[2] = 0;
         for (int p = 0; p < 3; p++) {
           msb[(size_t)p * R * s + (size_t)rho * s + i] = b[p];
           if (msb_out) msb_out[p * zplane + n * s + i] = b[p];
@@ -626,7 +630,8 @@ void orc_mpc_match(const orc_mpc_cfg* cfg, const orc_geom* g,
                    const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
                    uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
                    orc_stats* st) {
-  mpc_match_with(orc_mpc_dot, cfg, g, db_code, db_mask, s, q_code, q_mask, Q, z_code, z_mask, msb_out, bits, st);
+  mpc_match_with(orc_mpc_dot, cfg, g, db_code, db_mask, s, q_code, q_mask, Q, NULL, z_code, z_mask, msb_out, bits,
+                 st);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -754,6 +759,43 @@ void orc_mpc_match_galois(const orc_mpc_cfg* cfg, const orc_geom* g,
                           uint16_t* z_code, uint16_t* z_mask, uint8_t* msb_out, uint8_t* bits,
                           orc_stats* st) {
   if (g->cell % 2 != 0) abort(); /* element pairs must not straddle rotated cells */
-  mpc_match_with(orc_mpc_dot_galois, cfg, g, db_code, db_mask, s, q_code, q_mask, Q, z_code, z_mask, msb_out, bits,
-                 st);
+  mpc_match_with(orc_mpc_dot_galois, cfg, g, db_code, db_mask, s, q_code, q_mask, Q, NULL, z_code, z_mask, msb_out,
+                 bits, st);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Both eyes and inner-batch matching (Sec. 5.4).                            */
+/* ------------------------------------------------------------------------ */
+void orc_mpc_match_batch(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
+                         const uint16_t* q_code, const uint16_t* q_mask, uint32_t P, uint8_t* bits,
+                         orc_stats* st) {
+  uint32_t* valid = (uint32_t*)malloc(sizeof(uint32_t) * (P ? P : 1));
+  for (uint32_t q = 0; q < P; q++) valid[q] = q; /* persons before q in the batch */
+  mpc_match_with(galois ? orc_mpc_dot_galois : orc_mpc_dot, cfg, g, q_code, q_mask, P, q_code, q_mask, P, valid,
+                 NULL, NULL, NULL, bits, st);
+  free(valid);
+}
+
+void orc_or_combine(const orc_mpc_cfg* cfg, const uint8_t* bits4, uint32_t P, uint8_t* out, orc_stats* st) {
+  size_t part = 3 * (size_t)P;
+  for (uint32_t p = 0; p < P; p++) {
+    rss_t b[4];
+    for (int k = 0; k < 4; k++) {
+      uint32_t comp[3];
+      for (int j = 0; j < 3; j++) comp[j] = bits4[k * part + (size_t)j * P + p];
+      b[k] = rss_from_components(comp, 0);
+    }
+    rss_t r[3];
+    for (uint32_t t = 0; t < 3; t++) {
+      uint32_t w[3][4], F[3];
+      for (int j = 0; j < 3; j++) {
+        prf(cfg->seeds[j], p, 0, cfg->req, (ORC_D_COMB << 24) | t, w[j]);
+        F[j] = w[j][0] & 1u;
+      }
+      rss_t x = t == 0 ? b[0] : (t == 1 ? b[2] : r[0]);
+      rss_t y = t == 0 ? b[1] : (t == 1 ? b[3] : r[1]);
+      r[t] = bor(x, y, F, st);
+    }
+    for (int j = 0; j < 3; j++) out[(size_t)j * P + p] = (uint8_t)(rss_component(&r[2], j) & 1u);
+  }
 }

@@ -35,6 +35,7 @@ extern "C" {
 #define ORC_D_INJ2  5u /* BitInject c_2, w_0, w_1 (seed_2)                             */
 #define ORC_D_OR    6u /* boolean zero shares of the OR-tree AND gates                 */
 #define ORC_D_GSHARE 7u /* client randomness of the Galois-ring Shamir sharing        */
+#define ORC_D_COMB  8u /* boolean zero shares of the per-person OR combination      */
 
 /* Gate numbering of the comparison circuit (D_AND counter). */
 #define ORC_LIFT_GATE0 0u  /* 33 gates of BitExtract(.,{17,16}) inside Lift      */
@@ -160,6 +161,21 @@ void orc_mpc_match_galois(const orc_mpc_cfg* cfg, const orc_geom* g,
                           const uint16_t* q_code, const uint16_t* q_mask, uint32_t Q,
                           uint16_t* z_code, uint16_t* z_mask, uint8_t* msb, uint8_t* bits,
                           orc_stats* st);
+
+/* ---- Both eyes and inner-batch matching (Sec. 5.4: a query is a person's two irises, and
+ * the persons of a batch are also matched with each other). ----
+ * Inner-batch part of one eye: the batch's own shares serve as database rows; query q (all R
+ * rotations) is compared with the unrotated codes of the persons p' < q only (rows p' >= q are
+ * the public 0 in q's OR tree), so of two duplicates in one batch the earlier one passes.
+ * galois selects the Galois-ring Shamir dot products. bits: [3][P]. */
+void orc_mpc_match_batch(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
+                         const uint16_t* q_code, const uint16_t* q_mask, uint32_t P, uint8_t* bits,
+                         orc_stats* st);
+/* Person bit = (b0 OR b1) OR (b2 OR b3) on boolean sharings (b0, b1: the two eyes against the
+ * database; b2, b3: the two eyes inside the batch). Gate t in {0: b0|b1, 1: b2|b3, 2: root}
+ * of person p uses bit 0 of word 0 of Philox(seed_j, (p, 0, req, D_COMB << 24 | t)).
+ * bits4: [4][3][P]; out: [3][P]. */
+void orc_or_combine(const orc_mpc_cfg* cfg, const uint8_t* bits4, uint32_t P, uint8_t* out, orc_stats* st);
 
 #ifdef __cplusplus
 }
