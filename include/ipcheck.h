@@ -68,6 +68,7 @@ extern "C" {
 #define IPC_D_INJ2 5u
 #define IPC_D_OR 6u
 #define IPC_D_GSHARE 7u /* client randomness of the Galois-ring Shamir sharing */
+#define IPC_D_COMB 8u   /* AND gates of the per-person OR of eyes and batch parts */
 
 typedef struct {
   uint32_t rows, cols, cell; /* code geometry; l = rows*cols*cell, a multiple of 128 */
@@ -407,6 +408,24 @@ const char* ipc_last_error(const ipc_ctx* ctx);
  * what = 1 -> 32-bit IMAD rate in T IMAD/s; what = 2 -> dp4a rate in TOP/s (8 ops per
  * instruction). Synchronous; allocates a small buffer. */
 int ipc_measure_peak(int what, void* stream, double* out);
+
+/*
+ * Both eyes and inner-batch matching (Sec. 5.4: a query is a person's two iris codes, each
+ * rotated R times; the persons of a batch are also matched with each other). ctx[e] holds the
+ * database of eye e (both contexts with the same path, geometry, seeds and threshold).
+ * code[3e + j], mask[3e + j]: component (or Galois-ring share) j of the P persons' eye-e codes,
+ * [P][l] uint16 (host, or device if src_is_device). Per person p the result is
+ *   (db_0 OR db_1) OR (batch_0 OR batch_1)
+ * with db_e the eye-e code against the eye-e database, and batch_e the eye-e code against the
+ * unrotated eye-e codes of the persons p' < p of the batch (later persons enter p's OR tree as
+ * the public 0, so of two duplicates the earlier one passes). The OR gates of the combination
+ * use Philox(seed_j, (p, 0, req, IPC_D_COMB<<24 | t)), bit 0 of word 0, t = 0 (db_0|db_1),
+ * 1 (batch_0|batch_1), 2 (root). Synchronous: writes the bit components [3][P] to host
+ * shares_out and the request ids of the five parts (db_0, db_1, batch_0, batch_1, combination)
+ * to req_ids. Errors as submit_queries / fetch_bit_shares; IPC_EINVAL for mismatched contexts.
+ */
+int ipc_check_persons(ipc_ctx* const ctx[2], const uint16_t* const code[6], const uint16_t* const mask[6], uint32_t P,
+                      int src_is_device, uint8_t* shares_out, uint64_t req_ids[5], int timeout_ms);
 
 /* ======================================================================== */
 /* Serving (A9): continuous batching over the resident database.           */

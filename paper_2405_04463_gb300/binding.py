@@ -109,6 +109,7 @@ _SIGS = {
     "ipc_ctx_stream": [_vp],
     "ipc_set_input_stream": [_vp, _vp],
     "ipc_measure_peak": [_int, _vp, ctypes.POINTER(ctypes.c_double)],
+    "ipc_check_persons": [_vp * 2, _vp * 6, _vp * 6, _u32, _int, _vp, _vp, _int],
     "ipc_serve_start": [_vp, ctypes.POINTER(ipc_serve_config)],
     "ipc_serve_submit": [_vp, _VP3, _VP3, _sz, ctypes.POINTER(_u64)],
     "ipc_serve_stop": [_vp],
@@ -401,3 +402,19 @@ def ipc_serve_first_fit(used, want) -> int:
     import numpy as np
     used = np.ascontiguousarray(used, dtype=np.uint8)
     return int(lib.ipc_serve_first_fit(ptr(used), len(used), want))
+
+
+# ---------------------------------------------------------------------------------------------
+# Both eyes and inner-batch matching
+# ---------------------------------------------------------------------------------------------
+
+def ipc_check_persons(ctx_eyes, code, mask, P, src_is_device, timeout_ms=-1):
+    """ctx_eyes: the two eyes' contexts; code, mask: 6 arrays each (eye-major, 3 components per
+    eye) [P][l] uint16. Returns (bit components [3][P] uint8, request ids of the 5 parts)."""
+    import numpy as np
+    out = np.zeros((3, P), np.uint8)
+    ids = (_u64 * 5)()
+    _check(lib.ipc_check_persons((_vp * 2)(*ctx_eyes), (_vp * 6)(*[ptr(a) for a in code]),
+                                 (_vp * 6)(*[ptr(a) for a in mask]), P, src_is_device, ptr(out),
+                                 ctypes.cast(ids, _vp), timeout_ms), ctx_eyes[0])
+    return out, list(ids)

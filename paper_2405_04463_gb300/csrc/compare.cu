@@ -127,6 +127,7 @@ struct CmpParams {
   const uint32_t* col_tiles;   // optional device list of tile_cols-wide column tiles
   const uint32_t* n_col_list;  // its length (device)
   uint32_t tile_cols;
+  const uint32_t* col_rows;    // optional per column: global rows >= col_rows[n] are the public 0
 };
 
 // Shared memory per thread (index [slot][threadIdx.x], conflict-free):
@@ -268,10 +269,16 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
     GateRng fa2{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc2{static_cast<uint32_t>(grow >> 5), tag, req, {}};
     bit_extract<31, MSB_GATE0>(P.seeds, fa2, rc2, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); },
                                msb, b30);
-    // rows past the end are the public 0 of the OR tree
-    msb.c0 &= lane_mask;
-    msb.c1 &= lane_mask;
-    msb.c2 &= lane_mask;
+    // rows past the end (and, with col_rows, rows past the column's limit) are the public 0
+    // of the OR tree
+    uint32_t keep = lane_mask;
+    if (P.col_rows) {
+      const uint64_t lim = P.col_rows[n];
+      keep &= lim <= grow ? 0u : (lim - grow >= 32 ? 0xFFFFFFFFu : ((1u << (lim - grow)) - 1u));
+    }
+    msb.c0 &= keep;
+    msb.c1 &= keep;
+    msb.c2 &= keep;
     if (P.msb_out) {
       for (uint32_t l = 0; l < nvalid; ++l) {
         const uint64_t at = static_cast<uint64_t>(n) * P.ld_msb + lrow + l;
@@ -399,7 +406,7 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
                          uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
                          const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
                          uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
-                         uint32_t tile_cols, cudaStream_t st) {
+                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows) {
   CmpParams P;
   for (int j = 0; j < 3; ++j) {
     P.zc[j] = z_code[j];
@@ -421,6 +428,7 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
   P.col_tiles = col_tiles;
   P.n_col_list = n_col_list;
   P.tile_cols = tile_cols;
+  P.col_rows = col_rows;
   const uint64_t threads = static_cast<uint64_t>(n_cols) * P.n_blocks;
   const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
   static std::once_flag once;
@@ -438,7 +446,7 @@ int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask
                    size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
                    uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, cudaStream_t st) {
   return compare_launch_tiles(z_code, z_mask, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, p, roots, ld_roots,
-                              msb_out, ld_msb, nullptr, nullptr, 0, st);
+                              msb_out, ld_msb, nullptr, nullptr, 0, st, nullptr);
 }
 
 // plane: words between the three components' root planes (n_cols * ld_roots for a stand-alone
@@ -452,6 +460,36 @@ int or_finalize_strided(uint32_t* roots, size_t ld_roots, size_t plane, uint32_t
   or_rows_kernel<<<(n_cols + 127) / 128, 128, 0, st>>>(roots, ld_roots, plane, n_cols, n_blocks, p, col_tags, sd);
   IPC_CUDA_TRY(cudaGetLastError());
   or_queries_kernel<<<(Q + 63) / 64, 64, 0, st>>>(roots, ld_roots, plane, Q, R, col_tags, sd, bit_shares);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+// Per person: (b0 OR b1) OR (b2 OR b3) on boolean sharings; gate t (0: b0|b1, 1: b2|b3, 2: the
+// root) of person p takes its zero-share bits from bit 0 of word 0 of
+// Philox(seed_j, (p, 0, req, D_COMB << 24 | t)).
+__global__ void or_combine_kernel(const uint8_t* b0, const uint8_t* b1, const uint8_t* b2, const uint8_t* b3,
+                                  uint32_t P, uint32_t req, Seeds sd, uint8_t* out) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  auto load = [&](const uint8_t* b) { return B3{b[p] & 1u, b[P + p] & 1u, b[2 * P + p] & 1u}; };
+  auto gate = [&](const B3& x, const B3& y, uint32_t t) {
+    const uint32_t F0 = philox(p, 0u, req, (IPC_D_COMB << 24) | t, sd.s[0]).x & 1u;
+    const uint32_t F1 = philox(p, 0u, req, (IPC_D_COMB << 24) | t, sd.s[1]).x & 1u;
+    const uint32_t F2 = philox(p, 0u, req, (IPC_D_COMB << 24) | t, sd.s[2]).x & 1u;
+    return bx(bx(x, y), band(x, y, F0, F1, F2));
+  };
+  const B3 left = gate(load(b0), load(b1), 0), right = gate(load(b2), load(b3), 1);
+  const B3 root = gate(left, right, 2);
+  out[p] = root.c0 & 1u;
+  out[P + p] = root.c1 & 1u;
+  out[2 * P + p] = root.c2 & 1u;
+}
+
+int or_combine_launch(const uint8_t* const bits[4], uint32_t P, uint32_t req, const uint64_t seeds[3], uint8_t* out,
+                      cudaStream_t st) {
+  Seeds sd;
+  for (int j = 0; j < 3; ++j) sd.s[j] = seeds[j];
+  or_combine_kernel<<<(P + 127) / 128, 128, 0, st>>>(bits[0], bits[1], bits[2], bits[3], P, req, sd, out);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }

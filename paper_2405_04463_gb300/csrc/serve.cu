@@ -34,7 +34,7 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
                          uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
                          const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
                          uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
-                         uint32_t tile_cols, cudaStream_t st);
+                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows);
 int or_finalize_strided(uint32_t* roots, size_t ld_roots, size_t plane, uint32_t n_blocks, uint32_t p, uint32_t Q,
                         uint32_t R, const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares,
                         cudaStream_t st);
@@ -207,7 +207,7 @@ int compare(Server& S, int v, const Chunk& ch, cudaStream_t st) {
   const uint16_t* zm[3] = {z_plane(S, 1, 0), z_plane(S, 1, 1), z_plane(S, 1, 2)};
   return compare_launch_tiles(zc, zm, S.c->cfg.db_chunk_rows, S.pool_pad, ch.rows, ch.row0, S.tags, S.c->cfg.seeds,
                               S.c->cfg.thr_a, kLog2BlockWords, S.roots, S.ld_roots, nullptr, 0, S.list_dev[v],
-                              S.count_dev[v], S.variants[v].tile_cols, st);
+                              S.count_dev[v], S.variants[v].tile_cols, st, nullptr);
 }
 
 // The graph of one step: fork the party streams off the control stream, two GEMMs per party,
