@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--rates", default="0.3,0.6,0.9", help="arrival rates as fractions of the measured capacity")
     ap.add_argument("--pool", type=int, default=0, help="serving pool in query slots (0 = library default)")
     ap.add_argument("--capacity-requests", type=int, default=8)
+    ap.add_argument("--persons", action="store_true",
+                    help="both eyes + inner-batch matching (ipc_check_persons), the paper's deployed query shape")
+    ap.add_argument("--persons-rows", type=int, default=262144, help="database rows per eye")
+    ap.add_argument("--persons-batch", type=int, default=32)
+    ap.add_argument("--persons-path", default="tcg", choices=["tc", "tcg", "i8mix"])
     ap.add_argument("--serving-path", default="tc", choices=["tc", "tcg"],
                     help="tc: replicated-sharing dots; tcg: Galois-ring Shamir dots")
     return ap.parse_args()
@@ -552,8 +557,68 @@ def run_serving(args):
         "data": "synthetic"}), flush=True)
 
 
+def run_persons(args):
+    """Batches of P persons x 2 eyes x 31 rotations against a database per eye, plus the
+    inner-batch matching of each batch (Sec. 5.4), through ipc_check_persons with host inputs:
+    each call is synchronous and returns the persons' bit components, so the time per batch is
+    host wall time around the call."""
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    from paper_2405_04463_gb300.workload import encode_gpu, galois, load_workload, make_ctx
+
+    torch.cuda.set_device(0)
+    path, P, rows = args.persons_path, args.persons_batch, args.persons_rows
+    gal = galois(path)
+    eyes = [synth.Workload(f"eye {e}: {rows} rows", s=rows, Q=P, seed=0x1A150004 + 16 * e) for e in range(2)]
+    seeds = eyes[0].prf_seeds
+    ctxs = []
+    for w in eyes:
+        w.prf_seeds = seeds
+        c = make_ctx(w, path=path, max_queries=P)
+        load_workload(c, w, chunk=32768, galois_shares=gal)
+        ctxs.append(c)
+    rng = np.random.default_rng(0x9E75)
+    batches = []
+    for k in range(args.warmup + args.steps):
+        code, mask = [], []
+        for e in range(2):
+            qc = rng.integers(0, 2**63, size=(P, eyes[e].nwords), dtype=np.int64).view(np.uint64)
+            qm = rng.integers(0, 2**63, size=(P, eyes[e].nwords), dtype=np.int64).view(np.uint64)
+            c_, m_ = encode_gpu(qc, qm, eyes[e].l, eyes[e].q_share_seed, 1, galois_shares=gal)
+            code += [c_[j].cpu().numpy() for j in range(3)]
+            mask += [m_[j].cpu().numpy() for j in range(3)]
+        batches.append((code, mask))
+    for code, mask in batches[:args.warmup]:
+        ipc.ipc_check_persons(ctxs, code, mask, P, 0)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for code, mask in batches[args.warmup:]:
+        ipc.ipc_check_persons(ctxs, code, mask, P, 0)
+    dt = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    for c in ctxs:
+        ipc.ipc_destroy(c)
+    R = eyes[0].R
+    db_cmp = 2 * P * R * rows
+    batch_cmp = 2 * R * P * (P - 1) // 2
+    print(json.dumps({
+        "metric": "persons: both eyes x 31 rotations against the database + inner-batch matching",
+        "value": (db_cmp + batch_cmp) / dt, "unit": "comparisons/s", "ms_per_batch": 1e3 * dt,
+        "persons_per_s": P / dt, "steps": args.steps, "warmup": args.warmup,
+        "config": {"persons": P, "eyes": 2, "rotations": R, "db_rows_per_eye": rows, "path": path,
+                   "comparisons_per_batch": {"database": db_cmp, "inner_batch": batch_cmp},
+                   "inputs": "host query shares, copied inside the call (e2e)"},
+        "clocks": clk, "data": "synthetic"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.persons:
+        run_persons(args)
+        return
     if args.serving:
         run_serving(args)
         return
