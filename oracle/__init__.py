@@ -124,6 +124,9 @@ def _declare(L):
     L.orc_mpc_dot_galois.argtypes = [C, _p(u16), u64, _p(u16), u64, u32, u32, u32, u32, u32, _p(u16), S]
     L.orc_mpc_match_galois.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
                                        _p(u16), _p(u16), _p(u8), _p(u8), S]
+    L.orc_mpc_compare_plain.argtypes = [C, _p(u16), u32, u32, u32, u32, _p(u8), S]
+    L.orc_mpc_match_plain.argtypes = [C, G, ctypes.c_int, _p(u16), _p(u64), u32, _p(u16), _p(u64), u32,
+                                      _p(u16), _p(u16), _p(u8), S]
     L.orc_mpc_match_batch.argtypes = [C, G, ctypes.c_int, _p(u16), _p(u16), u32, _p(u8), S]
     L.orc_or_combine.argtypes = [C, _p(u8), u32, _p(u8), S]
     L.orc_mpc_match.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
@@ -341,6 +344,39 @@ def mpc_match_galois(cfg: MpcCfg, g: Geom, db_code, db_mask, q_code, q_mask, wan
                      want_msb: bool = False):
     """mpc_match with the dot products on Galois-ring Shamir shares (encode_share_galois)."""
     return _mpc_match(lib().orc_mpc_match_galois, cfg, g, db_code, db_mask, q_code, q_mask, want_z, want_msb)
+
+
+# ---- protocol 1 (Sec. 4, Alg. 2): shared codes, public masks ----
+
+def mpc_compare_plain(cfg: MpcCfg, dot, ml: int, q: int = 0, rho: int = 0, i: int = 0,
+                      stats: Stats | None = None):
+    """MSB(floor(a ml / 2^16) - dot) on the dot components dot[3] with public ml -> msb[3]."""
+    d = np.ascontiguousarray(dot, dtype=np.uint16)
+    out = np.zeros(3, np.uint8)
+    st = stats if stats is not None else Stats()
+    lib().orc_mpc_compare_plain(ctypes.byref(cfg), _ptr(d, ctypes.c_uint16), ml, q, rho, i,
+                                _ptr(out, ctypes.c_uint8), ctypes.byref(st))
+    return out
+
+
+def mpc_match_plain(cfg: MpcCfg, g: Geom, db_code, db_mask_bits, q_code, q_mask_bits, galois: bool = False,
+                    want_z: bool = False):
+    """Alg. 2: code shares [3][n][l] (additive or Galois), plain mask bits [n][words]."""
+    db_code = np.ascontiguousarray(db_code, dtype=np.uint16)
+    q_code = np.ascontiguousarray(q_code, dtype=np.uint16)
+    dm = np.ascontiguousarray(db_mask_bits, dtype=np.uint64)
+    qm = np.ascontiguousarray(q_mask_bits, dtype=np.uint64)
+    s, Q = db_code.shape[1], q_code.shape[1]
+    n = Q * g.R
+    zc = np.zeros((3, n, s), np.uint16) if want_z else None
+    ml = np.zeros((n, s), np.uint16) if want_z else None
+    bits = np.zeros((3, Q), np.uint8)
+    st = Stats()
+    lib().orc_mpc_match_plain(ctypes.byref(cfg), ctypes.byref(g), int(galois), _ptr(db_code, ctypes.c_uint16),
+                              _ptr(dm, ctypes.c_uint64), s, _ptr(q_code, ctypes.c_uint16), _ptr(qm, ctypes.c_uint64),
+                              Q, _ptr(zc, ctypes.c_uint16), _ptr(ml, ctypes.c_uint16), _ptr(bits, ctypes.c_uint8),
+                              ctypes.byref(st))
+    return {"bits": bits, "z_code": zc, "ml": ml, "stats": st.as_dict()}
 
 
 # ---- both eyes and inner-batch matching (Sec. 5.4) ----

@@ -799,3 +799,63 @@ void orc_or_combine(const orc_mpc_cfg* cfg, const uint8_t* bits4, uint32_t P, ui
     for (int j = 0; j < 3; j++) out[(size_t)j * P + p] = (uint8_t)(rss_component(&r[2], j) & 1u);
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Protocol 1 (Sec. 4, Alg. 2): shared codes, public masks.                  */
+/* ------------------------------------------------------------------------ */
+void orc_mpc_compare_plain(const orc_mpc_cfg* cfg, const uint16_t dot[3], uint32_t ml, uint32_t q, uint32_t rho,
+                           uint32_t i, uint8_t msb[3], orc_stats* st) {
+  uint32_t t = (uint32_t)(((uint64_t)cfg->thr_a * ml) >> 16); /* floor(f ml), f = a / 2^16 */
+  /* public t enters through component 0; the dot product is reshared (one round deep) */
+  uint32_t v[3] = {(t - dot[0]) & 0xFFFFu, (0u - dot[1]) & 0xFFFFu, (0u - dot[2]) & 0xFFFFu};
+  rss_t V = rss_from_components(v, 1);
+  gate_rng g = {cfg, i >> 5, col_tag(q, rho), ORC_D_AND, i & 31u};
+  rss_t top, below;
+  uint64_t and0 = st->and_gates;
+  bit_extract_rss(&V, 15, &g, 0, &top, &below, st);
+  for (int j = 0; j < 3; j++) msb[j] = (uint8_t)rss_component(&top, j);
+  st->and_msb = (uint32_t)(st->and_gates - and0);
+  st->depth_msb = top.depth - V.depth;
+  st->depth_total = top.depth;
+}
+
+void orc_mpc_match_plain(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
+                         const uint16_t* db_code, const uint64_t* db_mask_bits, uint32_t s,
+                         const uint16_t* q_code, const uint64_t* q_mask_bits, uint32_t Q,
+                         uint16_t* z_code, uint16_t* ml_out, uint8_t* bits, orc_stats* st) {
+  uint32_t l = g->rows * g->cols * g->cell, nw = (l + 63) / 64, R = g->R;
+  uint64_t db_plane = (uint64_t)s * l, q_plane = (uint64_t)Q * l;
+  size_t zplane = (size_t)Q * R * s;
+  dot_fn dot = galois ? orc_mpc_dot_galois : orc_mpc_dot;
+  uint16_t* ry = (uint16_t*)malloc(sizeof(uint16_t) * 3 * l);
+  uint64_t* rm = (uint64_t*)malloc(sizeof(uint64_t) * nw);
+  uint8_t* msb = (uint8_t*)malloc(3 * (size_t)R * s + 1);
+  for (uint32_t q = 0; q < Q; q++) {
+    for (uint32_t rho = 0; rho < R; rho++) {
+      int32_t shift = g->rot_lo + (int32_t)rho;
+      for (int j = 0; j < 3; j++)
+        orc_rotate_u16(g, q_code + j * q_plane + (size_t)q * l, ry + (size_t)j * l, shift);
+      orc_rotate_bits(g, q_mask_bits + (size_t)q * nw, rm, shift);
+      size_t n = (size_t)q * R + rho;
+      for (uint32_t i = 0; i < s; i++) {
+        uint16_t zc[3];
+        dot(cfg, db_code + (size_t)i * l, db_plane, ry, l, l, q, rho, i, 0, zc, st);
+        uint32_t ml = 0; /* public: CountOnes(rot(m) AND M_i) */
+        for (uint32_t w = 0; w < nw; w++) ml += (uint32_t)popcount64(rm[w] & db_mask_bits[(size_t)i * nw + w]);
+        if (z_code)
+          for (int p = 0; p < 3; p++) z_code[p * zplane + n * s + i] = zc[p];
+        if (ml_out) ml_out[n * s + i] = (uint16_t)ml;
+        uint8_t b[3];
+        orc_mpc_compare_plain(cfg, zc, ml, q, rho, i, b, st);
+        for (int p = 0; p < 3; p++) msb[(size_t)p * R * s + (size_t)rho * s + i] = b[p];
+      }
+    }
+    uint8_t bit[3];
+    orc_or_tree(cfg, msb, R, s, q, bit, st);
+    if (bits)
+      for (int p = 0; p < 3; p++) bits[(size_t)p * Q + q] = bit[p];
+  }
+  free(ry);
+  free(rm);
+  free(msb);
+}

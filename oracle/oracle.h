@@ -177,6 +177,21 @@ void orc_mpc_match_batch(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
  * bits4: [4][3][P]; out: [3][P]. */
 void orc_or_combine(const orc_mpc_cfg* cfg, const uint8_t* bits4, uint32_t P, uint8_t* out, orc_stats* st);
 
+/* ---- Protocol 1 (Sec. 4, Alg. 2): shared codes, public masks ----
+ * ml = CountOnes(rot(m_q) AND M_i) is public; only the code dot product is shared. A match is
+ * MSB(t - <c', C'>) over Z_{2^16} with the public t = floor(a * ml / 2^16) (reading: the floor
+ * makes the test exactly <c', C'> > (a / 2^16) ml, Alg. 1's strict rule), added by component 0;
+ * BitExtract of bit 15 (29 ANDs, 15 rounds; gates from 0 in the D_AND counters). */
+void orc_mpc_compare_plain(const orc_mpc_cfg* cfg, const uint16_t dot[3], uint32_t ml, uint32_t q, uint32_t rho,
+                           uint32_t i, uint8_t msb[3], orc_stats* st);
+/* Alg. 2 for all queries: code shares [3][n][l] (additive components, or Galois-ring Shamir
+ * shares when galois != 0), masks as packed bits [n][ceil(l/64)]. Outputs (may be NULL):
+ * z_code [3][Q*R][s] (the dot-product components), ml [Q*R][s], bits [3][Q]. */
+void orc_mpc_match_plain(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
+                         const uint16_t* db_code, const uint64_t* db_mask_bits, uint32_t s,
+                         const uint16_t* q_code, const uint64_t* q_mask_bits, uint32_t Q,
+                         uint16_t* z_code, uint16_t* ml_out, uint8_t* bits, orc_stats* st);
+
 #ifdef __cplusplus
 }
 #endif
