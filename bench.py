@@ -265,7 +265,7 @@ def run_ours(args, w):
     import torch
 
     import paper_2405_04463_gb300 as ipc
-    from paper_2405_04463_gb300.workload import galois, load_workload, make_ctx, query_shares_gpu
+    from paper_2405_04463_gb300.workload import galois, load_workload, make_ctx, plain_mask_u16, query_shares_gpu
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -277,25 +277,26 @@ def run_ours(args, w):
     # ---- setup (untimed): resident database, query shares, contexts ----
     # headline: the tcgen05 path; beside it the two int8 mma.sync paths and the int32 path
     # plus the paper's deployed Galois-ring Shamir dot products on the same tcgen05 kernels
-    ctxs = {p: make_ctx(w, path=p, max_queries=w.Q) for p in ("tc", "tcg", "i8mix", "i8mma")}
-    if not args.no_i32:
-        ctxs["i32"] = make_ctx(w, path="i32", max_queries=w.Q)
-    for p, c in ctxs.items():
-        load_workload(c, w, chunk=32768, galois_shares=galois(p))
+    # (the other paths' contexts are made one at a time below, each freed after its run)
+    ctxs = {"tc": make_ctx(w, path="tc", max_queries=w.Q)}
+    load_workload(ctxs["tc"], w, chunk=32768)
     qcode, qmask = query_shares_gpu(w)
     gqcode, gqmask = query_shares_gpu(w, galois_shares=True)
+    pqmask = plain_mask_u16(w.query_bits()[1], w.l)
     hcode = [qcode[j].cpu().pin_memory() for j in range(3)]
     hmask = [qmask[j].cpu().pin_memory() for j in range(3)]
     torch.cuda.synchronize()
     n_chunks = (w.s + 65535) // 65536
     launches_per_step = 6 + n_chunks * 7 + 2
 
-    def run_steps(ctx, k, host_inputs, gal=False):
+    def run_steps(ctx, k, host_inputs, gal=False, plain=False):
         stream = torch.cuda.ExternalStream(ipc.ipc_ctx_stream(ctx))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         qc_, qm_ = (gqcode, gqmask) if gal else (qcode, qmask)
         code = hcode if host_inputs else [qc_[j] for j in range(3)]
         mask = hmask if host_inputs else [qm_[j] for j in range(3)]
+        if plain:
+            mask = [pqmask, None, None]
         bits = np.zeros(w.Q, np.uint8)
         torch.cuda.synchronize()
         if world > 1:
@@ -325,17 +326,24 @@ def run_ours(args, w):
     run_steps(main, 1, True)
     ms_e2e, wall_e2e, bits_e2e = run_steps(main, args.steps, True)
 
-    def other(path):
+    def other(path, plain=False):
         gal = galois(path)
-        run_steps(ctxs[path], 1, False, gal)
-        ms, _, b = run_steps(ctxs[path], args.steps, False, gal)
+        ctx = make_ctx(w, path=path, max_queries=w.Q, plain_mask=plain)
+        try:
+            load_workload(ctx, w, chunk=32768, galois_shares=gal, plain_mask=plain)
+            run_steps(ctx, 1, False, gal, plain)
+            ms, _, b = run_steps(ctx, args.steps, False, gal, plain)
+        finally:
+            ipc.ipc_destroy(ctx)
         return {"value": w.comparisons * world / (ms * 1e-3), "ms_per_step": ms,
                 "bits_equal_to_headline_path": bool((b == bits).all())}
 
     out_gal = other("tcg")
+    out_plain = other("tc", plain=True)
+    out_plain_gal = other("tcg", plain=True)
     out_mix = other("i8mix")
     out_mma = other("i8mma")
-    out_i32 = other("i32") if "i32" in ctxs else None
+    out_i32 = other("i32") if not args.no_i32 else None
 
     # ---- each ring-GEMM kernel alone: one launch over a 65536-row chunk, all query columns ----
     l, N = w.l, w.Q * w.R
@@ -431,6 +439,9 @@ def run_ours(args, w):
         "galois_shamir_path": dict(out_gal, note="the paper's deployed sharing of the dot products "
                                                  "(Sec. 4.3.2): one length-l GEMM per party and vector "
                                                  "instead of 2l, same tcgen05 kernel, same comparison phase"),
+        "plain_mask_path": dict(out_plain, galois_shamir=out_plain_gal,
+                                note="protocol 1 (Sec. 4, Alg. 2): public masks, ml one plaintext GEMM "
+                                     "(K = l) instead of three shared ones, 16-bit comparison (29 ANDs)"),
         "int8_mix_path": out_mix,
         "int8_tensor_only_path": out_mma,
         "int32_path": out_i32,

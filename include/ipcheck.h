@@ -276,6 +276,23 @@ int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3]
                 void* stream);
 
 /*
+ * A4-A7 of protocol 1 (Sec. 4, Alg. 2: the masks are public) -- the comparison
+ * with a public mask length. ml: [n_cols][ldz] uint16, the plaintext ml of each
+ * comparison (the same value at every party); z_code as in ipc_compare. For
+ * every column n and row r < n_rows: t = floor(thr_a * ml / 2^16) (public;
+ * since dot is an integer, dot < thr_a * ml / 2^16 iff dot < t, which is why
+ * the floor and not the lemma's ceiling), v = t - dot over Z_{2^16} with t entering
+ * component 0, and MSB(v) by BitExtract(v, {15}) (29 ANDs; App. D) with gates
+ * G = 0..28 (positions 0..14, then ripple positions 1..14) drawn as in
+ * ipc_compare. MSB = 1 means a match. Block roots, msb_out, row0 alignment and
+ * errors as in ipc_compare; ml must be 16-byte aligned.
+ */
+int ipc_compare_plain(const uint16_t* const z_code[3], const uint16_t* ml, size_t ldz, uint32_t n_cols,
+                      size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3],
+                      uint32_t thr_a, uint32_t log2_block_words, uint32_t* roots, size_t ld_roots,
+                      uint8_t* msb_out, size_t ld_msb, void* stream);
+
+/*
  * A8 -- rest of the OR tree (Sec. 4.2: x OR y = x + y + xy, evaluated as a
  * binary tree). The tree has a fixed shape so that shares do not depend on
  * launch shapes: per column, the 32-row words g = 0, 1, ... are combined
@@ -333,6 +350,11 @@ typedef struct {
   uint64_t seeds[3];        /* pairwise PRF seeds; seeds[j] shared by parties j and j+1 */
   uint32_t keep_distances;  /* nonzero: keep each request's dot products for fetch_distances */
   int32_t device;           /* CUDA device ordinal */
+  uint32_t plain_mask;      /* nonzero: protocol 1 (Sec. 4, Alg. 2), masks public (IPC_PATH_TC or
+                               IPC_PATH_TCG): load_db_shares and submit_queries take the plain
+                               mask bits as 0/1 uint16 in mask[0] (mask[1], mask[2] unused); ml is
+                               a plaintext GEMM and a match is MSB(floor(thr_a ml / 2^16) - dot),
+                               a 16-bit BitExtract. Not for serving or ipc_check_persons. */
 } ipc_config;
 
 /* Creates a context on cfg->device with per-party streams. Ownership of *out

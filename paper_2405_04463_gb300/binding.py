@@ -46,7 +46,8 @@ def iris_geom(rot_lo: int = -15, R: int = 31) -> ipc_geom:
 class ipc_config(ctypes.Structure):
     _fields_ = [("geom", ipc_geom), ("thr_a", ctypes.c_uint32), ("path", ctypes.c_int32),
                 ("db_chunk_rows", ctypes.c_uint32), ("max_queries", ctypes.c_uint32),
-                ("seeds", ctypes.c_uint64 * 3), ("keep_distances", ctypes.c_uint32), ("device", ctypes.c_int32)]
+                ("seeds", ctypes.c_uint64 * 3), ("keep_distances", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("plain_mask", ctypes.c_uint32)]
 
 
 IPC_SERVE_AUTOTUNE = -1
@@ -93,6 +94,7 @@ _SIGS = {
     "ipc_ring_gemm_tiles": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
                             _u64, _vp, _vp, _vp],
     "ipc_compare": [_VP3, _VP3, _sz, _u32, _sz, _u64, _vp, _U64x3, _u32, _u32, _vp, _sz, _vp, _sz, _vp],
+    "ipc_compare_plain": [_VP3, _vp, _sz, _u32, _sz, _u64, _vp, _U64x3, _u32, _u32, _vp, _sz, _vp, _sz, _vp],
     "ipc_or_finalize": [_vp, _sz, _u32, _u32, _u32, _u32, _vp, _U64x3, _vp, _vp],
     "ipc_status": [],
     "ipc_compare_or_noalloc": [_VP3, _VP3, _sz, _u32, _u32, _sz, _vp, _U64x3, _u32, _vp, _vp],
@@ -247,6 +249,13 @@ def ipc_compare(z_code, z_mask, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_
                            ptr(roots), ld_roots, ptr(msb_out), ld_msb, _stream(stream)))
 
 
+def ipc_compare_plain(z_code, ml, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, log2_block_words, roots,
+                      ld_roots, msb_out=None, ld_msb=0, stream=None):
+    _check(lib.ipc_compare_plain(_VP3(*[ptr(a) for a in z_code]), ptr(ml), ldz, n_cols, n_rows, row0, ptr(col_tags),
+                                 _U64x3(*[s & (2**64 - 1) for s in seeds]), thr_a, log2_block_words, ptr(roots),
+                                 ld_roots, ptr(msb_out), ld_msb, _stream(stream)))
+
+
 def ipc_or_finalize(roots, ld_roots, n_blocks, log2_block_words, Q, R, col_tags, seeds, bit_shares, stream=None):
     _check(lib.ipc_or_finalize(ptr(roots), ld_roots, n_blocks, log2_block_words, Q, R, ptr(col_tags),
                                _U64x3(*[s & (2**64 - 1) for s in seeds]), ptr(bit_shares), _stream(stream)))
@@ -268,7 +277,7 @@ def ipc_status():
 
 def make_config(geom: ipc_geom | None = None, thr_a: int = 16384, path="i8mma", db_chunk_rows: int = 0,
                 max_queries: int = 0, seeds=(0x51EED0, 0x51EED1, 0x51EED2), keep_distances: bool = False,
-                device: int = 0) -> ipc_config:
+                device: int = 0, plain_mask: bool = False) -> ipc_config:
     c = ipc_config()
     c.geom = geom if geom is not None else iris_geom()
     c.thr_a = thr_a
@@ -279,6 +288,7 @@ def make_config(geom: ipc_geom | None = None, thr_a: int = 16384, path="i8mma", 
         c.seeds[j] = seeds[j] & (2**64 - 1)
     c.keep_distances = 1 if keep_distances else 0
     c.device = device
+    c.plain_mask = 1 if plain_mask else 0
     return c
 
 

@@ -143,6 +143,11 @@ __device__ __forceinline__ B3 bor(const Seeds& sd, const B3& a, const B3& b, uin
   return bx(bx(a, b), band(a, b, F0, F1, F2));
 }
 
+// PLAIN (protocol 1, Sec. 4, Alg. 2): zm[0] holds the public ml of each comparison (all three
+// pointers may point to it); v = floor(a ml / 2^16) - dot over Z_{2^16}, the public term entering
+// component 0, and the match bit is BitExtract(v, {15}) (29 ANDs, gates from 0). Otherwise the
+// shared-mask comparison: Lift of ml, ConstLift of dot, BitExtract(v, {31}).
+template <bool PLAIN>
 __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
   extern __shared__ uint32_t sm[];  // [S_WORDS][CT]
   const uint32_t tid = threadIdx.x;
@@ -200,75 +205,101 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
         }
       }
     }
-    // ---- ShareSplit of ml: bit-slice each component (bits 0..15) ----
+    B3 msb, b30;
+    if constexpr (PLAIN) {
+      // ---- v = t - dot, t = floor(a ml / 2^16) public (component 0); bit-slice; MSB of 16 bits ----
+      for (uint32_t l = 0; l < 32; ++l) {
+        const uint32_t mlw = S(S_RAWML + (l >> 1));
+        const uint32_t ml = (mlw >> (16 * (l & 1))) & 0xFFFFu;
+        const uint32_t t = (P.thr_a * ml) >> 16;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      uint32_t a[32];
-#pragma unroll
-      for (int v = 0; v < 16; ++v) {
-        const uint32_t x = S(S_RAWML + 16 * j + v);
-        a[2 * v] = x & 0xFFFFu;
-        a[2 * v + 1] = x >> 16;
-      }
-      transpose32(a);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) S(S_X + 16 * j + b) = a[b];
-    }
-    GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
-    B3 r17, r16;
-    bit_extract<17, LIFT_GATE0>(
-        P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return b < 16 ? S(S_X + 16 * j + b) : 0u; }, r17, r16);
-    // ---- per comparison: BitInject (3-party OT), ConstLift, v = a*ml' - 2^16*dot ----
-    uint4 q0w = make_uint4(0u, 0u, 0u, 0u);  // D_INJ0 words: one Philox call per 4 rows
-    for (uint32_t l = 0; l < 32; ++l) {
-      const uint64_t g = grow + l;
-      if ((l & 3u) == 0) q0w = philox(static_cast<uint32_t>(g >> 2), tag, req, IPC_D_INJ0 << 24, P.seeds.s[0]);
-      const uint32_t inj0 = word_of(q0w, l & 3u);
-      const uint4 w2 = philox(static_cast<uint32_t>(g), tag, req, IPC_D_INJ2 << 24, P.seeds.s[2]);
-      uint32_t A[3], Bv[3];
-#pragma unroll
-      for (int which = 0; which < 2; ++which) {
-        const uint32_t k = which == 0 ? 15u : 16u;
-        const uint32_t mask = (1u << k) - 1u;
-        const uint32_t sh = which == 0 ? 0u : 16u;
-        const B3& bit = which == 0 ? r17 : r16;
-        const uint32_t x0 = (bit.c0 >> l) & 1u, x1 = (bit.c1 >> l) & 1u, x2 = (bit.c2 >> l) & 1u;
-        const uint32_t c0 = (inj0 >> sh) & mask, c2 = (w2.x >> sh) & mask;
-        const uint32_t w0 = (w2.y >> sh) & mask, w1 = (w2.z >> sh) & mask;
-        // party 0 (OT sender): m_beta = (beta ^ x_0 ^ x_2) - c_0 - c_2, masked k_beta = w_beta ^ m_beta
-        const uint32_t m0 = ((0u ^ x0 ^ x2) - c0 - c2) & mask;
-        const uint32_t m1 = ((1u ^ x0 ^ x2) - c0 - c2) & mask;
-        const uint32_t k0 = w0 ^ m0, k1 = w1 ^ m1;
-        // party 2 (helper) sends w_{x_1}; party 1 (receiver) unmasks k_{x_1}
-        const uint32_t wsel = x1 ? w1 : w0;
-        const uint32_t c1 = (wsel ^ (x1 ? k1 : k0)) & mask;
-        uint32_t* out = which == 0 ? A : Bv;
-        out[0] = c0;
-        out[1] = c1;
-        out[2] = c2;
+        for (int j = 0; j < 3; ++j) {
+          const uint32_t dw = S(S_RAWDOT + 16 * j + (l >> 1));
+          const uint32_t dt = (dw >> (16 * (l & 1))) & 0xFFFFu;
+          S(S_X + 32 * j + l) = ((j == 0 ? t : 0u) - dt) & 0xFFFFu;
+        }
       }
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const uint32_t mlw = S(S_RAWML + 16 * j + (l >> 1)), dw = S(S_RAWDOT + 16 * j + (l >> 1));
-        const uint32_t ml = (mlw >> (16 * (l & 1))) & 0xFFFFu, dt = (dw >> (16 * (l & 1))) & 0xFFFFu;
-        const uint32_t mll = ml - (A[j] << 17) - (Bv[j] << 16);
-        S(S_X + 32 * j + l) = P.thr_a * mll - (dt << 16);
+        uint32_t a[32];
+#pragma unroll
+        for (int v = 0; v < 32; ++v) a[v] = S(S_X + 32 * j + v);
+        transpose32(a);
+#pragma unroll
+        for (int v = 0; v < 16; ++v) S(S_X + 32 * j + v) = a[v];
       }
+      GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
+      bit_extract<15, 0>(P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); }, msb, b30);
+    } else {
+      // ---- ShareSplit of ml: bit-slice each component (bits 0..15) ----
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uint32_t a[32];
+#pragma unroll
+        for (int v = 0; v < 16; ++v) {
+          const uint32_t x = S(S_RAWML + 16 * j + v);
+          a[2 * v] = x & 0xFFFFu;
+          a[2 * v + 1] = x >> 16;
+        }
+        transpose32(a);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) S(S_X + 16 * j + b) = a[b];
+      }
+      GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
+      B3 r17, r16;
+      bit_extract<17, LIFT_GATE0>(
+          P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return b < 16 ? S(S_X + 16 * j + b) : 0u; }, r17, r16);
+      // ---- per comparison: BitInject (3-party OT), ConstLift, v = a*ml' - 2^16*dot ----
+      uint4 q0w = make_uint4(0u, 0u, 0u, 0u);  // D_INJ0 words: one Philox call per 4 rows
+      for (uint32_t l = 0; l < 32; ++l) {
+        const uint64_t g = grow + l;
+        if ((l & 3u) == 0) q0w = philox(static_cast<uint32_t>(g >> 2), tag, req, IPC_D_INJ0 << 24, P.seeds.s[0]);
+        const uint32_t inj0 = word_of(q0w, l & 3u);
+        const uint4 w2 = philox(static_cast<uint32_t>(g), tag, req, IPC_D_INJ2 << 24, P.seeds.s[2]);
+        uint32_t A[3], Bv[3];
+#pragma unroll
+        for (int which = 0; which < 2; ++which) {
+          const uint32_t k = which == 0 ? 15u : 16u;
+          const uint32_t mask = (1u << k) - 1u;
+          const uint32_t sh = which == 0 ? 0u : 16u;
+          const B3& bit = which == 0 ? r17 : r16;
+          const uint32_t x0 = (bit.c0 >> l) & 1u, x1 = (bit.c1 >> l) & 1u, x2 = (bit.c2 >> l) & 1u;
+          const uint32_t c0 = (inj0 >> sh) & mask, c2 = (w2.x >> sh) & mask;
+          const uint32_t w0 = (w2.y >> sh) & mask, w1 = (w2.z >> sh) & mask;
+          // party 0 (OT sender): m_beta = (beta ^ x_0 ^ x_2) - c_0 - c_2, masked k_beta = w_beta ^ m_beta
+          const uint32_t m0 = ((0u ^ x0 ^ x2) - c0 - c2) & mask;
+          const uint32_t m1 = ((1u ^ x0 ^ x2) - c0 - c2) & mask;
+          const uint32_t k0 = w0 ^ m0, k1 = w1 ^ m1;
+          // party 2 (helper) sends w_{x_1}; party 1 (receiver) unmasks k_{x_1}
+          const uint32_t wsel = x1 ? w1 : w0;
+          const uint32_t c1 = (wsel ^ (x1 ? k1 : k0)) & mask;
+          uint32_t* out = which == 0 ? A : Bv;
+          out[0] = c0;
+          out[1] = c1;
+          out[2] = c2;
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const uint32_t mlw = S(S_RAWML + 16 * j + (l >> 1)), dw = S(S_RAWDOT + 16 * j + (l >> 1));
+          const uint32_t ml = (mlw >> (16 * (l & 1))) & 0xFFFFu, dt = (dw >> (16 * (l & 1))) & 0xFFFFu;
+          const uint32_t mll = ml - (A[j] << 17) - (Bv[j] << 16);
+          S(S_X + 32 * j + l) = P.thr_a * mll - (dt << 16);
+        }
+      }
+      // ---- MSB: bit-slice v and BitExtract(v, {31}) ----
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uint32_t a[32];
+#pragma unroll
+        for (int v = 0; v < 32; ++v) a[v] = S(S_X + 32 * j + v);
+        transpose32(a);
+#pragma unroll
+        for (int v = 0; v < 32; ++v) S(S_X + 32 * j + v) = a[v];
+      }
+      GateRng fa2{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc2{static_cast<uint32_t>(grow >> 5), tag, req, {}};
+      bit_extract<31, MSB_GATE0>(P.seeds, fa2, rc2, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); },
+                                 msb, b30);
     }
-    // ---- MSB: bit-slice v and BitExtract(v, {31}) ----
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      uint32_t a[32];
-#pragma unroll
-      for (int v = 0; v < 32; ++v) a[v] = S(S_X + 32 * j + v);
-      transpose32(a);
-#pragma unroll
-      for (int v = 0; v < 32; ++v) S(S_X + 32 * j + v) = a[v];
-    }
-    B3 msb, b30;
-    GateRng fa2{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc2{static_cast<uint32_t>(grow >> 5), tag, req, {}};
-    bit_extract<31, MSB_GATE0>(P.seeds, fa2, rc2, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); },
-                               msb, b30);
     // rows past the end (and, with col_rows, rows past the column's limit) are the public 0
     // of the OR tree
     uint32_t keep = lane_mask;
@@ -406,7 +437,7 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
                          uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
                          const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
                          uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
-                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows) {
+                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows, bool plain) {
   CmpParams P;
   for (int j = 0; j < 3; ++j) {
     P.zc[j] = z_code[j];
@@ -434,10 +465,18 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [smem] {
-    attr = cudaFuncSetAttribute(compare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    attr = cudaFuncSetAttribute(compare_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(compare_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem));
   });
   IPC_CUDA_TRY(attr);
-  compare_kernel<<<static_cast<unsigned>((threads + CT - 1) / CT), CT, smem, st>>>(P);
+  const unsigned grid = static_cast<unsigned>((threads + CT - 1) / CT);
+  if (plain)
+    compare_kernel<true><<<grid, CT, smem, st>>>(P);
+  else
+    compare_kernel<false><<<grid, CT, smem, st>>>(P);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
@@ -446,7 +485,7 @@ int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask
                    size_t n_rows, uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
                    uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, cudaStream_t st) {
   return compare_launch_tiles(z_code, z_mask, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, p, roots, ld_roots,
-                              msb_out, ld_msb, nullptr, nullptr, 0, st, nullptr);
+                              msb_out, ld_msb, nullptr, nullptr, 0, st, nullptr, false);
 }
 
 // plane: words between the three components' root planes (n_cols * ld_roots for a stand-alone

@@ -132,6 +132,9 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
     return fail(nullptr, IPC_EINVAL, "ipc_create: path");
   if (cfg->path == IPC_PATH_TCG && (l % 256 != 0 || g.cell % 2 != 0))
     return fail(nullptr, IPC_EINVAL, "ipc_create: Galois-ring shares need l % 256 == 0 and an even cell size");
+  if (cfg->plain_mask && ((cfg->path != IPC_PATH_TC && cfg->path != IPC_PATH_TCG) || l % 256 != 0 || g.cell % 2 != 0))
+    return fail(nullptr, IPC_EINVAL,
+                "ipc_create: plain masks (protocol 1) need the tc or tcg path, l % 256 == 0 and an even cell size");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
   ipc_ctx* c = new ipc_ctx();
   c->cfg = *cfg;
@@ -200,8 +203,9 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
                               size_t n_rows, int src_is_device) {
   if (!c || !code || !mask) return fail(c, IPC_EINVAL, "load_db_shares: null argument");
   if (c->srv) return fail(c, IPC_EINVAL, "load_db_shares: the context is serving");
+  const int mask_parts = c->cfg.plain_mask ? 1 : 3;
   for (int j = 0; j < 3; ++j)
-    if (!code[j] || !mask[j]) return fail(c, IPC_EINVAL, "load_db_shares: null component");
+    if (!code[j] || (j < mask_parts && !mask[j])) return fail(c, IPC_EINVAL, "load_db_shares: null component");
   if (n_rows == 0) return IPC_OK;
   CTX_TRY(c, cudaSetDevice(c->cfg.device));
   const size_t cap = c->cfg.db_chunk_rows, l = c->l;
@@ -245,7 +249,7 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
       }
     const size_t take = std::min(n_rows - done, ch->cap - ch->rows);
     for (int vec = 0; vec < 2; ++vec)
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 0; j < (vec == 0 ? 3 : mask_parts); ++j) {
         const uint16_t* src = (vec == 0 ? code[j] : mask[j]) + done * l;
         CTX_TRY(c, cudaMemcpyAsync(c->stage, src, take * l * sizeof(uint16_t), kind, c->sc));
         uint8_t* lo = plane(c, *ch, j, vec, 0) + ch->rows * l * c->esz;
@@ -272,6 +276,10 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
     return fail(c, IPC_EINVAL, "submit_queries: n_queries must be in 1..max_queries");
   if (c->srv) return fail(c, IPC_EINVAL, "submit_queries: the context is serving; use ipc_serve_submit");
   if (c->rows == 0) return fail(c, IPC_EINVAL, "submit_queries: no database rows loaded");
+  const bool plain = c->cfg.plain_mask != 0;
+  const int mask_parts = plain ? 1 : 3;
+  for (int j = 0; j < 3; ++j)
+    if (!code[j] || (j < mask_parts && !mask[j])) return fail(c, IPC_EINVAL, "submit_queries: null component");
   CTX_TRY(c, cudaSetDevice(c->cfg.device));
   const ipc_geom& g = c->cfg.geom;
   const uint32_t l = c->l, Q = static_cast<uint32_t>(n_queries), R = g.R, N = Q * R;
@@ -322,7 +330,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CTX_TRY(c, cudaMemcpyAsync(r.tags, tags.data(), tags.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
   for (int vec = 0; vec < 2; ++vec)
-    for (int j = 0; j < 3; ++j)
+    for (int j = 0; j < (vec == 0 ? 3 : mask_parts); ++j)
       CTX_TRY(c, cudaMemcpyAsync(r.qstage + (static_cast<size_t>(vec) * 3 + j) * Q * l, vec == 0 ? code[j] : mask[j],
                                  static_cast<size_t>(Q) * l * sizeof(uint16_t), kind, c->sc));
   CTX_TRY(c, cudaEventRecord(c->ev_setup, c->sc));
@@ -333,7 +341,12 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
     CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
     for (int vec = 0; vec < 2; ++vec) {
       const uint16_t* y = r.qstage + static_cast<size_t>(vec) * 3 * Q * l;
-      if (c->cfg.path == IPC_PATH_TCG)
+      if (plain && vec == 1) {
+        // protocol 1: the rotated public query mask, prepared once (party 0's stream runs the ml GEMM)
+        if (i == 0)
+          CTX_RC(c, prep_query_rotate_plain(y, Q, &g, reinterpret_cast<uint16_t*>(bq(0, 1, 0)),
+                                            reinterpret_cast<uint16_t*>(bq(0, 1, 1)), n_pad, c->sp[0]));
+      } else if (c->cfg.path == IPC_PATH_TCG)
         CTX_RC(c, prep_query_galois_strided(y, static_cast<uint64_t>(Q) * l, Q, &g, i,
                                             reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
                                             reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
@@ -368,7 +381,17 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
       for (int vec = 0; vec < 2; ++vec) {
         uint16_t* zo = vec == 0 ? zc[i] : zm[i];
-        if (c->cfg.path == IPC_PATH_TCG) {
+        if (plain && vec == 1) {
+          // protocol 1: ml = <rotated query mask, database mask> in the clear, K = l; equal seeds
+          // make the zero share vanish
+          if (i != 0) continue;
+          auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
+          const uint16_t* xl[2] = {p16(plane(c, ch, 0, 1, 0)), p16(plane(c, ch, 0, 1, 0))};
+          const uint16_t* xh[2] = {p16(plane(c, ch, 0, 1, 1)), p16(plane(c, ch, 0, 1, 1))};
+          CTX_RC(c, ring_gemm_tc_variant(256, 1, xl, xh, ch.rows, p16(bq(0, 1, 0)), p16(bq(0, 1, 1)), N, n_pad, l,
+                                         r.tags, c->cfg.seeds[0], c->cfg.seeds[0], 1u, zo, ldz, ch.row0, nullptr,
+                                         nullptr, c->sp[0]));
+        } else if (c->cfg.path == IPC_PATH_TCG) {
           // Galois-ring Shamir: party i's own share only, K = l
           auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
           const uint16_t* xl[2] = {p16(plane(c, ch, i, vec, 0)), p16(plane(c, ch, i, vec, 0))};
@@ -396,9 +419,10 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       CTX_TRY(c, cudaStreamWaitEvent(c->sc, c->ev_gemm[i][set], 0));
     }
     const uint16_t* zcc[3] = {zc[0], zc[1], zc[2]};
-    const uint16_t* zmc[3] = {zm[0], zm[1], zm[2]};
-    CTX_RC(c, ipc_compare(zcc, zmc, ldz, N, ch.rows, ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a, kLog2BlockWords,
-                          r.roots, r.ld_roots, nullptr, 0, c->sc));
+    const uint16_t* zmc[3] = {zm[0], plain ? zm[0] : zm[1], plain ? zm[0] : zm[2]};
+    CTX_RC(c, compare_launch_tiles(zcc, zmc, ldz, N, ch.rows, ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a,
+                                   kLog2BlockWords, r.roots, r.ld_roots, nullptr, 0, nullptr, nullptr, 0, c->sc,
+                                   nullptr, plain));
     CTX_TRY(c, cudaEventRecord(c->ev_cmp[set], c->sc));
   }
   const uint32_t n_blocks =
@@ -454,8 +478,9 @@ extern "C" int fetch_distances(ipc_ctx* c, uint64_t req_id, uint32_t q, uint32_t
   const size_t n = static_cast<size_t>(q) * c->cfg.geom.R + rho, cnt = row_end - row_begin;
   std::vector<uint16_t> tmp(cnt);
   std::vector<uint32_t> acc[2] = {std::vector<uint32_t>(cnt, 0), std::vector<uint32_t>(cnt, 0)};
+  const bool plain = c->cfg.plain_mask != 0;
   for (int vec = 0; vec < 2; ++vec)
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < (plain && vec == 1 ? 1 : 3); ++i) {  // protocol 1 keeps ml itself in component 0
       const uint16_t* src = r.zkeep + ((static_cast<size_t>(vec) * 3 + i) * r.N + n) * r.zkeep_rows + row_begin;
       CTX_TRY(c, cudaMemcpy(tmp.data(), src, cnt * sizeof(uint16_t), cudaMemcpyDeviceToHost));
       for (size_t k = 0; k < cnt; ++k) acc[vec][k] += tmp[k];

@@ -47,6 +47,13 @@ int ctx_fail(ipc_ctx* c, int code, const std::string& msg);
 int ctx_cfail(ipc_ctx* c, cudaError_t e, const char* what);
 uint8_t* ctx_plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb);
 int ctx_check_device_status(ipc_ctx* c);
+int prep_query_rotate_plain(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint16_t* b_lo, uint16_t* b_hi,
+                            uint32_t n_pad, void* stream);
+int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
+                         uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
+                         const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
+                         uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
+                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows, bool plain);
 int prep_query_galois_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party,
                               uint16_t* b_lo, uint16_t* b_hi, uint32_t n_pad, void* stream);
 int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* const x_lo[2],

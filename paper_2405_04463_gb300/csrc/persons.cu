@@ -11,11 +11,6 @@
 #include "context.cuh"
 
 namespace ipc {
-int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
-                         uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
-                         const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
-                         uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
-                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows);
 int or_combine_launch(const uint8_t* const bits[4], uint32_t P, uint32_t req, const uint64_t seeds[3], uint8_t* out,
                       cudaStream_t st);
 }  // namespace ipc
@@ -174,7 +169,7 @@ int batch_part(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const 
   const uint16_t* zcc[3] = {zc[0], zc[1], zc[2]};
   const uint16_t* zmc[3] = {zm[0], zm[1], zm[2]};
   P_RC(compare_launch_tiles(zcc, zmc, ldz, N, P, 0, bb.tags, c->cfg.seeds, c->cfg.thr_a, kLog2BlockWords, bb.roots, nb,
-                            nullptr, 0, nullptr, nullptr, 0, st, bb.col_rows));
+                            nullptr, 0, nullptr, nullptr, 0, st, bb.col_rows, c->cfg.plain_mask != 0));
   P_RC(ipc_or_finalize(bb.roots, nb, nb, kLog2BlockWords, P, R, bb.tags, c->cfg.seeds, bb.bits, st));
   return IPC_OK;
 }
@@ -193,6 +188,7 @@ extern "C" int ipc_check_persons(ipc_ctx* const ctx[2], const uint16_t* const co
     return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: the two eyes' contexts must share path, geometry and seeds");
   if (ctx[0]->srv || ctx[1]->srv) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: a context is serving");
   if (ctx[0] == ctx[1]) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: one context per eye");
+  if (a.plain_mask || b.plain_mask) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: protocol 1 is not supported");
   if (P == 0 || P > a.max_queries || P > b.max_queries)
     return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: P must be in 1..max_queries");
   for (int k = 0; k < 6; ++k)

@@ -402,6 +402,22 @@ int prep_query_galois_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, c
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
+// Public operand of protocol 1: B[n][k] = bf16 of rot_rho(y[q])[k] for 0/1 values y [Q][l] (the
+// plain mask bits; K = l): the Galois preparation with lambda = 1 reads each element unchanged.
+int prep_query_rotate_plain(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint16_t* b_lo, uint16_t* b_hi,
+                            uint32_t n_pad, void* stream) {
+  if (!geom_ok(g) || g->cell % 2 != 0 || !y || !b_lo || !b_hi || Q == 0 || static_cast<uint64_t>(Q) * g->R > n_pad) {
+    set_error("plain-mask operand: invalid geometry (even cell) or n_pad < Q*R");
+    return IPC_EINVAL;
+  }
+  const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
+  const uint64_t total = static_cast<uint64_t>(n_pad) * l;
+  const uint32_t bs = 256;
+  prep_query_galois_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+      y, static_cast<uint64_t>(Q) * l, Q, *g, 0, Gr{1, 0}, b_lo, b_hi, n_pad);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
 }  // namespace ipc
 
 extern "C" int ipc_prep_query_galois(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party,

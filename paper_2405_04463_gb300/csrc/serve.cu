@@ -30,11 +30,6 @@ int ring_gemm_i8_variant(int variant, const int8_t* const x_lo[2], const int8_t*
                          const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
                          size_t ldz, uint64_t row0, const uint32_t* col_tiles, const uint32_t* n_col_list,
                          cudaStream_t stream);
-int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
-                         uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
-                         const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
-                         uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
-                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows);
 int or_finalize_strided(uint32_t* roots, size_t ld_roots, size_t plane, uint32_t n_blocks, uint32_t p, uint32_t Q,
                         uint32_t R, const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares,
                         cudaStream_t st);
@@ -207,7 +202,7 @@ int compare(Server& S, int v, const Chunk& ch, cudaStream_t st) {
   const uint16_t* zm[3] = {z_plane(S, 1, 0), z_plane(S, 1, 1), z_plane(S, 1, 2)};
   return compare_launch_tiles(zc, zm, S.c->cfg.db_chunk_rows, S.pool_pad, ch.rows, ch.row0, S.tags, S.c->cfg.seeds,
                               S.c->cfg.thr_a, kLog2BlockWords, S.roots, S.ld_roots, nullptr, 0, S.list_dev[v],
-                              S.count_dev[v], S.variants[v].tile_cols, st, nullptr);
+                              S.count_dev[v], S.variants[v].tile_cols, st, nullptr, S.c->cfg.plain_mask != 0);
 }
 
 // The graph of one step: fork the party streams off the control stream, two GEMMs per party,
@@ -594,6 +589,7 @@ extern "C" int ipc_serve_start(ipc_ctx* c, const ipc_serve_config* cfg) {
   if (c->srv) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: already serving");
   if (c->rows == 0) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: no database rows loaded");
   if (c->cfg.path == IPC_PATH_I32) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: the int32 path has no tile variants");
+  if (c->cfg.plain_mask) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: protocol 1 (plain masks) is not served");
   cudaError_t e = cudaSetDevice(c->cfg.device);
   if (e != cudaSuccess) return ctx_cfail(c, e, "cudaSetDevice");
   e = cudaDeviceSynchronize();

@@ -68,16 +68,28 @@ def db_bits_device(w: synth.Workload, row0: int, n: int):
     return code, mask
 
 
-def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=False):
-    """Generate the workload's database on the device, share it (A0) and load it (A1)."""
+def plain_mask_u16(mask_bits, l: int):
+    """Packed mask bits [n][words] (bit k of an iris in word k >> 6, bit k & 63; numpy or device
+    int64) -> device int16 [n][l] of 0/1: the public mask operand of protocol 1."""
+    torch = torch_mod()
+    mb = mask_bits if hasattr(mask_bits, "data_ptr") else dev_u64(mask_bits)
+    shifts = torch.arange(64, device=mb.device, dtype=torch.int64)
+    bits = (mb.unsqueeze(-1) >> shifts) & 1
+    return bits.reshape(mb.shape[0], -1)[:, :l].to(torch.int16).contiguous()
+
+
+def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=False, plain_mask=False):
+    """Generate the workload's database on the device, share it (A0) and load it (A1). With
+    plain_mask the masks stay public (protocol 1): mask[0] carries the 0/1 mask elements."""
     torch = torch_mod()
     ipc = lib()
     for r0 in range(0, w.s, chunk):
         n = min(chunk, w.s - r0)
         cb, mb = db_bits_device(w, r0, n)
         code, mask = encode_gpu(cb, mb, w.l, w.db_share_seed, 0, idx0=r0, galois_shares=galois_shares)
-        ipc.load_db_shares(ctx, [code[j] for j in range(3)], [mask[j] for j in range(3)], n, 1)
-        del code, mask
+        masks = [plain_mask_u16(mb, w.l), None, None] if plain_mask else [mask[j] for j in range(3)]
+        ipc.load_db_shares(ctx, [code[j] for j in range(3)], masks, n, 1)
+        del code, mask, masks
     torch.cuda.synchronize()
 
 
@@ -87,11 +99,11 @@ def query_shares_gpu(w: synth.Workload, qc=None, qm=None, galois_shares=False):
     return encode_gpu(qc, qm, w.l, w.q_share_seed, 1, galois_shares=galois_shares)
 
 
-def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0):
+def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0, plain_mask=False):
     ipc = lib()
     g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
     cfg = ipc.make_config(g, thr_a=w.thr_a, path=path, db_chunk_rows=chunk_rows, max_queries=max_queries or w.Q,
-                          seeds=w.prf_seeds, keep_distances=keep)
+                          seeds=w.prf_seeds, keep_distances=keep, plain_mask=plain_mask)
     ctx = ipc.ipc_create(cfg)
     ipc.ipc_set_input_stream(ctx)   # device inputs come from torch's current stream
     return ctx
