@@ -20,6 +20,8 @@ _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 D_SHARE, D_ZA, D_AND, D_INJ0, D_INJ2, D_OR = 1, 2, 3, 4, 5, 6
+D_SHARE32, D_ZA32 = 9, 10
+LIFT_CONST, LIFT_NONE = 1, 2   # lifting variants (Sec. 5.1, Sec. 6.2)
 LIFT_GATE0, MSB_GATE0 = 0, 36
 
 
@@ -131,6 +133,12 @@ def _declare(L):
     L.orc_or_combine.argtypes = [C, _p(u8), u32, _p(u8), S]
     L.orc_mpc_match.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
                                 _p(u16), _p(u16), _p(u8), _p(u8), S]
+    vp = ctypes.c_void_p
+    L.orc_encode_share32.argtypes = [_p(u64), _p(u64), u32, u32, u64, u32, u32, _p(u32), _p(u32)]
+    L.orc_mpc_dot32.argtypes = [C, _p(u32), u64, _p(u32), u64, u32, u32, u32, u32, u32, _p(u32), S]
+    L.orc_mpc_compare_liftfree.argtypes = [C, ctypes.c_int, _p(u32), _p(u32), u32, u32, u32, u32, _p(u8), _p(u32), S]
+    L.orc_mpc_match_lift.argtypes = [C, G, ctypes.c_int, u32, vp, _p(u32), u32, vp, _p(u32), u32, vp, _p(u32),
+                                     _p(u8), S]
     for f in ("orc_philox4x32_10", "orc_rotate_u16", "orc_rotate_bits", "orc_encode_share", "orc_plain_pair",
               "orc_plain_match", "orc_mpc_dot", "orc_mpc_compare", "orc_bit_extract", "orc_or_tree",
               "orc_mpc_match"):
@@ -414,3 +422,66 @@ def reconstruct_u16(shares) -> np.ndarray:
 def reconstruct_bits(shares) -> np.ndarray:
     s = np.asarray(shares).astype(np.uint8)
     return (s[0] ^ s[1] ^ s[2]) & 1
+
+
+# ---- lifting variants (Sec. 5.1, Sec. 6.2 Table 2): ConstLift and NoLift ----
+
+def encode_share32(code_bits, mask_bits, l: int, client_seed: int, side: int, idx0: int = 0):
+    """Masked-bit encoding and client sharing over Z_{2^32}: code, mask shares [3][n][l] u32."""
+    cb = np.ascontiguousarray(code_bits, dtype=np.uint64)
+    mb = np.ascontiguousarray(mask_bits, dtype=np.uint64)
+    n = cb.shape[0]
+    code = np.empty((3, n, l), np.uint32)
+    mask = np.empty((3, n, l), np.uint32)
+    lib().orc_encode_share32(_ptr(cb, ctypes.c_uint64), _ptr(mb, ctypes.c_uint64), n, l,
+                             client_seed & 0xFFFFFFFFFFFFFFFF, side, idx0,
+                             _ptr(code, ctypes.c_uint32), _ptr(mask, ctypes.c_uint32))
+    return code, mask
+
+
+def mpc_dot32(cfg: MpcCfg, x, y, q: int, rho: int, i: int, vec: int, stats: Stats | None = None):
+    """App. C dot over Z_{2^32} of DB share row x[3][l] with rotated query shares y[3][l] -> z[3]."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    l = x.shape[-1]
+    z = np.zeros(3, np.uint32)
+    st = stats if stats is not None else Stats()
+    lib().orc_mpc_dot32(ctypes.byref(cfg), _ptr(x, ctypes.c_uint32), l, _ptr(y, ctypes.c_uint32), l, l,
+                        q, rho, i, vec, _ptr(z, ctypes.c_uint32), ctypes.byref(st))
+    return z
+
+
+def mpc_compare_liftfree(cfg: MpcCfg, mode: int, dot, ml, thr_b: int = 0, q: int = 0, rho: int = 0, i: int = 0,
+                         stats: Stats | None = None):
+    """MSB(a ml - b dot) over Z_{2^32} without Lift: ml components over Z_{2^32}, dot components
+    over Z_{2^16} (LIFT_CONST) or Z_{2^32} (LIFT_NONE, b = thr_b). Returns (msb[3], v[3])."""
+    d = np.ascontiguousarray(np.asarray(dot, dtype=np.uint64).astype(np.uint32))
+    m = np.ascontiguousarray(np.asarray(ml, dtype=np.uint64).astype(np.uint32))
+    msb = np.zeros(3, np.uint8)
+    v = np.zeros(3, np.uint32)
+    st = stats if stats is not None else Stats()
+    lib().orc_mpc_compare_liftfree(ctypes.byref(cfg), mode, _ptr(d, ctypes.c_uint32), _ptr(m, ctypes.c_uint32),
+                                   thr_b, q, rho, i, _ptr(msb, ctypes.c_uint8), _ptr(v, ctypes.c_uint32),
+                                   ctypes.byref(st))
+    return msb, v
+
+
+def mpc_match_lift(cfg: MpcCfg, g: Geom, mode: int, db_code, db_mask, q_code, q_mask, thr_b: int = 0,
+                   want_z: bool = False):
+    """Alg. 3 with ConstLift (code shares u16, mask shares u32) or NoLift (both u32)."""
+    ct = np.uint32 if mode == LIFT_NONE else np.uint16
+    db_code = np.ascontiguousarray(db_code, dtype=ct)
+    q_code = np.ascontiguousarray(q_code, dtype=ct)
+    db_mask = np.ascontiguousarray(db_mask, dtype=np.uint32)
+    q_mask = np.ascontiguousarray(q_mask, dtype=np.uint32)
+    s, Q = db_code.shape[1], q_code.shape[1]
+    n = Q * g.R
+    zc = np.zeros((3, n, s), ct) if want_z else None
+    zm = np.zeros((3, n, s), np.uint32) if want_z else None
+    bits = np.zeros((3, Q), np.uint8)
+    st = Stats()
+    vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    lib().orc_mpc_match_lift(ctypes.byref(cfg), ctypes.byref(g), mode, thr_b, vp(db_code),
+                             _ptr(db_mask, ctypes.c_uint32), s, vp(q_code), _ptr(q_mask, ctypes.c_uint32), Q,
+                             vp(zc), _ptr(zm, ctypes.c_uint32), _ptr(bits, ctypes.c_uint8), ctypes.byref(st))
+    return {"bits": bits, "z_code": zc, "z_mask": zm, "stats": st.as_dict()}

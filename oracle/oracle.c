@@ -859,3 +859,155 @@ void orc_mpc_match_plain(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
   free(rm);
   free(msb);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Lifting variants (Sec. 5.1, Sec. 6.2 Table 2): ConstLift and NoLift.      */
+/* ------------------------------------------------------------------------ */
+void orc_encode_share32(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                        uint64_t client_seed, uint32_t side, uint32_t idx0, uint32_t* code_sh, uint32_t* mask_sh) {
+  uint32_t nw = (l + 63) / 64;
+  size_t plane = (size_t)n * l;
+  for (uint32_t r = 0; r < n; r++) {
+    const uint64_t* c = code_bits + (size_t)r * nw;
+    const uint64_t* m = mask_bits + (size_t)r * nw;
+    for (uint32_t b = 0; b < l; b++) {
+      int cb = get_bit(c, b), mb = get_bit(m, b);
+      uint32_t val[2] = {(uint32_t)(mb - 2 * (cb & mb)), (uint32_t)mb}; /* masked bit (Sec. 4.1.1) and mask */
+      for (uint32_t vec = 0; vec < 2; vec++) {
+        uint32_t w[4];
+        prf(client_seed, b >> 1, idx0 + r, (side << 8) | vec, ORC_D_SHARE32 << 24, w);
+        uint32_t x0 = w[2 * (b & 1u)], x1 = w[2 * (b & 1u) + 1];
+        uint32_t* dst = vec == 0 ? code_sh : mask_sh;
+        size_t at = (size_t)r * l + b;
+        dst[at] = x0;
+        dst[plane + at] = x1;
+        dst[2 * plane + at] = val[vec] - x0 - x1;
+      }
+    }
+  }
+}
+
+static uint32_t za32_value(uint64_t seed, uint32_t req, uint32_t q, uint32_t rho, uint32_t i, uint32_t vec) {
+  uint32_t w[4];
+  prf(seed, i >> 2, col_tag(q, rho), req, (ORC_D_ZA32 << 24) | vec, w);
+  return w[i & 3u];
+}
+
+/* App. C over Z_{2^32}: z_i = x_i y_i + x_{i-1} y_i + x_i y_{i-1} + r_i. */
+void orc_mpc_dot32(const orc_mpc_cfg* cfg, const uint32_t* x, uint64_t x_stride, const uint32_t* y,
+                   uint64_t y_stride, uint32_t l, uint32_t q, uint32_t rho, uint32_t i, uint32_t vec, uint32_t z[3],
+                   orc_stats* st) {
+  for (int p = 0; p < 3; p++) {
+    const uint32_t* xp = x + (size_t)p * x_stride;
+    const uint32_t* xm = x + (size_t)P(p - 1) * x_stride;
+    const uint32_t* yp = y + (size_t)p * y_stride;
+    const uint32_t* ym = y + (size_t)P(p - 1) * y_stride;
+    uint32_t acc = 0;
+    for (uint32_t k = 0; k < l; k++) acc += xp[k] * yp[k] + xm[k] * yp[k] + xp[k] * ym[k];
+    z[p] = acc + za32_value(cfg->seeds[p], cfg->req, q, rho, i, vec) -
+           za32_value(cfg->seeds[P(p - 1)], cfg->req, q, rho, i, vec);
+    if (st) st->bits_sent[p] += 32; /* resharing: z_p to party p+1 */
+  }
+}
+
+void orc_mpc_compare_liftfree(const orc_mpc_cfg* cfg, int mode, const uint32_t dot[3], const uint32_t ml[3],
+                              uint32_t thr_b, uint32_t q, uint32_t rho, uint32_t i, uint8_t msb[3],
+                              uint32_t v_out[3], orc_stats* st) {
+  /* ml is already a sharing over Z_{2^32}: no Lift */
+  rss_t L = rss_from_components(ml, 1);
+  rss_t D;
+  if (mode == ORC_LIFT_CONST) {
+    uint32_t d16[3] = {dot[0] & 0xFFFFu, dot[1] & 0xFFFFu, dot[2] & 0xFFFFu};
+    D = const_lift(rss_from_components(d16, 1), 1u << 16); /* [2^16 dot]_{2^32}, free */
+  } else {
+    uint32_t b = (thr_b == 0) ? (1u << 16) : thr_b;
+    D = rss_from_components(dot, 1);
+    for (int p = 0; p < 3; p++) { /* multiplication by a public constant is local */
+      D.v[p].own *= b;
+      D.v[p].prev *= b;
+    }
+  }
+  rss_t V;
+  for (int p = 0; p < 3; p++) {
+    V.v[p].own = cfg->thr_a * L.v[p].own - D.v[p].own;
+    V.v[p].prev = cfg->thr_a * L.v[p].prev - D.v[p].prev;
+  }
+  V.depth = 1;
+  gate_rng g = {cfg, i >> 5, col_tag(q, rho), ORC_D_AND, i & 31u};
+  rss_t top, below;
+  uint64_t and0 = st->and_gates;
+  bit_extract_rss(&V, 31, &g, ORC_MSB_GATE0, &top, &below, st);
+  for (int j = 0; j < 3; j++) {
+    msb[j] = (uint8_t)rss_component(&top, j);
+    if (v_out) v_out[j] = rss_component(&V, j);
+  }
+  st->and_lift = 0;
+  st->and_msb = (uint32_t)(st->and_gates - and0);
+  st->depth_lift = 0;
+  st->depth_msb = top.depth - V.depth;
+  st->depth_total = top.depth;
+}
+
+static void rotate_u32(const orc_geom* g, const uint32_t* in, uint32_t* out, int32_t shift) {
+  for (uint32_t r = 0; r < g->rows; r++)
+    for (uint32_t j = 0; j < g->cols; j++)
+      for (uint32_t k = 0; k < g->cell; k++)
+        out[(r * g->cols + j) * g->cell + k] = in[(r * g->cols + src_col(g, j, shift)) * g->cell + k];
+}
+
+void orc_mpc_match_lift(const orc_mpc_cfg* cfg, const orc_geom* g, int mode, uint32_t thr_b,
+                        const void* db_code, const uint32_t* db_mask, uint32_t s, const void* q_code,
+                        const uint32_t* q_mask, uint32_t Q, void* z_code, uint32_t* z_mask, uint8_t* bits,
+                        orc_stats* st) {
+  uint32_t l = g->rows * g->cols * g->cell, R = g->R;
+  uint64_t db_plane = (uint64_t)s * l, q_plane = (uint64_t)Q * l;
+  size_t zplane = (size_t)Q * R * s;
+  int wide = mode == ORC_LIFT_NONE; /* code shares over Z_{2^32} */
+  uint32_t* ry = (uint32_t*)malloc(sizeof(uint32_t) * 6 * l); /* rotated query: code 0..2, mask 0..2 */
+  uint16_t* ry16 = (uint16_t*)malloc(sizeof(uint16_t) * 3 * l);
+  uint8_t* msb = (uint8_t*)malloc(3 * (size_t)R * s + 1);
+  for (uint32_t q = 0; q < Q; q++) {
+    for (uint32_t rho = 0; rho < R; rho++) {
+      int32_t shift = g->rot_lo + (int32_t)rho;
+      for (int j = 0; j < 3; j++) {
+        if (wide)
+          rotate_u32(g, (const uint32_t*)q_code + j * q_plane + (size_t)q * l, ry + (size_t)j * l, shift);
+        else
+          orc_rotate_u16(g, (const uint16_t*)q_code + j * q_plane + (size_t)q * l, ry16 + (size_t)j * l, shift);
+        rotate_u32(g, q_mask + j * q_plane + (size_t)q * l, ry + (size_t)(3 + j) * l, shift);
+      }
+      size_t n = (size_t)q * R + rho;
+      for (uint32_t i = 0; i < s; i++) {
+        uint32_t zc[3], zm[3];
+        if (wide) {
+          orc_mpc_dot32(cfg, (const uint32_t*)db_code + (size_t)i * l, db_plane, ry, l, l, q, rho, i, 0, zc, st);
+        } else {
+          uint16_t z16[3];
+          orc_mpc_dot(cfg, (const uint16_t*)db_code + (size_t)i * l, db_plane, ry16, l, l, q, rho, i, 0, z16, st);
+          for (int p = 0; p < 3; p++) zc[p] = z16[p];
+        }
+        orc_mpc_dot32(cfg, db_mask + (size_t)i * l, db_plane, ry + (size_t)3 * l, l, l, q, rho, i, 1, zm, st);
+        for (int p = 0; p < 3; p++) {
+          size_t at = p * zplane + n * s + i;
+          if (z_code) {
+            if (wide)
+              ((uint32_t*)z_code)[at] = zc[p];
+            else
+              ((uint16_t*)z_code)[at] = (uint16_t)zc[p];
+          }
+          if (z_mask) z_mask[at] = zm[p];
+        }
+        uint8_t b[3];
+        orc_mpc_compare_liftfree(cfg, mode, zc, zm, thr_b, q, rho, i, b, NULL, st);
+        for (int p = 0; p < 3; p++) msb[(size_t)p * R * s + (size_t)rho * s + i] = b[p];
+      }
+    }
+    uint8_t bit[3];
+    orc_or_tree(cfg, msb, R, s, q, bit, st);
+    if (bits)
+      for (int p = 0; p < 3; p++) bits[(size_t)p * Q + q] = bit[p];
+  }
+  free(ry);
+  free(ry16);
+  free(msb);
+}

@@ -36,6 +36,8 @@ extern "C" {
 #define ORC_D_OR    6u /* boolean zero shares of the OR-tree AND gates                 */
 #define ORC_D_GSHARE 7u /* client randomness of the Galois-ring Shamir sharing        */
 #define ORC_D_COMB  8u /* boolean zero shares of the per-person OR combination      */
+#define ORC_D_SHARE32 9u /* client sharing randomness over Z_{2^32} (lifting variants) */
+#define ORC_D_ZA32 10u /* 32-bit arithmetic zero shares of Z_{2^32} dot products    */
 
 /* Gate numbering of the comparison circuit (D_AND counter). */
 #define ORC_LIFT_GATE0 0u  /* 33 gates of BitExtract(.,{17,16}) inside Lift      */
@@ -191,6 +193,39 @@ void orc_mpc_match_plain(const orc_mpc_cfg* cfg, const orc_geom* g, int galois,
                          const uint16_t* db_code, const uint64_t* db_mask_bits, uint32_t s,
                          const uint16_t* q_code, const uint64_t* q_mask_bits, uint32_t Q,
                          uint16_t* z_code, uint16_t* ml_out, uint8_t* bits, orc_stats* st);
+
+/* ---- Lifting variants (Sec. 5.1 and Sec. 6.2, Table 2) ----
+ * MPCLift (the default of Alg. 3 above): dot and ml over Z_{2^16}, ml lifted to Z_{2^32} in
+ * MPC. ConstLift: ml computed over Z_{2^32} from 32-bit mask shares, dot over Z_{2^16} and
+ * lifted for free by ConstLift with b = 2^16. NoLift: dot and ml both computed over Z_{2^32}
+ * (b any 16-bit constant). Either way v = a ml - b dot over Z_{2^32} and the match bit is
+ * MSB(v) = BitExtract(v, {31}) (61 ANDs, gates from ORC_MSB_GATE0) -- no Lift. */
+#define ORC_LIFT_CONST 1
+#define ORC_LIFT_NONE 2
+/* Client sharing over Z_{2^32} of the masked code bits and of the mask bits (values -1, 0, 1
+ * and 0, 1 read in Z_{2^32}): x_0, x_1 are words 2(b & 1), 2(b & 1) + 1 of
+ * Philox(client_seed, (b >> 1, idx0 + row, side<<8 | vec, D_SHARE32 << 24)), x_2 = v - x_0 - x_1.
+ * Output [3][n][l] u32. */
+void orc_encode_share32(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                        uint64_t client_seed, uint32_t side, uint32_t idx0, uint32_t* code_sh, uint32_t* mask_sh);
+/* orc_mpc_dot over Z_{2^32}; the zero share of (q, rho, i, vec) under one seed is word i & 3
+ * of Philox(seed, (i >> 2, (q<<5)|rho, req, D_ZA32 << 24 | vec)). */
+void orc_mpc_dot32(const orc_mpc_cfg* cfg, const uint32_t* x, uint64_t x_stride, const uint32_t* y,
+                   uint64_t y_stride, uint32_t l, uint32_t q, uint32_t rho, uint32_t i, uint32_t vec, uint32_t z[3],
+                   orc_stats* st);
+/* One comparison without Lift. ml: components over Z_{2^32}. dot: components over Z_{2^16}
+ * (mode ORC_LIFT_CONST; b must be 2^16) or over Z_{2^32} (ORC_LIFT_NONE, b = thr_b < 2^16, or
+ * 2^16 when thr_b is 0 or 2^16). Writes the MSB's boolean components, optionally v's. */
+void orc_mpc_compare_liftfree(const orc_mpc_cfg* cfg, int mode, const uint32_t dot[3], const uint32_t ml[3],
+                              uint32_t thr_b, uint32_t q, uint32_t rho, uint32_t i, uint8_t msb[3],
+                              uint32_t v_out[3], orc_stats* st);
+/* Alg. 3 with a lifting variant. db_code / q_code: [3][n][l] u16 shares (ORC_LIFT_CONST) or
+ * u32 shares (ORC_LIFT_NONE); db_mask / q_mask: [3][n][l] u32 shares. Outputs (may be NULL):
+ * z_code [3][Q*R][s] (u16 or u32 as the code shares), z_mask [3][Q*R][s] u32, bits [3][Q]. */
+void orc_mpc_match_lift(const orc_mpc_cfg* cfg, const orc_geom* g, int mode, uint32_t thr_b,
+                        const void* db_code, const uint32_t* db_mask, uint32_t s, const void* q_code,
+                        const uint32_t* q_mask, uint32_t Q, void* z_code, uint32_t* z_mask, uint8_t* bits,
+                        orc_stats* st);
 
 #ifdef __cplusplus
 }
