@@ -69,6 +69,13 @@ extern "C" {
 #define IPC_D_OR 6u
 #define IPC_D_GSHARE 7u /* client randomness of the Galois-ring Shamir sharing */
 #define IPC_D_COMB 8u   /* AND gates of the per-person OR of eyes and batch parts */
+#define IPC_D_SHARE32 9u /* client randomness of the Z_2^32 sharing (lifting variants) */
+#define IPC_D_ZA32 10u   /* zero shares of the Z_2^32 dot products (lifting variants) */
+
+/* Lifting variants (Sec. 5.1, Sec. 6.2 Table 2), ipc_config.lift. 0 (MPCLift, the default):
+ * code and mask dot products over Z_2^16, ml lifted to Z_2^32 in MPC. */
+#define IPC_LIFT_CONST 1 /* ConstLift: ml over Z_2^32 (32-bit mask shares), dot over Z_2^16 */
+#define IPC_LIFT_NONE 2  /* NoLift: code and mask dot products both over Z_2^32 */
 
 typedef struct {
   uint32_t rows, cols, cell; /* code geometry; l = rows*cols*cell, a multiple of 128 */
@@ -275,6 +282,61 @@ int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3]
                 uint32_t log2_block_words, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
                 void* stream);
 
+/* ---- Lifting variants (Sec. 5.1, Sec. 6.2): A0-A3 over Z_2^32 ---- */
+
+/*
+ * A0 over Z_2^32: the masked bits (T = -1, U = 0, F = +1) and mask bits read in Z_2^32, shared
+ * as x_0 + x_1 + x_2 with x_0, x_1 words 2(b & 1), 2(b & 1) + 1 of Philox(client_seed,
+ * (b >> 1, idx0 + r, side<<8 | vec, IPC_D_SHARE32<<24)). code_sh, mask_sh: [3][n][l] uint32,
+ * 8-byte aligned. Errors: IPC_EINVAL for odd l or null pointers.
+ */
+int ipc_encode_share32(const uint64_t* code_bits, const uint64_t* mask_bits, uint32_t n, uint32_t l,
+                       uint64_t client_seed, uint32_t side, uint32_t idx0, uint32_t* code_sh, uint32_t* mask_sh,
+                       void* stream);
+
+/*
+ * A1 over Z_2^32: x = l0 + 2^8 l1 + 2^16 l2 + 2^24 l3 (mod 2^32) with balanced limbs in
+ * [-128, 127], written as bf16 bit patterns (exact) to limbs[0..3] ([count] each, 8-byte
+ * aligned; x 16-byte aligned).
+ */
+int ipc_split_limbs32_bf16(const uint32_t* x, size_t count, uint16_t* const limbs[4], void* stream);
+
+/*
+ * A2 over Z_2^32: party's query operand, four bf16 limb planes b[0..3] of [n_pad][K]: with
+ * segments = 2, K = 2l and row n = q R + rho holds [rot(Y_p + Y_{p-1}) | rot(Y_p)] (the ABY3
+ * product, as ipc_prep_query); with segments = 1, K = l and rot(Y_p) alone. y: [3][Q][l] uint32
+ * components. Rows Q R .. n_pad - 1 are zero.
+ */
+int ipc_prep_query32_bf16(const uint32_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint32_t segments,
+                          uint16_t* const b[4], uint32_t n_pad, void* stream);
+
+/*
+ * A3 over Z_2^32 on tcgen05 (the ring product of ipc_ring_gemm_tc with four limbs: ten limb
+ * products, exact): z[n][r] = sum_k X[r][k] B[n][k] + F(seed_own) - F(seed_prev) (mod 2^32),
+ * X = [x[0..3] | x[4..7]] (segments = 2; limb planes [x_rows][l] of this party's and the
+ * previous party's components) or x[0..3] (segments = 1), B from ipc_prep_query32_bf16. The
+ * zero share of row g (global, row0 + r) and column n is word g & 3 of Philox(seed,
+ * (g >> 2, col_tags[2n+1], col_tags[2n], IPC_D_ZA32<<24 | vec)). z: [n_cols][ldz] uint32,
+ * 16-byte aligned, ldz % 4 == 0. Requires segments * l % 256 == 0, n_pad % 128 == 0,
+ * n_cols <= n_pad. Errors: IPC_EINVAL for bad sizes or unaligned pointers.
+ */
+int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows, const uint16_t* const b[4],
+                       uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                       uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, void* stream);
+
+/*
+ * A5-A7 without Lift (ConstLift and NoLift): ml32: [3] components over Z_2^32 of ml,
+ * [n_cols][ldz] uint32 each. The dot product's components are either over Z_2^16 (z16, then
+ * z32 = NULL; ConstLift: each component read as an integer and multiplied by 2^16) or over
+ * Z_2^32 (z32, then z16 = NULL; NoLift: multiplied by b = thr_b, 1 <= thr_b <= 2^16, 0 meaning
+ * 2^16). v = thr_a ml - b dot over Z_2^32 and MSB(v) = BitExtract(v, {31}) (61 ANDs; gates
+ * G = 36..96 as in ipc_compare). Block roots, msb_out, alignment and errors as in ipc_compare.
+ */
+int ipc_compare_liftfree(const uint16_t* const z16[3], const uint32_t* const z32[3], const uint32_t* const ml32[3],
+                         size_t ldz, uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
+                         const uint64_t seeds[3], uint32_t thr_a, uint32_t thr_b, uint32_t log2_block_words,
+                         uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb, void* stream);
+
 /*
  * A4-A7 of protocol 1 (Sec. 4, Alg. 2: the masks are public) -- the comparison
  * with a public mask length. ml: [n_cols][ldz] uint16, the plaintext ml of each
@@ -355,6 +417,14 @@ typedef struct {
                                mask bits as 0/1 uint16 in mask[0] (mask[1], mask[2] unused); ml is
                                a plaintext GEMM and a match is MSB(floor(thr_a ml / 2^16) - dot),
                                a 16-bit BitExtract. Not for serving or ipc_check_persons. */
+  uint32_t lift;            /* 0, IPC_LIFT_CONST or IPC_LIFT_NONE (IPC_PATH_TC with shared masks
+                               only; not for serving or ipc_check_persons). With a lifting
+                               variant the vectors shared over Z_2^32 (the mask; with NoLift the
+                               code too) are passed to load_db_shares and submit_queries as
+                               uint32 components (from ipc_encode_share32) through the same
+                               pointer arrays, cast; the others stay uint16. */
+  uint32_t thr_b;           /* b of the threshold a/b: 0 or 2^16, or with IPC_LIFT_NONE any value
+                               in 1..2^16 (0 meaning 2^16) */
 } ipc_config;
 
 /* Creates a context on cfg->device with per-party streams. Ownership of *out

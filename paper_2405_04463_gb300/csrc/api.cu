@@ -25,6 +25,11 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
                          const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
                          uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
                          uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows, bool plain);
+int compare_launch_liftfree(const uint16_t* const zc16[3], const uint32_t* const zc32[3],
+                            const uint32_t* const ml32[3], size_t ldz, uint32_t n_cols, size_t n_rows, uint64_t row0,
+                            const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a, uint32_t thr_b,
+                            uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
+                            cudaStream_t st);
 int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t p, uint32_t Q, uint32_t R,
                        const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares, cudaStream_t st);
 int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
@@ -216,6 +221,31 @@ extern "C" int ipc_compare_plain(const uint16_t* const z_code[3], const uint16_t
   const uint16_t* zm[3] = {ml, ml, ml};
   return compare_launch_tiles(z_code, zm, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, log2_block_words, roots,
                               ld_roots, msb_out, ld_msb, nullptr, nullptr, 0, as_stream(stream), nullptr, true);
+}
+
+extern "C" int ipc_compare_liftfree(const uint16_t* const z16[3], const uint32_t* const z32[3],
+                                    const uint32_t* const ml32[3], size_t ldz, uint32_t n_cols, size_t n_rows,
+                                    uint64_t row0, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
+                                    uint32_t thr_b, uint32_t log2_block_words, uint32_t* roots, size_t ld_roots,
+                                    uint8_t* msb_out, size_t ld_msb, void* stream) {
+  if (!ml32 || !col_tags || !seeds || !roots || (!z16) == (!z32))
+    return bad("ipc_compare_liftfree: null pointer, or not exactly one of z16 and z32");
+  for (int j = 0; j < 3; ++j) {
+    const void* d = z16 ? static_cast<const void*>(z16[j]) : static_cast<const void*>(z32[j]);
+    if (!ml32[j] || !d || !aligned(ml32[j], 16) || !aligned(d, 16))
+      return bad("ipc_compare_liftfree: planes must be non-null and 16-byte aligned");
+  }
+  if (log2_block_words > 5) return bad("ipc_compare_liftfree: log2_block_words must be <= 5");
+  if (ldz % 8 != 0 || ldz < n_rows) return bad("ipc_compare_liftfree: ldz must be a multiple of 8 and >= n_rows");
+  if (thr_b > 65536 || (z16 && thr_b != 0 && thr_b != 65536))
+    return bad("ipc_compare_liftfree: thr_b must be 2^16 with Z_2^16 dots, and at most 2^16");
+  if (row0 % (32ull << log2_block_words) != 0) return bad("ipc_compare_liftfree: row0 must be block aligned");
+  const uint64_t blocks = (n_rows + (32ull << log2_block_words) - 1) >> (5 + log2_block_words);
+  if (ld_roots < (row0 >> (5 + log2_block_words)) + blocks) return bad("ipc_compare_liftfree: ld_roots too small");
+  if (msb_out && ld_msb < n_rows) return bad("ipc_compare_liftfree: ld_msb too small");
+  if (n_rows == 0 || n_cols == 0) return IPC_OK;
+  return compare_launch_liftfree(z16, z32, ml32, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, thr_b,
+                                 log2_block_words, roots, ld_roots, msb_out, ld_msb, as_stream(stream));
 }
 
 extern "C" int ipc_or_finalize(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t log2_block_words,

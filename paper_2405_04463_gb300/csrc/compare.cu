@@ -128,7 +128,14 @@ struct CmpParams {
   const uint32_t* n_col_list;  // its length (device)
   uint32_t tile_cols;
   const uint32_t* col_rows;    // optional per column: global rows >= col_rows[n] are the public 0
+  // lift-free comparison (ConstLift / NoLift): ml components over Z_2^32, and the dot's either
+  // over Z_2^32 (zc32, NoLift, times thr_b) or over Z_2^16 (zc, ConstLift, times 2^16)
+  const uint32_t* zm32[3];
+  const uint32_t* zc32[3];
+  uint32_t thr_b;
 };
+
+constexpr int MODE_LIFT = 0, MODE_PLAIN = 1, MODE_LIFTFREE = 2;
 
 // Shared memory per thread (index [slot][threadIdx.x], conflict-free):
 //   raw ml / dot: 3 x 16 words each (two u16 per word), X (lift input words, later v words): 96,
@@ -143,11 +150,13 @@ __device__ __forceinline__ B3 bor(const Seeds& sd, const B3& a, const B3& b, uin
   return bx(bx(a, b), band(a, b, F0, F1, F2));
 }
 
-// PLAIN (protocol 1, Sec. 4, Alg. 2): zm[0] holds the public ml of each comparison (all three
+// MODE_LIFT (Alg. 3): Lift of ml, ConstLift of dot, v = a ml' - 2^16 dot', BitExtract(v, {31}).
+// MODE_PLAIN (protocol 1, Sec. 4, Alg. 2): zm[0] holds the public ml of each comparison (all three
 // pointers may point to it); v = floor(a ml / 2^16) - dot over Z_{2^16}, the public term entering
-// component 0, and the match bit is BitExtract(v, {15}) (29 ANDs, gates from 0). Otherwise the
-// shared-mask comparison: Lift of ml, ConstLift of dot, BitExtract(v, {31}).
-template <bool PLAIN>
+// component 0, and the match bit is BitExtract(v, {15}) (29 ANDs, gates from 0).
+// MODE_LIFTFREE (ConstLift / NoLift, Sec. 5.1, Sec. 6.2): ml already shared over Z_{2^32}, so
+// v = a ml - b dot over Z_{2^32} directly and BitExtract(v, {31}) (61 ANDs, the MSB gates).
+template <int MODE>
 __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
   extern __shared__ uint32_t sm[];  // [S_WORDS][CT]
   const uint32_t tid = threadIdx.x;
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
     const uint32_t lane_mask = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
     // ---- load the 32 rows of this word (3 components of ml and of dot) ----
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < (MODE == MODE_LIFTFREE ? 0 : 3); ++j) {
       const uint16_t* pm = P.zm[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
       const uint16_t* pd = P.zc[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
       if (nvalid == 32) {
@@ -206,7 +215,68 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
       }
     }
     B3 msb, b30;
-    if constexpr (PLAIN) {
+    if constexpr (MODE == MODE_LIFTFREE) {
+      // ---- v = a ml - b dot over Z_{2^32}, straight from the loads; bit-slice; MSB ----
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const uint32_t* pm = P.zm32[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+        if (nvalid == 32) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const uint4 a = reinterpret_cast<const uint4*>(pm)[v];
+            S(S_X + 32 * j + 4 * v + 0) = P.thr_a * a.x;
+            S(S_X + 32 * j + 4 * v + 1) = P.thr_a * a.y;
+            S(S_X + 32 * j + 4 * v + 2) = P.thr_a * a.z;
+            S(S_X + 32 * j + 4 * v + 3) = P.thr_a * a.w;
+          }
+        } else {
+          for (uint32_t l = 0; l < 32; ++l) S(S_X + 32 * j + l) = l < nvalid ? P.thr_a * pm[l] : 0u;
+        }
+        if (P.zc32[0]) {  // NoLift: dot components over Z_{2^32}, times b
+          const uint32_t* pd = P.zc32[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+          if (nvalid == 32) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const uint4 d = reinterpret_cast<const uint4*>(pd)[v];
+              S(S_X + 32 * j + 4 * v + 0) -= P.thr_b * d.x;
+              S(S_X + 32 * j + 4 * v + 1) -= P.thr_b * d.y;
+              S(S_X + 32 * j + 4 * v + 2) -= P.thr_b * d.z;
+              S(S_X + 32 * j + 4 * v + 3) -= P.thr_b * d.w;
+            }
+          } else {
+            for (uint32_t l = 0; l < nvalid; ++l) S(S_X + 32 * j + l) -= P.thr_b * pd[l];
+          }
+        } else {  // ConstLift: each Z_{2^16} component read as an integer, times 2^16
+          const uint16_t* pd = P.zc[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+          if (nvalid == 32) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const uint4 d = reinterpret_cast<const uint4*>(pd)[v];
+              const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                S(S_X + 32 * j + 8 * v + 2 * e) -= w[e] << 16;
+                S(S_X + 32 * j + 8 * v + 2 * e + 1) -= w[e] & 0xFFFF0000u;
+              }
+            }
+          } else {
+            for (uint32_t l = 0; l < nvalid; ++l) S(S_X + 32 * j + l) -= static_cast<uint32_t>(pd[l]) << 16;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uint32_t a[32];
+#pragma unroll
+        for (int v = 0; v < 32; ++v) a[v] = S(S_X + 32 * j + v);
+        transpose32(a);
+#pragma unroll
+        for (int v = 0; v < 32; ++v) S(S_X + 32 * j + v) = a[v];
+      }
+      GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
+      bit_extract<31, MSB_GATE0>(P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); }, msb,
+                                 b30);
+    } else if constexpr (MODE == MODE_PLAIN) {
       // ---- v = t - dot, t = floor(a ml / 2^16) public (component 0); bit-slice; MSB of 16 bits ----
       for (uint32_t l = 0; l < 32; ++l) {
         const uint32_t mlw = S(S_RAWML + (l >> 1));
@@ -431,19 +501,39 @@ __global__ void or_queries_kernel(const uint32_t* roots, uint64_t ld_roots, uint
   bit_shares[2 * Q + q] = x.c2 & 1u;
 }
 
-}  // namespace
+int launch_compare(CmpParams& P, int mode, cudaStream_t st) {
+  P.n_blocks = static_cast<uint32_t>((P.n_rows + (32ull << P.p) - 1) >> (5 + P.p));
+  const uint64_t threads = static_cast<uint64_t>(P.n_cols) * P.n_blocks;
+  const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(compare_kernel<MODE_LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(compare_kernel<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(compare_kernel<MODE_LIFTFREE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem));
+  });
+  IPC_CUDA_TRY(attr);
+  const unsigned grid = static_cast<unsigned>((threads + CT - 1) / CT);
+  if (mode == MODE_PLAIN)
+    compare_kernel<MODE_PLAIN><<<grid, CT, smem, st>>>(P);
+  else if (mode == MODE_LIFTFREE)
+    compare_kernel<MODE_LIFTFREE><<<grid, CT, smem, st>>>(P);
+  else
+    compare_kernel<MODE_LIFT><<<grid, CT, smem, st>>>(P);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
 
-int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
-                         uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
-                         const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
-                         uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
-                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows, bool plain) {
-  CmpParams P;
-  for (int j = 0; j < 3; ++j) {
-    P.zc[j] = z_code[j];
-    P.zm[j] = z_mask[j];
-    P.seeds.s[j] = seeds[j];
-  }
+CmpParams base_params(size_t ldz, uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
+                      const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
+                      uint8_t* msb_out, size_t ld_msb) {
+  CmpParams P{};
+  for (int j = 0; j < 3; ++j) P.seeds.s[j] = seeds[j];
   P.ldz = ldz;
   P.n_cols = n_cols;
   P.n_rows = n_rows;
@@ -451,34 +541,46 @@ int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const 
   P.col_tags = col_tags;
   P.thr_a = thr_a;
   P.p = p;
-  P.n_blocks = static_cast<uint32_t>((n_rows + (32ull << p) - 1) >> (5 + p));
   P.roots = roots;
   P.ld_roots = ld_roots;
   P.msb_out = msb_out;
   P.ld_msb = ld_msb;
+  return P;
+}
+
+}  // namespace
+
+int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
+                         uint32_t n_cols, size_t n_rows, uint64_t row0, const uint32_t* col_tags,
+                         const uint64_t seeds[3], uint32_t thr_a, uint32_t p, uint32_t* roots, size_t ld_roots,
+                         uint8_t* msb_out, size_t ld_msb, const uint32_t* col_tiles, const uint32_t* n_col_list,
+                         uint32_t tile_cols, cudaStream_t st, const uint32_t* col_rows, bool plain) {
+  CmpParams P = base_params(ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, p, roots, ld_roots, msb_out, ld_msb);
+  for (int j = 0; j < 3; ++j) {
+    P.zc[j] = z_code[j];
+    P.zm[j] = z_mask[j];
+  }
   P.col_tiles = col_tiles;
   P.n_col_list = n_col_list;
   P.tile_cols = tile_cols;
   P.col_rows = col_rows;
-  const uint64_t threads = static_cast<uint64_t>(n_cols) * P.n_blocks;
-  const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [smem] {
-    attr = cudaFuncSetAttribute(compare_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(compare_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem));
-  });
-  IPC_CUDA_TRY(attr);
-  const unsigned grid = static_cast<unsigned>((threads + CT - 1) / CT);
-  if (plain)
-    compare_kernel<true><<<grid, CT, smem, st>>>(P);
-  else
-    compare_kernel<false><<<grid, CT, smem, st>>>(P);
-  IPC_CUDA_TRY(cudaGetLastError());
-  return IPC_OK;
+  return launch_compare(P, plain ? MODE_PLAIN : MODE_LIFT, st);
+}
+
+// ConstLift (zc16 set, zc32 null) or NoLift (zc32 set): ml32 the Z_2^32 components of ml.
+int compare_launch_liftfree(const uint16_t* const zc16[3], const uint32_t* const zc32[3],
+                            const uint32_t* const ml32[3], size_t ldz, uint32_t n_cols, size_t n_rows, uint64_t row0,
+                            const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a, uint32_t thr_b,
+                            uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
+                            cudaStream_t st) {
+  CmpParams P = base_params(ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, p, roots, ld_roots, msb_out, ld_msb);
+  for (int j = 0; j < 3; ++j) {
+    P.zc[j] = zc16 ? zc16[j] : nullptr;
+    P.zc32[j] = zc32 ? zc32[j] : nullptr;
+    P.zm32[j] = ml32[j];
+  }
+  P.thr_b = zc32 ? (thr_b == 0 ? 65536u : thr_b) : 65536u;
+  return launch_compare(P, MODE_LIFTFREE, st);
 }
 
 int compare_launch(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz, uint32_t n_cols,

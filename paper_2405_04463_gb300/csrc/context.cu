@@ -38,7 +38,12 @@ int cfail(ipc_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 uint8_t* plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
-  return ch.planes + static_cast<size_t>((comp * 2 + vec) * 2 + limb) * ch.cap * c->l * c->esz;
+  return ch.planes + static_cast<size_t>((comp * 2 + vec) * c->nlimb + limb) * ch.cap * c->l * c->esz;
+}
+
+// Whether a vector (0 code, 1 mask) is shared over Z_2^32 (lifting variants) rather than Z_2^16.
+bool wide(const ipc_ctx* c, int vec) {
+  return vec == 1 ? c->cfg.lift != 0 : c->cfg.lift == IPC_LIFT_NONE;
 }
 
 uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
@@ -61,7 +66,7 @@ int ensure_zbuf(ipc_ctx* c, uint32_t n_pad) {
   CTX_TRY(c, cudaDeviceSynchronize());
   cudaFree(c->zbuf);
   c->zbuf = nullptr;
-  const size_t bytes = 2ull * 2 * 3 * n_pad * static_cast<size_t>(c->cfg.db_chunk_rows) * sizeof(uint16_t);
+  const size_t bytes = 2ull * 2 * 3 * n_pad * static_cast<size_t>(c->cfg.db_chunk_rows) * c->zsz;
   if (cudaMalloc(&c->zbuf, bytes) != cudaSuccess) {
     cudaGetLastError();
     c->zbuf_cols = 0;
@@ -71,8 +76,8 @@ int ensure_zbuf(ipc_ctx* c, uint32_t n_pad) {
   return IPC_OK;
 }
 
-uint16_t* zslot(ipc_ctx* c, int set, int vec, int party) {
-  return c->zbuf + ((static_cast<size_t>(set) * 2 + vec) * 3 + party) * c->zbuf_cols * c->cfg.db_chunk_rows;
+uint8_t* zslot(ipc_ctx* c, int set, int vec, int party) {
+  return c->zbuf + ((static_cast<size_t>(set) * 2 + vec) * 3 + party) * c->zbuf_cols * c->cfg.db_chunk_rows * c->zsz;
 }
 
 int wait_event(ipc_ctx* c, cudaEvent_t ev, int timeout_ms) {
@@ -135,6 +140,10 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   if (cfg->plain_mask && ((cfg->path != IPC_PATH_TC && cfg->path != IPC_PATH_TCG) || l % 256 != 0 || g.cell % 2 != 0))
     return fail(nullptr, IPC_EINVAL,
                 "ipc_create: plain masks (protocol 1) need the tc or tcg path, l % 256 == 0 and an even cell size");
+  if (cfg->lift > IPC_LIFT_NONE || (cfg->lift != 0 && (cfg->path != IPC_PATH_TC || cfg->plain_mask)))
+    return fail(nullptr, IPC_EINVAL, "ipc_create: the lifting variants need the tc path and shared masks");
+  if (cfg->thr_b > 65536 || (cfg->lift != IPC_LIFT_NONE && cfg->thr_b != 0 && cfg->thr_b != 65536))
+    return fail(nullptr, IPC_EINVAL, "ipc_create: thr_b is 2^16 unless lift is IPC_LIFT_NONE (then 1..2^16)");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
   ipc_ctx* c = new ipc_ctx();
   c->cfg = *cfg;
@@ -143,6 +152,8 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   c->l = static_cast<uint32_t>(l);
   c->esz = (cfg->path == IPC_PATH_TC || cfg->path == IPC_PATH_TCG) ? 2 : 1;
   c->kq = cfg->path == IPC_PATH_TCG ? c->l : 2 * c->l;
+  c->nlimb = cfg->lift ? 4 : 2;
+  c->zsz = cfg->lift ? 4 : 2;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete c;
@@ -210,7 +221,7 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
   CTX_TRY(c, cudaSetDevice(c->cfg.device));
   const size_t cap = c->cfg.db_chunk_rows, l = c->l;
   if (!c->stage) {
-    if (cudaMalloc(&c->stage, cap * l * sizeof(uint16_t)) != cudaSuccess) {
+    if (cudaMalloc(&c->stage, cap * l * (c->cfg.lift ? 4 : 2)) != cudaSuccess) {
       cudaGetLastError();
       return fail(c, IPC_ENOMEM, "load_db_shares: staging buffer");
     }
@@ -224,7 +235,7 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
     Chunk ch;
     ch.cap = cap;
     ch.row0 = next_row0;
-    if (cudaMalloc(&ch.planes, 12 * cap * l * c->esz) != cudaSuccess) {
+    if (cudaMalloc(&ch.planes, 6 * c->nlimb * cap * l * c->esz) != cudaSuccess) {
       cudaGetLastError();
       for (auto& f : fresh) cudaFree(f.planes);
       return fail(c, IPC_ENOMEM, "load_db_shares: device memory exhausted");
@@ -250,15 +261,21 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
     const size_t take = std::min(n_rows - done, ch->cap - ch->rows);
     for (int vec = 0; vec < 2; ++vec)
       for (int j = 0; j < (vec == 0 ? 3 : mask_parts); ++j) {
-        const uint16_t* src = (vec == 0 ? code[j] : mask[j]) + done * l;
-        CTX_TRY(c, cudaMemcpyAsync(c->stage, src, take * l * sizeof(uint16_t), kind, c->sc));
+        const size_t es = wide(c, vec) ? 4 : 2;  // bytes per input element
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(vec == 0 ? code[j] : mask[j]) + done * l * es;
+        CTX_TRY(c, cudaMemcpyAsync(c->stage, src, take * l * es, kind, c->sc));
         uint8_t* lo = plane(c, *ch, j, vec, 0) + ch->rows * l * c->esz;
         uint8_t* hi = plane(c, *ch, j, vec, 1) + ch->rows * l * c->esz;
-        if (c->esz == 2)
-          CTX_RC(c, ipc_split_limbs_bf16(c->stage, take * l, reinterpret_cast<uint16_t*>(lo),
+        if (es == 4) {
+          uint16_t* out[4];
+          for (int t = 0; t < 4; ++t)
+            out[t] = reinterpret_cast<uint16_t*>(plane(c, *ch, j, vec, t) + ch->rows * l * c->esz);
+          CTX_RC(c, ipc_split_limbs32_bf16(reinterpret_cast<const uint32_t*>(c->stage), take * l, out, c->sc));
+        } else if (c->esz == 2)
+          CTX_RC(c, ipc_split_limbs_bf16(reinterpret_cast<const uint16_t*>(c->stage), take * l, reinterpret_cast<uint16_t*>(lo),
                                          reinterpret_cast<uint16_t*>(hi), c->sc));
         else
-          CTX_RC(c, ipc_split_limbs(c->stage, take * l, reinterpret_cast<int8_t*>(lo), reinterpret_cast<int8_t*>(hi),
+          CTX_RC(c, ipc_split_limbs(reinterpret_cast<const uint16_t*>(c->stage), take * l, reinterpret_cast<int8_t*>(lo), reinterpret_cast<int8_t*>(hi),
                                     c->sc));
       }
     ch->rows += take;
@@ -297,8 +314,9 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   r.n_pad = n_pad;
   const size_t total_blocks = (c->chunks.size() * c->cfg.db_chunk_rows) >> (5 + kLog2BlockWords);
   r.ld_roots = total_blocks;
-  bool ok = cudaMalloc(&r.bq, 12ull * n_pad * c->kq * c->esz) == cudaSuccess &&
-            cudaMalloc(&r.qstage, 2ull * 3 * Q * l * sizeof(uint16_t)) == cudaSuccess &&
+  const size_t qes = c->cfg.lift ? 4 : 2;  // bytes per staged query element
+  bool ok = cudaMalloc(&r.bq, 6ull * c->nlimb * n_pad * c->kq * c->esz) == cudaSuccess &&
+            cudaMalloc(&r.qstage, 2ull * 3 * Q * l * qes) == cudaSuccess &&
             cudaMalloc(&r.tags, 2ull * N * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&r.roots, 3ull * N * r.ld_roots * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&r.shares_dev, 3ull * Q) == cudaSuccess &&
@@ -306,7 +324,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
             cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) == cudaSuccess;
   if (ok && c->cfg.keep_distances) {
     r.zkeep_rows = round_up(static_cast<uint32_t>(c->chunks.size() * c->cfg.db_chunk_rows), 8);
-    ok = cudaMalloc(&r.zkeep, 2ull * 3 * N * r.zkeep_rows * sizeof(uint16_t)) == cudaSuccess;
+    ok = cudaMalloc(&r.zkeep, 2ull * 3 * N * r.zkeep_rows * c->zsz) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -329,19 +347,27 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   }
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CTX_TRY(c, cudaMemcpyAsync(r.tags, tags.data(), tags.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
+  auto qvec = [&](int vec) { return r.qstage + static_cast<size_t>(vec) * 3 * Q * l * qes; };
   for (int vec = 0; vec < 2; ++vec)
-    for (int j = 0; j < (vec == 0 ? 3 : mask_parts); ++j)
-      CTX_TRY(c, cudaMemcpyAsync(r.qstage + (static_cast<size_t>(vec) * 3 + j) * Q * l, vec == 0 ? code[j] : mask[j],
-                                 static_cast<size_t>(Q) * l * sizeof(uint16_t), kind, c->sc));
+    for (int j = 0; j < (vec == 0 ? 3 : mask_parts); ++j) {
+      const size_t es = wide(c, vec) ? 4 : 2;
+      CTX_TRY(c, cudaMemcpyAsync(qvec(vec) + static_cast<size_t>(j) * Q * l * es, vec == 0 ? code[j] : mask[j],
+                                 static_cast<size_t>(Q) * l * es, kind, c->sc));
+    }
   CTX_TRY(c, cudaEventRecord(c->ev_setup, c->sc));
   // the host tags vector dies at return: make the copy complete before that
   const size_t qplane = static_cast<size_t>(n_pad) * c->kq * c->esz;
-  auto bq = [&](int party, int vec, int limb) { return r.bq + ((party * 2 + vec) * 2 + limb) * qplane; };
+  auto bq = [&](int party, int vec, int limb) { return r.bq + ((party * 2 + vec) * c->nlimb + limb) * qplane; };
   for (int i = 0; i < 3; ++i) {
     CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
     for (int vec = 0; vec < 2; ++vec) {
-      const uint16_t* y = r.qstage + static_cast<size_t>(vec) * 3 * Q * l;
-      if (plain && vec == 1) {
+      const uint16_t* y = reinterpret_cast<const uint16_t*>(qvec(vec));
+      if (wide(c, vec)) {
+        uint16_t* b4[4];
+        for (int t = 0; t < 4; ++t) b4[t] = reinterpret_cast<uint16_t*>(bq(i, vec, t));
+        CTX_RC(c, prep_query32(reinterpret_cast<const uint32_t*>(qvec(vec)), static_cast<uint64_t>(Q) * l, Q, &g, i, 2,
+                               b4, n_pad, c->sp[i]));
+      } else if (plain && vec == 1) {
         // protocol 1: the rotated public query mask, prepared once (party 0's stream runs the ml GEMM)
         if (i == 0)
           CTX_RC(c, prep_query_rotate_plain(y, Q, &g, reinterpret_cast<uint16_t*>(bq(0, 1, 0)),
@@ -362,13 +388,15 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
     const Chunk& ch = c->chunks[ci];
     if (ch.rows == 0) continue;
     const int set = static_cast<int>(ci & 1);
-    uint16_t* zc[3];
-    uint16_t* zm[3];
+    uint8_t* zc[3];  // 2-byte (Z_2^16) or 4-byte (Z_2^32) elements, ldz per column
+    uint8_t* zm[3];
     size_t ldz;
     for (int i = 0; i < 3; ++i) {
       if (c->cfg.keep_distances) {
-        zc[i] = r.zkeep + (static_cast<size_t>(0) * 3 + i) * N * r.zkeep_rows + ch.row0;
-        zm[i] = r.zkeep + (static_cast<size_t>(1) * 3 + i) * N * r.zkeep_rows + ch.row0;
+        // slot (vec, party) holds N columns of zkeep_rows elements; this chunk starts at row0
+        const size_t slot = static_cast<size_t>(N) * r.zkeep_rows * c->zsz;
+        zc[i] = r.zkeep + (0 * 3 + i) * slot + ch.row0 * (wide(c, 0) ? 4 : 2);
+        zm[i] = r.zkeep + (1 * 3 + i) * slot + ch.row0 * (wide(c, 1) ? 4 : 2);
         ldz = r.zkeep_rows;
       } else {
         zc[i] = zslot(c, set, 0, i);
@@ -380,8 +408,20 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       const int prev = (i + 2) % 3;
       CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
       for (int vec = 0; vec < 2; ++vec) {
-        uint16_t* zo = vec == 0 ? zc[i] : zm[i];
-        if (plain && vec == 1) {
+        uint16_t* zo = reinterpret_cast<uint16_t*>(vec == 0 ? zc[i] : zm[i]);
+        if (wide(c, vec)) {
+          // lifting variants: the ring product over Z_2^32, four limbs, K = 2l
+          const uint16_t* x8[8];
+          const uint16_t* b4[4];
+          for (int t = 0; t < 4; ++t) {
+            x8[t] = reinterpret_cast<const uint16_t*>(plane(c, ch, i, vec, t));
+            x8[4 + t] = reinterpret_cast<const uint16_t*>(plane(c, ch, prev, vec, t));
+            b4[t] = reinterpret_cast<const uint16_t*>(bq(i, vec, t));
+          }
+          CTX_RC(c, ring_gemm_tc32(2, x8, ch.rows, b4, N, n_pad, l, r.tags, c->cfg.seeds[i], c->cfg.seeds[prev],
+                                   static_cast<uint32_t>(vec), reinterpret_cast<uint32_t*>(zo), ldz, ch.row0,
+                                   c->sp[i]));
+        } else if (plain && vec == 1) {
           // protocol 1: ml = <rotated query mask, database mask> in the clear, K = l; equal seeds
           // make the zero share vanish
           if (i != 0) continue;
@@ -418,11 +458,23 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       CTX_TRY(c, cudaEventRecord(c->ev_gemm[i][set], c->sp[i]));
       CTX_TRY(c, cudaStreamWaitEvent(c->sc, c->ev_gemm[i][set], 0));
     }
-    const uint16_t* zcc[3] = {zc[0], zc[1], zc[2]};
-    const uint16_t* zmc[3] = {zm[0], plain ? zm[0] : zm[1], plain ? zm[0] : zm[2]};
-    CTX_RC(c, compare_launch_tiles(zcc, zmc, ldz, N, ch.rows, ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a,
-                                   kLog2BlockWords, r.roots, r.ld_roots, nullptr, 0, nullptr, nullptr, 0, c->sc,
-                                   nullptr, plain));
+    auto u16p = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
+    auto u32p = [](const uint8_t* p) { return reinterpret_cast<const uint32_t*>(p); };
+    if (c->cfg.lift) {
+      const uint32_t* ml32[3] = {u32p(zm[0]), u32p(zm[1]), u32p(zm[2])};
+      const uint32_t* zc32[3] = {u32p(zc[0]), u32p(zc[1]), u32p(zc[2])};
+      const uint16_t* zc16[3] = {u16p(zc[0]), u16p(zc[1]), u16p(zc[2])};
+      const bool nolift = c->cfg.lift == IPC_LIFT_NONE;
+      CTX_RC(c, compare_launch_liftfree(nolift ? nullptr : zc16, nolift ? zc32 : nullptr, ml32, ldz, N, ch.rows,
+                                        ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a, c->cfg.thr_b, kLog2BlockWords,
+                                        r.roots, r.ld_roots, nullptr, 0, c->sc));
+    } else {
+      const uint16_t* zcc[3] = {u16p(zc[0]), u16p(zc[1]), u16p(zc[2])};
+      const uint16_t* zmc[3] = {u16p(zm[0]), u16p(plain ? zm[0] : zm[1]), u16p(plain ? zm[0] : zm[2])};
+      CTX_RC(c, compare_launch_tiles(zcc, zmc, ldz, N, ch.rows, ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a,
+                                     kLog2BlockWords, r.roots, r.ld_roots, nullptr, 0, nullptr, nullptr, 0, c->sc,
+                                     nullptr, plain));
+    }
     CTX_TRY(c, cudaEventRecord(c->ev_cmp[set], c->sc));
   }
   const uint32_t n_blocks =
@@ -476,15 +528,29 @@ extern "C" int fetch_distances(ipc_ctx* c, uint64_t req_id, uint32_t q, uint32_t
   int rc = wait_event(c, r.done, -1);
   if (rc) return rc;
   const size_t n = static_cast<size_t>(q) * c->cfg.geom.R + rho, cnt = row_end - row_begin;
-  std::vector<uint16_t> tmp(cnt);
+  std::vector<uint8_t> tmp(cnt * 4);
   std::vector<uint32_t> acc[2] = {std::vector<uint32_t>(cnt, 0), std::vector<uint32_t>(cnt, 0)};
   const bool plain = c->cfg.plain_mask != 0;
-  for (int vec = 0; vec < 2; ++vec)
+  const size_t slot = static_cast<size_t>(r.N) * r.zkeep_rows * c->zsz;
+  for (int vec = 0; vec < 2; ++vec) {
+    const size_t es = wide(c, vec) ? 4 : 2;
     for (int i = 0; i < (plain && vec == 1 ? 1 : 3); ++i) {  // protocol 1 keeps ml itself in component 0
-      const uint16_t* src = r.zkeep + ((static_cast<size_t>(vec) * 3 + i) * r.N + n) * r.zkeep_rows + row_begin;
-      CTX_TRY(c, cudaMemcpy(tmp.data(), src, cnt * sizeof(uint16_t), cudaMemcpyDeviceToHost));
-      for (size_t k = 0; k < cnt; ++k) acc[vec][k] += tmp[k];
+      const uint8_t* src = r.zkeep + (static_cast<size_t>(vec) * 3 + i) * slot + (n * r.zkeep_rows + row_begin) * es;
+      CTX_TRY(c, cudaMemcpy(tmp.data(), src, cnt * es, cudaMemcpyDeviceToHost));
+      // the components sum to the value mod 2^16 or mod 2^32; its low 16 bits are returned
+      for (size_t k = 0; k < cnt; ++k) {
+        uint32_t v = 0;
+        if (es == 4) {
+          std::memcpy(&v, tmp.data() + 4 * k, 4);
+        } else {
+          uint16_t h;
+          std::memcpy(&h, tmp.data() + 2 * k, 2);
+          v = h;
+        }
+        acc[vec][k] += v;
+      }
     }
+  }
   for (size_t k = 0; k < cnt; ++k) {
     dot[k] = static_cast<int16_t>(static_cast<uint16_t>(acc[0][k] & 0xFFFFu));
     ml[k] = static_cast<uint16_t>(acc[1][k] & 0xFFFFu);

@@ -30,16 +30,12 @@
 // Tile widths TN = 256 (the fixed-shape launch) and 128; see gemm_tc_kernel for the list mode.
 // Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
 // status word, lets its copies and MMAs finish, frees its tensor memory and stores nothing.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include <mutex>
-#include <string>
-
-#include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace ipc {
 namespace {
+
+using namespace tc;
 
 constexpr int TM = 128;          // database rows per tile (MMA M = TMEM lanes)
 constexpr int KB = 32;           // bf16 elements of K per stage: one 64-byte swizzled row
@@ -88,133 +84,6 @@ struct TcParams {
   uint64_t row0;
   uint32_t* status;
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase of the given parity. Gives up after 2 s (raising the status word and the
-// CTA's abort flag) or, when `abort` is given, as soon as another role has raised that flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status, volatile uint32_t* abort) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (;;) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try(bar, parity)) return true;
-    if (abort && *abort) return false;
-    if (global_ns() - t0 > 2000000000ull) {
-      raise_status(status, ST_WAIT_TIMEOUT);
-      if (abort) *abort = 1u;
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row core-matrix groups 512 bytes
-// apart (SBO), LBO unused for this layout (1), descriptor version 1 (bits 46-47), layout type
-// SWIZZLE_64B (4 at bits 61-63). Stage tiles are 1024-byte aligned, so the base offset is 0.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (static_cast<uint64_t>(512 >> 4) << 32) |
-         (1ull << 46) | (4ull << 61);
-}
-
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(1u)
-      : "memory");
-}
-
-// Arrives on the mbarrier once every MMA issued so far by this thread has completed.
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-}
-
-// Stores v into 32 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
-      "r"(v)
-      : "memory");
-}
-
-// Two 16-bit lanes added independently (mod 2^16 each).
-__device__ __forceinline__ uint32_t add16x2(uint32_t a, uint32_t b) {
-  uint32_t d;
-  asm("add.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-  return d;
-}
-
-// Low 16 bits of x (lane 0) and of y (lane 1): the L contributions of two columns.
-__device__ __forceinline__ uint32_t pack_lo16(uint32_t x, uint32_t y) {
-  uint32_t d;
-  asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(d) : "r"(x), "r"(y));
-  return d;
-}
-
-// (x << 8) mod 2^16 and (y << 8) mod 2^16 in lanes 0 and 1: the 256 C contributions of two
-// columns. Byte 0 of each goes to bit 8 of its lane; the zero bytes are the replicated sign of
-// byte 3 of x, which is 0x4B for every accumulator value in [2^23, 2^24).
-__device__ __forceinline__ uint32_t pack_c16(uint32_t x, uint32_t y) {
-  uint32_t d;
-  asm("prmt.b32 %0, %1, %2, 0x4B0B;" : "=r"(d) : "r"(x), "r"(y));
-  return d;
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 
 // Without a list (LIST false) the grid is (column tiles, row tiles), one tile per CTA. With a list,
 // gridDim.x persistent CTAs walk items w = blockIdx.x + i * gridDim.x: column tile
@@ -491,41 +360,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
   }
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  });
-  return fn;
-}
-
-// 2-D bf16 tensor [rows][cols], box 32 elements (64 bytes) x box_rows, 64-byte swizzle, zero fill
-// outside the tensor (ragged row tails and query rows past n_pad).
-int make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
-  auto fn = encode_fn();
-  if (!fn) {
-    set_error("cuTensorMapEncodeTiled is not available from the driver");
-    return IPC_ECUDA;
-  }
-  cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * 2};
-  cuuint32_t box[2] = {KB, box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled (bf16) failed with CUresult " + std::to_string(static_cast<int>(r)));
-    return IPC_ECUDA;
-  }
-  return IPC_OK;
 }
 
 int sm_count_tc() {

@@ -189,6 +189,7 @@ extern "C" int ipc_check_persons(ipc_ctx* const ctx[2], const uint16_t* const co
   if (ctx[0]->srv || ctx[1]->srv) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: a context is serving");
   if (ctx[0] == ctx[1]) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: one context per eye");
   if (a.plain_mask || b.plain_mask) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: protocol 1 is not supported");
+  if (a.lift || b.lift) return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: the lifting variants are not supported");
   if (P == 0 || P > a.max_queries || P > b.max_queries)
     return ctx_fail(c, IPC_EINVAL, "ipc_check_persons: P must be in 1..max_queries");
   for (int k = 0; k < 6; ++k)

@@ -590,6 +590,7 @@ extern "C" int ipc_serve_start(ipc_ctx* c, const ipc_serve_config* cfg) {
   if (c->rows == 0) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: no database rows loaded");
   if (c->cfg.path == IPC_PATH_I32) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: the int32 path has no tile variants");
   if (c->cfg.plain_mask) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: protocol 1 (plain masks) is not served");
+  if (c->cfg.lift) return ctx_fail(c, IPC_EINVAL, "ipc_serve_start: the lifting variants are not served");
   cudaError_t e = cudaSetDevice(c->cfg.device);
   if (e != cudaSuccess) return ctx_cfail(c, e, "cudaSetDevice");
   e = cudaDeviceSynchronize();

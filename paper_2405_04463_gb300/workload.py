@@ -45,6 +45,29 @@ def encode_gpu(code_bits, mask_bits, l, seed, side, idx0=0, galois_shares=False)
     return code, mask
 
 
+def encode_gpu32(code_bits, mask_bits, l, seed, side, idx0=0):
+    """A0 over Z_2^32 through the C ABI: torch int32 [3][n][l] code and mask shares."""
+    torch = torch_mod()
+    ipc = lib()
+    cb = code_bits if hasattr(code_bits, "data_ptr") else dev_u64(code_bits)
+    mb = mask_bits if hasattr(mask_bits, "data_ptr") else dev_u64(mask_bits)
+    n = cb.shape[0]
+    code = torch.empty((3, n, l), dtype=torch.int32, device="cuda")
+    mask = torch.empty((3, n, l), dtype=torch.int32, device="cuda")
+    ipc.ipc_encode_share32(cb, mb, n, l, seed, side, idx0, code, mask)
+    return code, mask
+
+
+def lift_shares(code_bits, mask_bits, l, seed, side, idx0=0, lift="const"):
+    """Shares of a lifting variant: ConstLift takes Z_2^16 code shares and Z_2^32 mask shares,
+    NoLift Z_2^32 shares of both."""
+    c32, m32 = encode_gpu32(code_bits, mask_bits, l, seed, side, idx0)
+    if lift in ("none", 2):
+        return c32, m32
+    c16, _ = encode_gpu(code_bits, mask_bits, l, seed, side, idx0)
+    return c16, m32
+
+
 def u16(t) -> np.ndarray:
     """torch int16 tensor -> numpy uint16."""
     return t.cpu().numpy().view(np.uint16)
@@ -78,7 +101,7 @@ def plain_mask_u16(mask_bits, l: int):
     return bits.reshape(mb.shape[0], -1)[:, :l].to(torch.int16).contiguous()
 
 
-def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=False, plain_mask=False):
+def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=False, plain_mask=False, lift=None):
     """Generate the workload's database on the device, share it (A0) and load it (A1). With
     plain_mask the masks stay public (protocol 1): mask[0] carries the 0/1 mask elements."""
     torch = torch_mod()
@@ -86,7 +109,10 @@ def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=Fals
     for r0 in range(0, w.s, chunk):
         n = min(chunk, w.s - r0)
         cb, mb = db_bits_device(w, r0, n)
-        code, mask = encode_gpu(cb, mb, w.l, w.db_share_seed, 0, idx0=r0, galois_shares=galois_shares)
+        if lift not in (None, "mpc", 0):
+            code, mask = lift_shares(cb, mb, w.l, w.db_share_seed, 0, idx0=r0, lift=lift)
+        else:
+            code, mask = encode_gpu(cb, mb, w.l, w.db_share_seed, 0, idx0=r0, galois_shares=galois_shares)
         masks = [plain_mask_u16(mb, w.l), None, None] if plain_mask else [mask[j] for j in range(3)]
         ipc.load_db_shares(ctx, [code[j] for j in range(3)], masks, n, 1)
         del code, mask, masks
@@ -99,11 +125,12 @@ def query_shares_gpu(w: synth.Workload, qc=None, qm=None, galois_shares=False):
     return encode_gpu(qc, qm, w.l, w.q_share_seed, 1, galois_shares=galois_shares)
 
 
-def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0, plain_mask=False):
+def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0, plain_mask=False,
+             lift="mpc", thr_b=0):
     ipc = lib()
     g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
     cfg = ipc.make_config(g, thr_a=w.thr_a, path=path, db_chunk_rows=chunk_rows, max_queries=max_queries or w.Q,
-                          seeds=w.prf_seeds, keep_distances=keep, plain_mask=plain_mask)
+                          seeds=w.prf_seeds, keep_distances=keep, plain_mask=plain_mask, lift=lift, thr_b=thr_b)
     ctx = ipc.ipc_create(cfg)
     ipc.ipc_set_input_stream(ctx)   # device inputs come from torch's current stream
     return ctx
