@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
-    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc) or compare")
+    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc32) or compare")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--serving", action="store_true",
@@ -69,7 +69,9 @@ def parse():
 
 def run_compare_kernel(args, w):
     """The comparison phase (A4-A8 with the in-block OR) of one chunk alone: all query columns
-    x --rows rows of random dot-product shares, timed with CUDA events."""
+    x --rows rows of random dot-product shares, timed with CUDA events. Besides the headline
+    MPCLift comparison, the same shape in the other settings of Table 2 (Sec. 6.2): plain masks
+    (16-bit MSB), ConstLift and NoLift (32-bit MSB without Lift)."""
     import torch
 
     import paper_2405_04463_gb300 as ipc
@@ -77,27 +79,39 @@ def run_compare_kernel(args, w):
     g = torch.Generator(device="cpu").manual_seed(7)
     zc = [torch.randint(-32768, 32768, (N, rows), dtype=torch.int16, generator=g).cuda() for _ in range(3)]
     zm = [torch.randint(0, 12801, (N, rows), dtype=torch.int16, generator=g).cuda() for _ in range(3)]
+    zc32 = [torch.randint(-2**31, 2**31 - 1, (N, rows), dtype=torch.int32, generator=g).cuda() for _ in range(3)]
+    zm32 = [torch.randint(-2**31, 2**31 - 1, (N, rows), dtype=torch.int32, generator=g).cuda() for _ in range(3)]
     tags = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
     nb = (rows + 1023) // 1024
     roots = torch.zeros((3, N, nb), dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream()
-
-    def launch():
-        ipc.ipc_compare(zc, zm, rows, N, rows, 0, tags, w.prf_seeds, w.thr_a, 5, roots, nb)
-
-    launch()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.reps):
+    modes = {
+        "mpclift": (lambda: ipc.ipc_compare(zc, zm, rows, N, rows, 0, tags, w.prf_seeds, w.thr_a, 5, roots, nb),
+                    12.0, 33 + 61),
+        "plain_mask": (lambda: ipc.ipc_compare_plain(zc, zm[0], rows, N, rows, 0, tags, w.prf_seeds, w.thr_a, 5,
+                                                     roots, nb), 8.0, 29),
+        "constlift": (lambda: ipc.ipc_compare_liftfree(zc, None, zm32, rows, N, rows, 0, tags, w.prf_seeds,
+                                                       w.thr_a, 0, 5, roots, nb), 18.0, 61),
+        "nolift": (lambda: ipc.ipc_compare_liftfree(None, zc32, zm32, rows, N, rows, 0, tags, w.prf_seeds,
+                                                    w.thr_a, 0, 5, roots, nb), 24.0, 61),
+    }
+    out = {"kernel": "compare", "rows": rows, "cols": N}
+    for name, (launch, bpc, ands) in modes.items():
         launch()
-    e1.record(st)
-    e1.synchronize()
-    ipc.ipc_status()
-    ms = e0.elapsed_time(e1) / args.reps
-    bytes_read = 12.0 * N * rows   # 3 parties x (dot, ml) x 2 B per comparison
-    print(json.dumps({"kernel": "compare", "rows": rows, "cols": N, "ms_per_launch": ms,
-                      "comparisons_per_s": N * rows / (ms * 1e-3), "algorithmic_bytes_per_launch": bytes_read,
-                      "achieved_gbs": bytes_read / (ms * 1e-3) / 1e9}))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.reps):
+            launch()
+        e1.record(st)
+        e1.synchronize()
+        ipc.ipc_status()
+        ms = e0.elapsed_time(e1) / args.reps
+        # bpc: bytes of dot-product components read per comparison (3 parties; ml public for plain)
+        out[name] = {"ms_per_launch": ms, "comparisons_per_s": N * rows / (ms * 1e-3), "and_gates": ands,
+                     "algorithmic_bytes_per_launch": bpc * N * rows,
+                     "achieved_gbs": bpc * N * rows / (ms * 1e-3) / 1e9}
+    out.update(out["mpclift"])
+    print(json.dumps(out))
 
 
 def run_kernel(args, w):
@@ -118,7 +132,19 @@ def run_kernel(args, w):
     z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.kernel == "tc":
+    products = 3.0
+    if args.kernel == "tc32":
+        # the Z_2^32 ring product: four limbs per operand, ten limb products, z as uint32
+        bf = lambda t: t.float().to(torch.bfloat16).view(torch.int16).contiguous()
+        x8 = [bf(torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda")) for _ in range(8)]
+        b4 = [bf(torch.randint(-128, 128, (n_pad, 2 * l), dtype=torch.int8, device="cuda")) for _ in range(4)]
+        del planes, blo, bhi
+        z = torch.empty((N, rows), dtype=torch.int32, device="cuda")
+        products = 10.0
+
+        def launch():
+            ipc.ipc_ring_gemm_tc32(2, x8, rows, b4, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+    elif args.kernel == "tc":
         # the same limbs as bf16 bit patterns (operand conversion outside the timed launches)
         planes = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in planes]
         blo, bhi = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in (blo, bhi)]
@@ -137,11 +163,13 @@ def run_kernel(args, w):
     e1.synchronize()
     ipc.ipc_status()
     ms = e0.elapsed_time(e1) / args.reps
-    macs = 3.0 * N * rows * 2 * l if args.kernel != "i32" else 1.0 * N * rows * 2 * l
+    macs = products * N * rows * 2 * l if args.kernel != "i32" else 1.0 * N * rows * 2 * l
+    limbs = 4 if args.kernel == "tc32" else 2
     print(json.dumps({"kernel": args.kernel, "rows": rows, "cols": N, "ms_per_launch": ms,
                       "algorithmic_ops_per_launch": 2 * macs, "achieved_tops": 2 * macs / (ms * 1e-3) / 1e12,
-                      "operand_bytes_per_launch": (2 if args.kernel == "tc" else 1) * (4 * rows * l + 2 * n_pad * 2 * l),
-                      "z_bytes": 2 * N * rows}))
+                      "operand_bytes_per_launch": (2 if args.kernel in ("tc", "tc32") else 1) *
+                      (2 * limbs * rows * l + limbs * n_pad * 2 * l),
+                      "z_bytes": (4 if args.kernel == "tc32" else 2) * N * rows}))
 
 
 def dist_env():
@@ -257,15 +285,23 @@ def ncu_traffic(kernel: str, src: str):
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return float(m.group(1)) if cur == h.group(1) else None
+    return float(m.group(1)) if source_hash(src) == h.group(1) else None
+
+
+def source_hash(src: str) -> str:
+    """SHA-256 of a kernel's .cu file followed by the headers its device code includes."""
+    hs = hashlib.sha256(open(src, "rb").read())
+    for hdr in ("tcgen05.cuh", "common.cuh"):
+        hs.update(open(os.path.join(ROOT, "paper_2405_04463_gb300", "csrc", hdr), "rb").read())
+    return hs.hexdigest()
 
 
 def run_ours(args, w):
     import torch
 
     import paper_2405_04463_gb300 as ipc
-    from paper_2405_04463_gb300.workload import galois, load_workload, make_ctx, plain_mask_u16, query_shares_gpu
+    from paper_2405_04463_gb300.workload import (galois, lift_shares, load_workload, make_ctx, plain_mask_u16,
+                                                 query_shares_gpu)
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -283,13 +319,14 @@ def run_ours(args, w):
     qcode, qmask = query_shares_gpu(w)
     gqcode, gqmask = query_shares_gpu(w, galois_shares=True)
     pqmask = plain_mask_u16(w.query_bits()[1], w.l)
+    lift_q = {lf: lift_shares(*w.query_bits(), w.l, w.q_share_seed, 1, lift=lf) for lf in ("const", "none")}
     hcode = [qcode[j].cpu().pin_memory() for j in range(3)]
     hmask = [qmask[j].cpu().pin_memory() for j in range(3)]
     torch.cuda.synchronize()
     n_chunks = (w.s + 65535) // 65536
     launches_per_step = 6 + n_chunks * 7 + 2
 
-    def run_steps(ctx, k, host_inputs, gal=False, plain=False):
+    def run_steps(ctx, k, host_inputs, gal=False, plain=False, lift=None):
         stream = torch.cuda.ExternalStream(ipc.ipc_ctx_stream(ctx))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         qc_, qm_ = (gqcode, gqmask) if gal else (qcode, qmask)
@@ -297,6 +334,8 @@ def run_ours(args, w):
         mask = hmask if host_inputs else [qm_[j] for j in range(3)]
         if plain:
             mask = [pqmask, None, None]
+        if lift:
+            code, mask = [lift_q[lift][0][j] for j in range(3)], [lift_q[lift][1][j] for j in range(3)]
         bits = np.zeros(w.Q, np.uint8)
         torch.cuda.synchronize()
         if world > 1:
@@ -326,13 +365,13 @@ def run_ours(args, w):
     run_steps(main, 1, True)
     ms_e2e, wall_e2e, bits_e2e = run_steps(main, args.steps, True)
 
-    def other(path, plain=False):
+    def other(path, plain=False, lift=None):
         gal = galois(path)
-        ctx = make_ctx(w, path=path, max_queries=w.Q, plain_mask=plain)
+        ctx = make_ctx(w, path=path, max_queries=w.Q, plain_mask=plain, lift=lift or "mpc")
         try:
-            load_workload(ctx, w, chunk=32768, galois_shares=gal, plain_mask=plain)
-            run_steps(ctx, 1, False, gal, plain)
-            ms, _, b = run_steps(ctx, args.steps, False, gal, plain)
+            load_workload(ctx, w, chunk=32768, galois_shares=gal, plain_mask=plain, lift=lift)
+            run_steps(ctx, 1, False, gal, plain, lift)
+            ms, _, b = run_steps(ctx, args.steps, False, gal, plain, lift)
         finally:
             ipc.ipc_destroy(ctx)
         return {"value": w.comparisons * world / (ms * 1e-3), "ms_per_step": ms,
@@ -341,6 +380,9 @@ def run_ours(args, w):
     out_gal = other("tcg")
     out_plain = other("tc", plain=True)
     out_plain_gal = other("tcg", plain=True)
+    out_const = other("tc", lift="const")
+    out_nolift = other("tc", lift="none")
+    del lift_q
     out_mix = other("i8mix")
     out_mma = other("i8mma")
     out_i32 = other("i32") if not args.no_i32 else None
@@ -357,8 +399,14 @@ def run_ours(args, w):
     z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
     st = torch.cuda.current_stream()
 
+    x8 = [t.view(torch.int16) for t in bf[0:4]] + [t.view(torch.int16) for t in bf[0:4]]
+    b4 = [bf[4], bf[5], bf[4], bf[5]]
+    z32 = torch.empty((N, rows), dtype=torch.int32, device="cuda")
+
     def launch(path):
-        if path == "tc":
+        if path == "tc32":
+            ipc.ipc_ring_gemm_tc32(2, x8, rows, b4, N, n_pad, l, tags, 1, 2, 0, z32, rows, 0)
+        elif path == "tc":
             ipc.ipc_ring_gemm_tc(bf[0:2], bf[2:4], rows, bf[4], bf[5], N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
         else:
             ipc.ipc_ring_gemm(path, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
@@ -375,6 +423,7 @@ def run_ours(args, w):
         return e0.elapsed_time(e1) / reps
 
     t_tc = gemm_time("tc", 10)
+    t_tc32 = gemm_time("tc32", 4)
     t_mix = gemm_time("i8mix", 3)
     t_i8 = gemm_time("i8mma", 3)
     t_i32 = gemm_time("i32", 2) if not args.no_i32 else None
@@ -401,6 +450,13 @@ def run_ours(args, w):
                         "frac_of_measured_mma": ops / (t_i8 * 1e-3) / 1e12 / peak_mma},
                     "measured_int8_peaks_tops": {"mma_sync_s8": peak_mma, "dp4a": peak_dp4a,
                                                  "source": "register-only loops (ipc_measure_peak)"}}}
+    ops32 = 2.0 * 10 * N * rows * 2 * l   # ten limb products per Z_2^32 ring multiply-add
+    tc32_kernel = {"kernel": "gemm_tc32_kernel (tcgen05.mma kind::f16, four limbs, Z_2^32)", "bound": "tensor",
+                   "achieved": ops32 / (t_tc32 * 1e-3) / 1e12, "peak": bf16_burst, "unit": "TFLOP/s",
+                   "frac": ops32 / (t_tc32 * 1e-3) / 1e12 / bf16_burst if bf16_burst else None,
+                   "launch_ms": t_tc32, "flops_per_launch": ops32,
+                   "traffic": ncu_traffic("gemm_tc32_kernel", os.path.join(ROOT, "paper_2405_04463_gb300", "csrc",
+                                                                           "ring32.cu"))}
     i32_kernel = None
     if t_i32:
         imads = 1.0 * N * rows * 2 * l
@@ -442,6 +498,11 @@ def run_ours(args, w):
         "plain_mask_path": dict(out_plain, galois_shamir=out_plain_gal,
                                 note="protocol 1 (Sec. 4, Alg. 2): public masks, ml one plaintext GEMM "
                                      "(K = l) instead of three shared ones, 16-bit comparison (29 ANDs)"),
+        "lift_variants": {
+            "constlift": out_const, "nolift": out_nolift,
+            "note": "Sec. 5.1 / Table 2: ml (ConstLift) or ml and dot (NoLift) computed over Z_2^32 by the "
+                    "ten-product tcgen05 ring GEMM, comparison without Lift (61 ANDs); the headline path is "
+                    "MPCLift"},
         "int8_mix_path": out_mix,
         "int8_tensor_only_path": out_mma,
         "int32_path": out_i32,
@@ -449,6 +510,7 @@ def run_ours(args, w):
         "ratio_int8_mix_vs_int32": (out_mix["value"] / out_i32["value"]) if out_i32 else None,
         "roofline": roofline,
         "int32_kernel": i32_kernel,
+        "tc32_kernel": tc32_kernel,
         "cpu_baseline": cpu,
         "e2e": {"value": w.comparisons * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 3 * w.Q, "wall_ms_per_step": 1e3 * wall_e2e,
