@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
-    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc32) or compare")
+    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc2 | tc32) or compare")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--serving", action="store_true",
@@ -144,13 +144,14 @@ def run_kernel(args, w):
 
         def launch():
             ipc.ipc_ring_gemm_tc32(2, x8, rows, b4, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
-    elif args.kernel == "tc":
+    elif args.kernel in ("tc", "tc2"):
         # the same limbs as bf16 bit patterns (operand conversion outside the timed launches)
         planes = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in planes]
         blo, bhi = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in (blo, bhi)]
+        gemm = ipc.ipc_ring_gemm_tc_pair if args.kernel == "tc2" else ipc.ipc_ring_gemm_tc
 
         def launch():
-            ipc.ipc_ring_gemm_tc(planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+            gemm(planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
     else:
         def launch():
             ipc.ipc_ring_gemm(args.kernel, planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, l, tags, 1, 2, 0, z,
@@ -167,7 +168,7 @@ def run_kernel(args, w):
     limbs = 4 if args.kernel == "tc32" else 2
     print(json.dumps({"kernel": args.kernel, "rows": rows, "cols": N, "ms_per_launch": ms,
                       "algorithmic_ops_per_launch": 2 * macs, "achieved_tops": 2 * macs / (ms * 1e-3) / 1e12,
-                      "operand_bytes_per_launch": (2 if args.kernel in ("tc", "tc32") else 1) *
+                      "operand_bytes_per_launch": (2 if args.kernel in ("tc", "tc2", "tc32") else 1) *
                       (2 * limbs * rows * l + limbs * n_pad * 2 * l),
                       "z_bytes": (4 if args.kernel == "tc32" else 2) * N * rows}))
 

@@ -225,6 +225,16 @@ int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2
                      size_t ldz, uint64_t row0, void* stream);
 
 /*
+ * ipc_ring_gemm_tc on CTA pairs (tcgen05 cta_group::2): same arguments, same z, bit for bit.
+ * One cluster of two CTAs computes a 256-row x 256-column tile as one M = 256 MMA, each CTA
+ * holding its 128 database rows and half of the query columns in its shared memory.
+ */
+int ipc_ring_gemm_tc_pair(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+                          const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                          const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
+                          uint16_t* z, size_t ldz, uint64_t row0, void* stream);
+
+/*
  * IPC_PATH_TC with a tile width and an optional list of column tiles (the form the serving
  * loop replays inside a CUDA graph). tile_cols: 256 or 128 query columns per tile.
  * col_tiles (device, may be NULL): indices of the tiles of that width to compute, n_col_list

@@ -98,6 +98,8 @@ _SIGS = {
                                 _u64, _vp, _vp, _vp],
     "ipc_prep_query_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_ring_gemm_tc": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
+    "ipc_ring_gemm_tc_pair": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64,
+                              _vp],
     "ipc_ring_gemm_tc_tiles": [_u32, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
                                _u64, _vp, _vp, _vp],
     "ipc_ring_gemm": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
@@ -261,6 +263,13 @@ def ipc_ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags,
     _check(lib.ipc_ring_gemm_tc(_VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
                                 ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
                                 seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
+
+
+def ipc_ring_gemm_tc_pair(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z,
+                          ldz, row0, stream=None):
+    _check(lib.ipc_ring_gemm_tc_pair(_VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
+                                     ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
+                                     seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
 
 
 def ipc_ring_gemm_tc_tiles(tile_cols, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,

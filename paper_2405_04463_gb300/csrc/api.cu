@@ -30,6 +30,10 @@ int compare_launch_liftfree(const uint16_t* const zc16[3], const uint32_t* const
                             const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a, uint32_t thr_b,
                             uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
                             cudaStream_t st);
+int ring_gemm_tc_pair(uint32_t segments, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+                      const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
+                      const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
+                      size_t ldz, uint64_t row0, cudaStream_t stream);
 int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t p, uint32_t Q, uint32_t R,
                        const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares, cudaStream_t st);
 int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
@@ -181,6 +185,18 @@ extern "C" int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const uint16_t* x_lo,
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
   return ring_gemm_tc_variant(tile_cols, 1, xl, xh, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
+}
+
+extern "C" int ipc_ring_gemm_tc_pair(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+                                     const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
+                                     uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
+                                     uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, void* stream) {
+  int rc = check_tc_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                         "ipc_ring_gemm_tc_pair");
+  if (rc != IPC_OK) return rc;
+  if (x_rows == 0 || n_cols == 0) return IPC_OK;
+  return ring_gemm_tc_pair(2, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec,
+                           z, ldz, row0, as_stream(stream));
 }
 
 extern "C" int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,

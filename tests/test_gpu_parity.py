@@ -393,6 +393,35 @@ def test_tc_gemm_matches_int32_on_random_limbs(torch, rows, N, row0):
     assert (z.cpu()[:, rows:] == 77).all()
 
 
+@pytest.mark.parametrize("rows,N,row0", [(300, 155, 0), (1000, 700, 1024), (4096, 992, 65536)])
+def test_tc_pair_matches_single_cta_and_int32(torch, rows, N, row0):
+    """The CTA-pair kernel (cta_group::2, 256-row x 256-column tiles) equals the single-CTA
+    tcgen05 kernel and the int32 path: a row pair whose second CTA is past the last row, ragged
+    column pairs, a row offset past the first chunk."""
+    ipc = lib()
+    n_pad = (N + 127) // 128 * 128
+    g = torch.Generator(device="cpu").manual_seed(rows + 3 * N)
+    planes = [torch.randint(-128, 128, (rows, L), dtype=torch.int8, generator=g).cuda() for _ in range(4)]
+    blo = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    bhi = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
+    tags = torch.from_numpy(tags_for(9, (N + 30) // 31, 31).view(np.int32)).cuda()
+    ldz = (rows + 7) // 8 * 8
+    ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, ref, ldz, row0)
+    p16 = [_bf16(torch, t) for t in planes]
+    b16 = [_bf16(torch, blo), _bf16(torch, bhi)]
+    single = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tc(p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 1, single, ldz, row0)
+    pair = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
+    ipc.ipc_ring_gemm_tc_pair(p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 1, pair, ldz, row0)
+    torch.cuda.synchronize()
+    ipc.ipc_status()
+    pair, single, ref = pair.cpu(), single.cpu(), ref.cpu()
+    assert (pair[:, :rows] == ref[:, :rows]).all()
+    assert (pair == single).all()
+    assert (pair[:, rows:] == 77).all()
+
+
 @pytest.mark.parametrize("tile_cols", [256, 128])
 def test_tc_tile_lists_match_int32(torch, tile_cols):
     """tcgen05 path with 256- and 128-column tiles: all tiles, then a sparse device-side list of
