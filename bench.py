@@ -173,6 +173,22 @@ def run_kernel(args, w):
                       "z_bytes": (4 if args.kernel == "tc32" else 2) * N * rows}))
 
 
+def max_over_ranks(x: float, device="cuda") -> float:
+    """The largest x over all ranks: the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units per second of the whole job: every rank processed units_per_rank in (at most) ms."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -199,6 +215,21 @@ def oracle_sample(w: synth.Workload, rows: int):
         return time.perf_counter() - t
 
     return step, rows * w.R, f"1 query x {w.R} rotations x {rows} database rows of the workload"
+
+
+def plaintext_rate(w: synth.Workload, rows: int, threads: int):
+    """Alg. 1 (the plaintext matcher of the oracle, all queries x rotations) on the first `rows`
+    database rows with `threads` OpenMP threads: comparisons/s. Context for the share-domain
+    numbers (the paper quotes its CPU matcher per core)."""
+    import oracle
+    og = oracle.Geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
+    dc, dm = w.db_bits(np.arange(rows))
+    qc, qm = w.query_bits()
+    t = time.perf_counter()
+    oracle.plain_match(og, qc, qm, dc, dm, threads=threads)
+    secs = time.perf_counter() - t
+    return {"value": rows * w.Q * w.R / secs, "unit": UNIT, "cores": threads, "seconds": secs,
+            "sample": f"{w.Q} queries x {w.R} rotations x {rows} database rows, plaintext Alg. 1"}
 
 
 def run_reference(args, w):
@@ -350,11 +381,7 @@ def run_ours(args, w):
         e1.synchronize()
         wall = time.perf_counter() - t0
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1))
         return ms / k, wall / k, bits.copy()
 
     main = ctxs["tc"]
@@ -375,7 +402,7 @@ def run_ours(args, w):
             ms, _, b = run_steps(ctx, args.steps, False, gal, plain, lift)
         finally:
             ipc.ipc_destroy(ctx)
-        return {"value": w.comparisons * world / (ms * 1e-3), "ms_per_step": ms,
+        return {"value": whole_job_rate(w.comparisons, world, ms), "ms_per_step": ms,
                 "bits_equal_to_headline_path": bool((b == bits).all())}
 
     out_gal = other("tcg")
@@ -469,7 +496,10 @@ def run_ours(args, w):
     if rank == 0 and not args.no_cpu_baseline:
         step, comps, sample = oracle_sample(w, args.cpu_sample_rows)
         secs = step()
-        cpu = {"value": comps / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs}
+        cpu = {"value": comps / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs,
+               "plaintext_alg1": {"one_core": plaintext_rate(w, 512, 1),
+                                  "all_cores": plaintext_rate(w, 4096, os.cpu_count() or 1),
+                                  "note": "the oracle's plaintext matcher, not the share-domain protocol"}}
 
     for c in ctxs.values():
         ipc.ipc_destroy(c)
@@ -477,7 +507,7 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
     if rank != 0:
         return
-    value = w.comparisons * world / (ms_main * 1e-3)
+    value = whole_job_rate(w.comparisons, world, ms_main)
     h2d = 2 * 3 * w.Q * w.l * 2
     flops_per_cmp = 921600.0   # 3 parties x 2 vectors x 2 l x 3 limb products x 2 ops
     res = {
@@ -513,7 +543,7 @@ def run_ours(args, w):
         "int32_kernel": i32_kernel,
         "tc32_kernel": tc32_kernel,
         "cpu_baseline": cpu,
-        "e2e": {"value": w.comparisons * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(w.comparisons, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 3 * w.Q, "wall_ms_per_step": 1e3 * wall_e2e,
                 "bits_equal": bool((bits_e2e == bits).all())},
         "gpu_launches": launches_per_step * args.steps,

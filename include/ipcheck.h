@@ -476,6 +476,18 @@ int fetch_match_bits(ipc_ctx* ctx, uint64_t req_id, uint8_t* bits_out, size_t n_
  * (host) without opening them, and keeps the request. */
 int fetch_bit_shares(ipc_ctx* ctx, uint64_t req_id, uint8_t* shares_out, size_t n_queries, int timeout_ms);
 
+/*
+ * A test entry point with no counterpart in the paper: a 64-bit fingerprint of a request's
+ * messages, for comparing runs and implementations without moving the messages. It covers every
+ * message of A4 (App. C: each party's reshared code and mask dot products, for every column and
+ * database row; protocol 1's public ml is not a message) and the three output bit components.
+ * H = XOR over messages of f(key, v), f(k, v) = mix(mix(k) + v) with mix the SplitMix64 output
+ * function, key = kind << 60 | party << 58 | column << 32 | row (kind 0 code, 1 mask, 2 output
+ * bit with column = query and row = 0), v the message as an unsigned integer (Z_2^16 or Z_2^32).
+ * Waits like fetch_bit_shares. Needs keep_distances: IPC_ENOSYS otherwise.
+ */
+int fetch_transcript_hash(ipc_ctx* ctx, uint64_t req_id, uint64_t* hash_out, int timeout_ms);
+
 /* Debug: reconstructed code dot (int16, i.e. ml - 2 hd) and mask length ml of
  * query q at rotation rho for database rows [row_begin, row_end), host
  * outputs. Needs keep_distances. Waits for the request. Errors: IPC_EINVAL,

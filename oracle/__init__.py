@@ -134,6 +134,10 @@ def _declare(L):
     L.orc_mpc_match.argtypes = [C, G, _p(u16), _p(u16), u32, _p(u16), _p(u16), u32,
                                 _p(u16), _p(u16), _p(u8), _p(u8), S]
     vp = ctypes.c_void_p
+    L.orc_mix64.argtypes = [u64]
+    L.orc_mix64.restype = u64
+    L.orc_transcript_hash.argtypes = [vp, u32, vp, u32, u32, u32, _p(u8), u32]
+    L.orc_transcript_hash.restype = u64
     L.orc_encode_share32.argtypes = [_p(u64), _p(u64), u32, u32, u64, u32, u32, _p(u32), _p(u32)]
     L.orc_mpc_dot32.argtypes = [C, _p(u32), u64, _p(u32), u64, u32, u32, u32, u32, u32, _p(u32), S]
     L.orc_mpc_compare_liftfree.argtypes = [C, ctypes.c_int, _p(u32), _p(u32), u32, u32, u32, u32, _p(u8), _p(u32), S]
@@ -485,3 +489,21 @@ def mpc_match_lift(cfg: MpcCfg, g: Geom, mode: int, db_code, db_mask, q_code, q_
                              _ptr(db_mask, ctypes.c_uint32), s, vp(q_code), _ptr(q_mask, ctypes.c_uint32), Q,
                              vp(zc), _ptr(zm, ctypes.c_uint32), _ptr(bits, ctypes.c_uint8), ctypes.byref(st))
     return {"bits": bits, "z_code": zc, "z_mask": zm, "stats": st.as_dict()}
+
+
+# ---- transcript hash (a test aid) ----
+
+def mix64(z: int) -> int:
+    """The SplitMix64 output function."""
+    return int(lib().orc_mix64(z & 0xFFFFFFFFFFFFFFFF))
+
+
+def transcript_hash(z_code, z_mask, bits) -> int:
+    """Fingerprint of a request's A4 messages z_code, z_mask ([3][n][s], u16 or u32; z_mask None
+    for protocol 1) and output bit components bits [3][Q]."""
+    zc = np.ascontiguousarray(z_code)
+    zm = None if z_mask is None else np.ascontiguousarray(z_mask)
+    b = np.ascontiguousarray(bits, dtype=np.uint8)
+    vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    return int(lib().orc_transcript_hash(vp(zc), zc.dtype.itemsize, vp(zm), 0 if zm is None else zm.dtype.itemsize,
+                                         zc.shape[1], zc.shape[2], _ptr(b, ctypes.c_uint8), b.shape[1]))

@@ -1011,3 +1011,36 @@ void orc_mpc_match_lift(const orc_mpc_cfg* cfg, const orc_geom* g, int mode, uin
   free(ry16);
   free(msb);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Transcript hash.                                                          */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static uint64_t msg_hash(uint64_t kind, uint64_t party, uint64_t col, uint64_t row, uint64_t v) {
+  uint64_t key = (kind << 60) | (party << 58) | (col << 32) | row;
+  return orc_mix64(orc_mix64(key) + v);
+}
+
+static uint64_t elem(const void* base, uint32_t bytes, size_t at) {
+  return bytes == 4 ? ((const uint32_t*)base)[at] : ((const uint16_t*)base)[at];
+}
+
+uint64_t orc_transcript_hash(const void* z_code, uint32_t elem_code, const void* z_mask, uint32_t elem_mask,
+                             uint32_t n_cols, uint32_t s, const uint8_t* bits, uint32_t Q) {
+  uint64_t h = 0;
+  for (uint32_t p = 0; p < 3; p++)
+    for (uint32_t n = 0; n < n_cols; n++)
+      for (uint32_t i = 0; i < s; i++) {
+        size_t at = ((size_t)p * n_cols + n) * s + i;
+        h ^= msg_hash(0, p, n, i, elem(z_code, elem_code, at));
+        if (z_mask) h ^= msg_hash(1, p, n, i, elem(z_mask, elem_mask, at));
+      }
+  for (uint32_t p = 0; p < 3; p++)
+    for (uint32_t q = 0; q < Q; q++) h ^= msg_hash(2, p, q, 0, bits[(size_t)p * Q + q]);
+  return h;
+}

@@ -227,6 +227,18 @@ void orc_mpc_match_lift(const orc_mpc_cfg* cfg, const orc_geom* g, int mode, uin
                         const uint32_t* q_mask, uint32_t Q, void* z_code, uint32_t* z_mask, uint8_t* bits,
                         orc_stats* st);
 
+/* ---- Transcript hash (a test aid; no counterpart in the paper) ----
+ * A 64-bit fingerprint of a request's messages: every A4 message (each party's reshared code and
+ * mask dot products, App. C) and the three output bit components. H = XOR over messages of
+ * f(key, v) = mix(mix(key) + v), mix = the SplitMix64 output function (Steele, Lea, Flood 2014),
+ * key = kind << 60 | party << 58 | column << 32 | row (kind 0 code, 1 mask, 2 output bit with
+ * column = query and row = 0), v the message as an unsigned integer. z_code, z_mask: [3][n][s]
+ * of elem_code / elem_mask bytes (2 or 4); z_mask may be NULL (protocol 1: ml is public); bits
+ * [3][Q]. orc_mix64 is exposed for its pin. */
+uint64_t orc_mix64(uint64_t z);
+uint64_t orc_transcript_hash(const void* z_code, uint32_t elem_code, const void* z_mask, uint32_t elem_mask,
+                             uint32_t n_cols, uint32_t s, const uint8_t* bits, uint32_t Q);
+
 #ifdef __cplusplus
 }
 #endif

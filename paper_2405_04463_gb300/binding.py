@@ -116,6 +116,7 @@ _SIGS = {
     "fetch_match_bits": [_vp, _u64, _vp, _sz, _int],
     "fetch_bit_shares": [_vp, _u64, _vp, _sz, _int],
     "fetch_distances": [_vp, _u64, _u32, _u32, _sz, _sz, _vp, _vp],
+    "fetch_transcript_hash": [_vp, _u64, ctypes.POINTER(_u64), _int],
     "ipc_release": [_vp, _u64],
     "ipc_db_rows": [_vp],
     "ipc_destroy": [_vp],
@@ -359,6 +360,12 @@ def submit_queries(ctx, code, mask, n_queries, src_is_device) -> int:
     _check(lib.submit_queries(ctx, _VP3(*[ptr(a) for a in code]), _VP3(*[ptr(a) for a in mask]), n_queries,
                               1 if src_is_device else 0, ctypes.byref(rid)), ctx)
     return rid.value
+
+
+def fetch_transcript_hash(ctx, req_id, timeout_ms=-1) -> int:
+    h = _u64()
+    _check(lib.fetch_transcript_hash(ctx, req_id, ctypes.byref(h), timeout_ms), ctx)
+    return h.value
 
 
 def fetch_match_bits(ctx, req_id, bits_out, n_queries, timeout_ms=-1):

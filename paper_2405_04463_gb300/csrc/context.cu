@@ -558,6 +558,76 @@ extern "C" int fetch_distances(ipc_ctx* c, uint64_t req_id, uint32_t q, uint32_t
   return IPC_OK;
 }
 
+namespace {
+
+// The SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t msg_hash(uint64_t kind, uint64_t party, uint64_t col, uint64_t row,
+                                                      uint64_t v) {
+  return mix64(mix64((kind << 60) | (party << 58) | (col << 32) | row) + v);
+}
+
+// XOR of msg_hash over one (kind, party) plane of kept dot products [n_cols][ld] (es-byte
+// elements, rows < n_rows), reduced per warp and folded into *out.
+__global__ void transcript_kernel(const uint8_t* __restrict__ z, uint32_t es, uint64_t ld, uint32_t n_cols,
+                                  uint64_t n_rows, uint32_t kind, uint32_t party, unsigned long long* out) {
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  uint64_t h = 0;
+  if (tid < static_cast<uint64_t>(n_cols) * n_rows) {
+    const uint64_t n = tid / n_rows, i = tid % n_rows;
+    const uint64_t at = n * ld + i;
+    const uint64_t v = es == 4 ? reinterpret_cast<const uint32_t*>(z)[at] : reinterpret_cast<const uint16_t*>(z)[at];
+    h = msg_hash(kind, party, n, i, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xFFFFFFFFu, h, o);
+  if ((threadIdx.x & 31) == 0 && h) atomicXor(out, static_cast<unsigned long long>(h));
+}
+
+}  // namespace
+
+extern "C" int fetch_transcript_hash(ipc_ctx* c, uint64_t req_id, uint64_t* hash_out, int timeout_ms) {
+  if (!c || !hash_out) return fail(c, IPC_EINVAL, "fetch_transcript_hash: null argument");
+  auto it = c->reqs.find(req_id);
+  if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
+  Request& r = it->second;
+  if (!r.zkeep) return fail(c, IPC_ENOSYS, "fetch_transcript_hash needs keep_distances");
+  int rc = wait_event(c, r.done, timeout_ms);
+  if (rc) return rc;
+  rc = check_device_status(c);
+  if (rc) return rc;
+  CTX_TRY(c, cudaSetDevice(c->cfg.device));
+  unsigned long long* acc = nullptr;
+  CTX_TRY(c, cudaMalloc(&acc, sizeof *acc));
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof *acc, c->sc);
+  const size_t slot = static_cast<size_t>(r.N) * r.zkeep_rows * c->zsz;
+  const uint32_t bs = 256;
+  const uint64_t total = static_cast<uint64_t>(r.N) * c->rows;
+  for (int vec = 0; vec < 2 && e == cudaSuccess; ++vec) {
+    if (vec == 1 && c->cfg.plain_mask) break;  // protocol 1: ml is public, not a message
+    for (int p = 0; p < 3 && e == cudaSuccess; ++p) {
+      transcript_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, c->sc>>>(
+          r.zkeep + (static_cast<size_t>(vec) * 3 + p) * slot, wide(c, vec) ? 4u : 2u, r.zkeep_rows, r.N, c->rows,
+          static_cast<uint32_t>(vec), static_cast<uint32_t>(p), acc);
+      e = cudaGetLastError();
+    }
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, acc, sizeof h, cudaMemcpyDeviceToHost, c->sc);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->sc);
+  cudaFree(acc);
+  if (e != cudaSuccess) return cfail(c, e, "fetch_transcript_hash");
+  for (uint32_t p = 0; p < 3; ++p)
+    for (uint32_t q = 0; q < r.Q; ++q) h ^= msg_hash(2, p, q, 0, r.shares_host[static_cast<size_t>(p) * r.Q + q]);
+  *hash_out = h;
+  return IPC_OK;
+}
+
 extern "C" int ipc_release(ipc_ctx* c, uint64_t req_id) {
   if (!c) return fail(c, IPC_EINVAL, "ipc_release: null context");
   auto it = c->reqs.find(req_id);

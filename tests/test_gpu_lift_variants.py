@@ -237,8 +237,9 @@ def test_context_lift_variant_matches_oracle(wl, torch, lift):
         else:
             dbc, qsc = c32, qc32
         ref = oracle.mpc_match_lift(oracle.mpc_cfg(w.prf_seeds, req=rid), oracle.iris_geom(), mode, dbc, m32, qsc,
-                                    qm32)
+                                    qm32, want_z=True)
         assert (sh == ref["bits"]).all()
+        assert ipc.fetch_transcript_hash(ctx, rid) == oracle.transcript_hash(ref["z_code"], ref["z_mask"], ref["bits"])
         for q, rho in ((0, 0), (0, 15), (1, 30)):
             dot = np.zeros(w.s, np.int16)
             ml = np.zeros(w.s, np.uint16)

@@ -208,8 +208,10 @@ def test_context_end_to_end_small(small, torch, path):
         sh = np.zeros((3, w.Q), np.uint8)
         ipc.fetch_bit_shares(ctx, rid, sh, w.Q, 60000)
         ref = oracle.mpc_match(oracle.mpc_cfg(w.prf_seeds, req=rid), oracle.iris_geom(), small["dbc"], small["dbm"],
-                               small["qsc"], small["qsm"])
+                               small["qsc"], small["qsm"], want_z=True)
         assert (sh == ref["bits"]).all()
+        # every A4 message and output component, through the transcript fingerprint
+        assert ipc.fetch_transcript_hash(ctx, rid) == oracle.transcript_hash(ref["z_code"], ref["z_mask"], ref["bits"])
         for q, rho in ((0, 0), (1, 15), (4, 30)):
             dot = np.zeros(w.s, np.int16)
             ml = np.zeros(w.s, np.uint16)
@@ -560,8 +562,9 @@ def test_context_galois_end_to_end(small, small_galois, torch, chunk_rows):
         sh = np.zeros((3, w.Q), np.uint8)
         ipc.fetch_bit_shares(ctx, rid, sh, w.Q, 60000)
         ref = oracle.mpc_match_galois(oracle.mpc_cfg(w.prf_seeds, req=rid), oracle.iris_geom(), small_galois["dbc"],
-                                      small_galois["dbm"], small_galois["qsc"], small_galois["qsm"])
+                                      small_galois["dbm"], small_galois["qsc"], small_galois["qsm"], want_z=True)
         assert (sh == ref["bits"]).all()
+        assert ipc.fetch_transcript_hash(ctx, rid) == oracle.transcript_hash(ref["z_code"], ref["z_mask"], ref["bits"])
         for q, rho in ((0, 0), (1, 15), (4, 30)):
             dot = np.zeros(w.s, np.int16)
             ml = np.zeros(w.s, np.uint16)

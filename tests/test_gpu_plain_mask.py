@@ -97,8 +97,10 @@ def test_context_plain_mask_matches_oracle(wl, torch, path):
         dbc, _ = enc(wl["dc"], wl["dm"], w.l, w.db_share_seed, 0)
         assert (u16(qcode) == enc(wl["qc"], wl["qm"], w.l, w.q_share_seed, 1)[0]).all()
         ref = oracle.mpc_match_plain(oracle.mpc_cfg(w.prf_seeds, req=rid), oracle.iris_geom(), dbc, wl["dm"],
-                                     u16(qcode), wl["qm"], galois=gal)
+                                     u16(qcode), wl["qm"], galois=gal, want_z=True)
         assert (sh == ref["bits"]).all()
+        # protocol 1's messages: the code dot products and the output components (ml is public)
+        assert ipc.fetch_transcript_hash(ctx, rid) == oracle.transcript_hash(ref["z_code"], None, ref["bits"])
         for q, rho in ((0, 0), (0, 15), (1, 30)):
             dot = np.zeros(w.s, np.int16)
             ml = np.zeros(w.s, np.uint16)
