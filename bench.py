@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
-    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc2 | tc32) or compare")
+    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc2 | tc32 | tc32p) or compare")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--serving", action="store_true",
@@ -133,7 +133,7 @@ def run_kernel(args, w):
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     products = 3.0
-    if args.kernel == "tc32":
+    if args.kernel in ("tc32", "tc32p"):
         # the Z_2^32 ring product: four limbs per operand, ten limb products, z as uint32
         bf = lambda t: t.float().to(torch.bfloat16).view(torch.int16).contiguous()
         x8 = [bf(torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda")) for _ in range(8)]
@@ -143,7 +143,7 @@ def run_kernel(args, w):
         products = 10.0
 
         def launch():
-            ipc.ipc_ring_gemm_tc32(2, x8, rows, b4, N, n_pad, l, tags, 1, 2, 0, z, rows, 0)
+            ipc.ipc_ring_gemm_tc32(2, x8, rows, b4, N, n_pad, l, tags, 1, 2, 0, z, rows, 0, pair=args.kernel == "tc32p")
     elif args.kernel in ("tc", "tc2"):
         # the same limbs as bf16 bit patterns (operand conversion outside the timed launches)
         planes = [t.float().to(torch.bfloat16).view(torch.int16).contiguous() for t in planes]
@@ -165,12 +165,12 @@ def run_kernel(args, w):
     ipc.ipc_status()
     ms = e0.elapsed_time(e1) / args.reps
     macs = products * N * rows * 2 * l if args.kernel != "i32" else 1.0 * N * rows * 2 * l
-    limbs = 4 if args.kernel == "tc32" else 2
+    limbs = 4 if args.kernel in ("tc32", "tc32p") else 2
     print(json.dumps({"kernel": args.kernel, "rows": rows, "cols": N, "ms_per_launch": ms,
                       "algorithmic_ops_per_launch": 2 * macs, "achieved_tops": 2 * macs / (ms * 1e-3) / 1e12,
-                      "operand_bytes_per_launch": (2 if args.kernel in ("tc", "tc2", "tc32") else 1) *
+                      "operand_bytes_per_launch": (2 if args.kernel in ("tc", "tc2", "tc32", "tc32p") else 1) *
                       (2 * limbs * rows * l + limbs * n_pad * 2 * l),
-                      "z_bytes": (4 if args.kernel == "tc32" else 2) * N * rows}))
+                      "z_bytes": (4 if args.kernel in ("tc32", "tc32p") else 2) * N * rows}))
 
 
 def max_over_ranks(x: float, device="cuda") -> float:

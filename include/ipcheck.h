@@ -328,11 +328,13 @@ int ipc_prep_query32_bf16(const uint32_t* y, uint32_t Q, const ipc_geom* g, uint
  * zero share of row g (global, row0 + r) and column n is word g & 3 of Philox(seed,
  * (g >> 2, col_tags[2n+1], col_tags[2n], IPC_D_ZA32<<24 | vec)). z: [n_cols][ldz] uint32,
  * 16-byte aligned, ldz % 4 == 0. Requires segments * l % 256 == 0, n_pad % 128 == 0,
- * n_cols <= n_pad. Errors: IPC_EINVAL for bad sizes or unaligned pointers.
+ * n_cols <= n_pad. pair != 0: CTA pairs (cta_group::2, 256-row tiles), the same z bit for bit.
+ * Errors: IPC_EINVAL for bad sizes or unaligned pointers.
  */
 int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows, const uint16_t* const b[4],
                        uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
-                       uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, void* stream);
+                       uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, uint32_t pair,
+                       void* stream);
 
 /*
  * A5-A7 without Lift (ConstLift and NoLift): ml32: [3] components over Z_2^32 of ml,

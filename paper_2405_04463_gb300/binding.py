@@ -89,7 +89,8 @@ _SIGS = {
     "ipc_encode_share32": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
     "ipc_split_limbs32_bf16": [_vp, _sz, _VP4, _vp],
     "ipc_prep_query32_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _u32, _VP4, _u32, _vp],
-    "ipc_ring_gemm_tc32": [_u32, _VP8, _sz, _VP4, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
+    "ipc_ring_gemm_tc32": [_u32, _VP8, _sz, _VP4, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _u32,
+                           _vp],
     "ipc_compare_liftfree": [_vp, _vp, _VP3, _sz, _u32, _sz, _u64, _vp, _U64x3, _u32, _u32, _u32, _vp, _sz, _vp,
                              _sz, _vp],
     "ipc_encode_share_galois": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
@@ -227,11 +228,11 @@ def ipc_prep_query32_bf16(y, Q, geom: ipc_geom, party, segments, b, n_pad, strea
 
 
 def ipc_ring_gemm_tc32(segments, x, x_rows, b, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz, row0,
-                       stream=None):
+                       pair=False, stream=None):
     xs = list(x) + [None] * (8 - len(x))
     _check(lib.ipc_ring_gemm_tc32(segments, _VP8(*[ptr(a) for a in xs]), x_rows, _VP4(*[ptr(a) for a in b]), n_cols,
                                   n_pad, l, ptr(col_tags), seed_own & (2**64 - 1), seed_prev & (2**64 - 1), vec,
-                                  ptr(z), ldz, row0, _stream(stream)))
+                                  ptr(z), ldz, row0, 1 if pair else 0, _stream(stream)))
 
 
 def ipc_compare_liftfree(z16, z32, ml32, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, thr_b,

@@ -41,6 +41,9 @@ uint8_t* plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
   return ch.planes + static_cast<size_t>((comp * 2 + vec) * c->nlimb + limb) * ch.cap * c->l * c->esz;
 }
 
+// The Z_2^32 ring GEMM on one CTA per tile: its CTA-pair form gives the same z in the same time.
+constexpr bool kTc32Pair = false;
+
 // Whether a vector (0 code, 1 mask) is shared over Z_2^32 (lifting variants) rather than Z_2^16.
 bool wide(const ipc_ctx* c, int vec) {
   return vec == 1 ? c->cfg.lift != 0 : c->cfg.lift == IPC_LIFT_NONE;
@@ -420,7 +423,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
           }
           CTX_RC(c, ring_gemm_tc32(2, x8, ch.rows, b4, N, n_pad, l, r.tags, c->cfg.seeds[i], c->cfg.seeds[prev],
                                    static_cast<uint32_t>(vec), reinterpret_cast<uint32_t*>(zo), ldz, ch.row0,
-                                   c->sp[i]));
+                                   c->sp[i], kTc32Pair));
         } else if (plain && vec == 1) {
           // protocol 1: ml = <rotated query mask, database mask> in the clear, K = l; equal seeds
           // make the zero share vanish

@@ -58,7 +58,8 @@ int prep_query_galois_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, c
                               uint16_t* b_lo, uint16_t* b_hi, uint32_t n_pad, void* stream);
 int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows, const uint16_t* const b[4],
                    uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
-                   uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, cudaStream_t stream);
+                   uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, cudaStream_t stream,
+                   bool pair);
 int prep_query32(const uint32_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party,
                  uint32_t segments, uint16_t* const b[4], uint32_t n_pad, cudaStream_t stream);
 int compare_launch_liftfree(const uint16_t* const zc16[3], const uint32_t* const zc32[3],

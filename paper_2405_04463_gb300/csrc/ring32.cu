@@ -28,7 +28,7 @@
 #include <mutex>
 #include <string>
 
-#include "tcgen05.cuh"
+#include "tcgen05_pair.cuh"
 
 namespace ipc {
 namespace {
@@ -144,20 +144,37 @@ __global__ void prep_query32_kernel(const uint32_t* __restrict__ y, uint64_t pla
 }
 
 // ----------------------------------- A3 -----------------------------------
-constexpr int TM = 128, TN = 128, KB = 32, STAGES = 3, LIMBS = 4;
-constexpr int TILE_BYTES = TM * KB * 2;              // 8 KiB: database and query tiles alike (TN = TM)
-constexpr int STAGE_BYTES = 2 * LIMBS * TILE_BYTES;  // 64 KiB
+// PAIR = false: one CTA per 128-row x 128-column tile (MMA 128 x 128 x 16).
+// PAIR = true:  a cluster of two CTAs per 256-row x 128-column tile (cta_group::2, M = 256): CTA
+//   rank r owns rows 128 r .. 128 r + 127 and holds query columns 64 r .. 64 r + 63 of the tile in
+//   its shared memory, so each SM reads half the query tile per MMA. With N = 128 a single CTA's
+//   MMAs read 8 KiB of shared memory per 64 tensor cycles, the whole read rate; the pair reads
+//   6 KiB. The leader (rank 0) issues the MMAs and commits to both CTAs' barriers; both CTAs'
+//   producers count their copies on the leader's full barrier; the drain-empty barriers live in
+//   the leader and count both CTAs' drain warps.
+constexpr int TM = 128, TN = 128, KB = 32, LIMBS = 4;
+constexpr int TILE_BYTES = TM * KB * 2;  // 8 KiB database tile
 constexpr int THREADS = 10 * 32, DRAIN_THREADS = 8 * 32;
 constexpr uint32_t KB_PER_CHUNK = 2;  // 64 k: the shortest drain period
-// full[S], empty[S], g_full[4], g_empty[4], done
-constexpr int NUM_BARS = 2 * STAGES + 9;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NUM_BARS;
 constexpr uint32_t TMEM_COLS = 4 * TN;
 constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
-// kind::f16: D f32, A and B bf16, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
-                           (static_cast<uint32_t>(TM >> 4) << 24);
-static_assert(TN * TM * 4 <= STAGES * STAGE_BYTES, "the z tile is staged in the stage ring");
+
+template <bool PAIR>
+struct Cfg32 {
+  static constexpr int HN = PAIR ? TN / 2 : TN;                  // query columns held by this CTA
+  static constexpr int B_TILE = HN * KB * 2;                     // 4 or 8 KiB
+  static constexpr int STAGE_BYTES = LIMBS * TILE_BYTES + LIMBS * B_TILE;  // 48 or 64 KiB
+  static constexpr int STAGES = PAIR ? 4 : 3;
+  // full[S], empty[S], g_full[4], g_empty[4], done
+  static constexpr int NUM_BARS = 2 * STAGES + 9;
+  // pair: 16 KiB after the ring, so that every MMA operand read stays inside the allocation
+  static constexpr int SLACK = PAIR ? 16384 : 0;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 8 * NUM_BARS;
+  // kind::f16: D f32, A and B bf16, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
+                                    (static_cast<uint32_t>((PAIR ? 2 * TM : TM) >> 4) << 24);
+  static_assert(TN * TM * 4 <= STAGES * STAGE_BYTES, "the z tile is staged in the stage ring");
+};
 
 // Drain period of S_s in 64-k chunks.
 __host__ __device__ constexpr uint32_t period(int s) { return s == 0 ? 4u : (s == 1 ? 2u : 1u); }
@@ -182,18 +199,25 @@ struct Tc32Params {
   uint32_t* status;
 };
 
+template <bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_constant__ Maps32 m, const Tc32Params p) {
+  using C = Cfg32<PAIR>;
+  constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ uint32_t s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t tiles = smem_addr(smem);
-  const uint32_t bars = tiles + STAGES * STAGE_BYTES;
+  const uint32_t bars = tiles + STAGES * STAGE_BYTES + C::SLACK;
   const uint32_t full0 = bars, empty0 = bars + 8 * STAGES;
   const uint32_t g_full = bars + 16 * STAGES, g_empty = g_full + 32, done_bar = g_full + 64;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t q0 = blockIdx.x * TN, d0 = blockIdx.y * TM;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const uint32_t q0 = (PAIR ? (blockIdx.x >> 1) : blockIdx.x) * TN;  // the tile's first query column
+  const uint32_t qh = q0 + rank * C::HN;                              // this CTA's query columns
+  const uint32_t d0 = PAIR ? blockIdx.y * (2 * TM) + rank * TM : blockIdx.y * TM;
   const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;  // a multiple of 4: K is a multiple of 256
 
   if (threadIdx.x == 0) {
@@ -203,20 +227,29 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     }
     for (int g = 0; g < 4; ++g) {
       mbar_init(g_full + 8 * g, 1);
-      mbar_init(g_empty + 8 * g, DRAIN_THREADS / 32);
+      mbar_init(g_empty + 8 * g, (PAIR ? 2 : 1) * DRAIN_THREADS / 32);
     }
     mbar_init(done_bar, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair allocates, collectively, the same columns in both
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs' barriers exist before any remote arrive or TMA
   fence_after();
   const uint32_t tmem = s_tmem;
 
@@ -227,28 +260,42 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
       for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
         const uint32_t s = kb % STAGES;
         if (!mbar_wait(empty0 + 8 * s, ((kb / STAGES) & 1u) ^ 1u, p.status, abort)) break;
-        const uint32_t full = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
-        mbar_expect_tx(full, STAGE_BYTES);
+        const uint32_t full_own = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
         const bool first = kb < p.kb_half;
         const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
+        if constexpr (PAIR) {
+          if (leader) mbar_expect_tx(full_own, 2 * STAGE_BYTES);  // both CTAs' halves
+          const uint32_t full = peer_addr(full_own, 0);
 #pragma unroll
-        for (int a = 0; a < LIMBS; ++a)
-          tma_load(base + a * TILE_BYTES, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full);
+          for (int a = 0; a < LIMBS; ++a)
+            tma_load_pair(base + a * TILE_BYTES, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full);
 #pragma unroll
-        for (int b = 0; b < LIMBS; ++b)
-          tma_load(base + (LIMBS + b) * TILE_BYTES, &m.b[b], static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0),
-                   full);
+          for (int b = 0; b < LIMBS; ++b)
+            tma_load_pair(base + LIMBS * TILE_BYTES + b * C::B_TILE, &m.b[b], static_cast<int32_t>(kb * KB),
+                          static_cast<int32_t>(qh), full);
+        } else {
+          mbar_expect_tx(full_own, STAGE_BYTES);
+#pragma unroll
+          for (int a = 0; a < LIMBS; ++a)
+            tma_load(base + a * TILE_BYTES, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full_own);
+#pragma unroll
+          for (int b = 0; b < LIMBS; ++b)
+            tma_load(base + LIMBS * TILE_BYTES + b * C::B_TILE, &m.b[b], static_cast<int32_t>(kb * KB),
+                     static_cast<int32_t>(qh), full_own);
+        }
         issued = kb + 1;
       }
       if (*abort) {
-        // copies that may still be in flight land before the CTA leaves (bounded, no abort)
+        // copies that may still be in flight land before the CTA goes on (bounded, no abort);
+        // a pair's copies are counted on the leader's barriers, so its own stage-empty phases
+        // stand in for them
         for (uint32_t kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-          mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1u, p.status, nullptr);
+          mbar_wait((PAIR ? empty0 : full0) + 8 * (kb % STAGES), (kb / STAGES) & 1u, p.status, nullptr);
       }
     }
   } else if (warp == 1) {
-    // -------------------------------- MMA issuer --------------------------------
-    if (lane == 0) {
+    // ------------------------- MMA issuer (the leader of a pair) -------------------------
+    if (leader && lane == 0) {
       bool ok = true;
       for (uint32_t kb = 0; kb < p.kb_total && ok; ++kb) {
         const uint32_t s = kb % STAGES, c = kb / KB_PER_CHUNK, j = kb % KB_PER_CHUNK;
@@ -271,21 +318,46 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
           for (uint32_t ks = 0; ks < KB / 16; ++ks) {
             const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
 #pragma unroll
-            for (int a = 0; a <= g; ++a)
-              umma(t, sdesc(base + a * TILE_BYTES + o), sdesc(base + (LIMBS + g - a) * TILE_BYTES + o), IDESC);
+            for (int a = 0; a <= g; ++a) {
+              const uint64_t da = sdesc(base + a * TILE_BYTES + o);
+              const uint64_t db = sdesc(base + LIMBS * TILE_BYTES + (g - a) * C::B_TILE + o);
+              if constexpr (PAIR)
+                umma_pair_desc(t, da, db, C::IDESC);
+              else
+                umma(t, da, db, C::IDESC);
+            }
           }
-          if (j == KB_PER_CHUNK - 1 && c % per == per - 1) umma_commit(g_full + 8 * g);
+          if (j == KB_PER_CHUNK - 1 && c % per == per - 1) {
+            if constexpr (PAIR)
+              umma_commit_pair(g_full + 8 * g);
+            else
+              umma_commit(g_full + 8 * g);
+          }
         }
-        if (ok) umma_commit(empty0 + 8 * s);  // stage free once these (and all earlier) MMAs are done
+        if (ok) {  // stage free once these (and all earlier) MMAs are done
+          if constexpr (PAIR)
+            umma_commit_pair(empty0 + 8 * s);
+          else
+            umma_commit(empty0 + 8 * s);
+        }
       }
       // every MMA issued above completes before the tensor memory is freed
-      umma_commit(done_bar);
+      if constexpr (PAIR)
+        umma_commit_pair(done_bar);
+      else
+        umma_commit(done_bar);
       mbar_wait(done_bar, 0, p.status, nullptr);
     }
   } else {
     // ----------------------------------- drain ----------------------------------
     const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - 2) >> 2;
     const uint32_t tl = tmem + ((32u * q) << 16) + 64u * h;
+    auto release = [&](int g) {
+      if constexpr (PAIR)
+        arrive_leader(g_empty + 8 * g, leader);
+      else
+        mbar_arrive(g_empty + 8 * g);
+    };
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       tmem_fill32(tl + TN * g, MAGIC);
@@ -295,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     fence_before();
     __syncwarp();
     if (lane == 0)
-      for (int g = 0; g < 4; ++g) mbar_arrive(g_empty + 8 * g);
+      for (int g = 0; g < 4; ++g) release(g);
     // each S_1 drain adds bits(M) << 8 and each S_0 drain bits(M) once too often
     const uint32_t corr = 0u - (n_chunks / period(1)) * (MAGIC << 8) - (n_chunks / period(0)) * MAGIC;
     uint32_t acc[64];
@@ -324,7 +396,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
         tmem_wait_st();
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(g_empty + 8 * g);
+        if (lane == 0) release(g);
       }
     }
     // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) over Z_{2^32} (App. C) ----
@@ -359,23 +431,63 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
       }
     }
   }
+  // a pair's MMAs are complete (the leader's issuer waited for them) before either CTA frees
+  // tensor memory or leaves
   fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+template <bool PAIR>
+int launch_tc32(const Maps32& m, const Tc32Params& p, uint32_t n_cols, size_t x_rows, cudaStream_t stream) {
+  using C = Cfg32<PAIR>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(gemm_tc32_kernel<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+  });
+  IPC_CUDA_TRY(attr);
+  const uint32_t rows_per = PAIR ? 2 * TM : TM;
+  const dim3 grid((PAIR ? 2 : 1) * ((n_cols + TN - 1) / TN), static_cast<unsigned>((x_rows + rows_per - 1) / rows_per));
+  if constexpr (PAIR) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = C::SMEM_BYTES;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    IPC_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_tc32_kernel<true>, m, p));
+  } else {
+    gemm_tc32_kernel<false><<<grid, THREADS, C::SMEM_BYTES, stream>>>(m, p);
+  }
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
 }  // namespace
 
 // segments: 2 for K = 2l over [x[0..3] | x[4..7]] (ABY3 replicated sharing, x[4..7] the
 // previous party's component), 1 for K = l over x[0..3] alone. K must be a multiple of 256.
+// pair: CTA pairs (256-row tiles) instead of one CTA per 128-row tile; the same z bit for bit.
 int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows, const uint16_t* const b[4],
                    uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
-                   uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, cudaStream_t stream) {
+                   uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, cudaStream_t stream,
+                   bool pair) {
   if (segments != 1 && segments != 2) {
     set_error("Z_2^32 ring GEMM: one or two K segments");
     return IPC_EINVAL;
@@ -393,10 +505,11 @@ int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows,
     set_error("Z_2^32 ring GEMM: too many rows for one launch");
     return IPC_EINVAL;
   }
+  const uint32_t hn = pair ? TN / 2 : TN;
   Maps32 m;
   int rc;
   for (int i = 0; i < LIMBS; ++i) {
-    if ((rc = make_map_bf16(&m.b[i], b[i], static_cast<uint64_t>(segments) * l, n_pad, TN)) ||
+    if ((rc = make_map_bf16(&m.b[i], b[i], static_cast<uint64_t>(segments) * l, n_pad, hn)) ||
         (rc = make_map_bf16(&m.a0[i], x[i], l, x_rows, TM)) ||
         (rc = make_map_bf16(&m.a1[i], x[segments == 2 ? LIMBS + i : i], l, x_rows, TM)))
       return rc;
@@ -414,16 +527,7 @@ int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows,
   p.ldz = ldz;
   p.row0 = row0;
   p.status = status_ptr();
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(gemm_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
-  IPC_CUDA_TRY(attr);
-  const dim3 grid((n_cols + TN - 1) / TN, static_cast<unsigned>((x_rows + TM - 1) / TM));
-  gemm_tc32_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(m, p);
-  IPC_CUDA_TRY(cudaGetLastError());
-  return IPC_OK;
+  return pair ? launch_tc32<true>(m, p, n_cols, x_rows, stream) : launch_tc32<false>(m, p, n_cols, x_rows, stream);
 }
 
 int prep_query32(const uint32_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party,
@@ -494,7 +598,7 @@ extern "C" int ipc_prep_query32_bf16(const uint32_t* y, uint32_t Q, const ipc_ge
 extern "C" int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows,
                                   const uint16_t* const b[4], uint32_t n_cols, uint32_t n_pad, uint32_t l,
                                   const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
-                                  uint32_t* z, size_t ldz, uint64_t row0, void* stream) {
+                                  uint32_t* z, size_t ldz, uint64_t row0, uint32_t pair, void* stream) {
   if (!x || !b || !col_tags || !z) {
     set_error("ipc_ring_gemm_tc32: null pointer");
     return IPC_EINVAL;
@@ -510,5 +614,5 @@ extern "C" int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8],
     return IPC_EINVAL;
   }
   return ring_gemm_tc32(segments, x, x_rows, b, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz, row0,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream), pair != 0);
 }

@@ -93,7 +93,7 @@ def test_prep_query32_is_rotated_aby3_operand(torch):
             assert (got[Q * R:] == 0).all()
 
 
-def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5)):
+def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5), pair=True):
     ipc = lib()
     n_pad = (N + 127) // 128 * 128
     K = segments * L
@@ -109,7 +109,7 @@ def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5)):
     tags = torch.from_numpy(tags_for(3, (N + 30) // 31, 31)[:N].copy().view(np.int32)).cuda()
     ldz = (rows + 7) // 8 * 8
     z = torch.full((N, ldz), 77, dtype=torch.int32, device="cuda")
-    ipc.ipc_ring_gemm_tc32(segments, xd, rows, bd, N, n_pad, L, tags, seeds[0], seeds[1], 1, z, ldz, row0)
+    ipc.ipc_ring_gemm_tc32(segments, xd, rows, bd, N, n_pad, L, tags, seeds[0], seeds[1], 1, z, ldz, row0, pair=pair)
     torch.cuda.synchronize()
     ipc.ipc_status()
     # exact reference: per limb pair (a, b) with a + b < 4 the integer product sum (below 2^29 in
@@ -124,17 +124,20 @@ def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5)):
     return u32(z), ref.astype(np.uint32), tags
 
 
+@pytest.mark.parametrize("pair", [False, True])
 @pytest.mark.parametrize("rows,N,segments,row0", [(300, 200, 2, 0), (1000, 93, 2, 1024), (130, 128, 1, 0)])
-def test_gemm_tc32_exact_on_random_limbs(torch, rows, N, segments, row0):
+def test_gemm_tc32_exact_on_random_limbs(torch, rows, N, segments, row0, pair):
     """Equal seeds make the zero share vanish: z is the exact ring product; ragged row and column
-    tiles, one and two K segments."""
-    z, ref, _ = _gemm_case(torch, rows, N, segments, row0)
+    tiles, one and two K segments, one CTA per tile and CTA pairs (the second CTA of the last
+    pair past the last row)."""
+    z, ref, _ = _gemm_case(torch, rows, N, segments, row0, pair=pair)
     assert (z[:, :rows] == ref).all()
     assert (z[:, rows:] == 77).all()
 
 
-def test_gemm_tc32_exact_at_extreme_limbs(torch):
-    z, ref, _ = _gemm_case(torch, 128, 128, 2, 0, extreme=True)
+@pytest.mark.parametrize("pair", [False, True])
+def test_gemm_tc32_exact_at_extreme_limbs(torch, pair):
+    z, ref, _ = _gemm_case(torch, 128, 128, 2, 0, extreme=True, pair=pair)
     assert (z[:, :128] == ref).all()
 
 
