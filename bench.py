@@ -321,10 +321,24 @@ def ncu_traffic(kernel: str, src: str):
 
 
 def source_hash(src: str) -> str:
-    """SHA-256 of a kernel's .cu file followed by the headers its device code includes."""
-    hs = hashlib.sha256(open(src, "rb").read())
-    for hdr in ("tcgen05.cuh", "common.cuh"):
-        hs.update(open(os.path.join(ROOT, "paper_2405_04463_gb300", "csrc", hdr), "rb").read())
+    """SHA-256 of a kernel's .cu file followed by the headers it includes from its own directory,
+    depth first in order of first inclusion."""
+    seen, order = set(), []
+
+    def visit(path):
+        if path in seen:
+            return
+        seen.add(path)
+        order.append(path)
+        for inc in re.findall(r'^#include "([^"/]+)"', open(path).read(), re.M):  # same directory only
+            dep = os.path.join(os.path.dirname(path), inc)
+            if os.path.exists(dep):
+                visit(dep)
+
+    visit(src)
+    hs = hashlib.sha256()
+    for path in order:
+        hs.update(open(path, "rb").read())
     return hs.hexdigest()
 
 
