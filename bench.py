@@ -537,6 +537,15 @@ def run_ours(args, w):
                    "l2": "inputs larger than L2: resident limb planes 24 B x rows x 12800 = "
                          f"{24 * w.s * w.l / 1e9:.1f} GB"},
         "tensor_peak_frac_step": value * flops_per_cmp / (bf16_sust * 1e12) if bf16_sust else None,
+        # the metric's "% of INT8 peak": limb ops per second (921,600 per comparison) against the
+        # measured dense INT8 tensor rate of this GPU (mma.sync s8; sm_103a has no integer tcgen05)
+        "int8_peak": {
+            "measured_mma_sync_s8_tops": peak_mma,
+            "headline_pct": 100.0 * value * flops_per_cmp / (peak_mma * 1e12),
+            "int8_tensor_only_path_pct": 100.0 * out_mma["value"] * flops_per_cmp / (peak_mma * 1e12),
+            "int8_mix_path_pct_of_mma_plus_dp4a": 100.0 * out_mix["value"] * flops_per_cmp /
+            ((peak_mma + peak_dp4a) * 1e12),
+            "note": "the headline carries the int8 limbs on the bf16 tcgen05 tensor cores, exactly"},
         "galois_shamir_path": dict(out_gal, note="the paper's deployed sharing of the dot products "
                                                  "(Sec. 4.3.2): one length-l GEMM per party and vector "
                                                  "instead of 2l, same tcgen05 kernel, same comparison phase"),
