@@ -51,6 +51,28 @@ bool wide(const ipc_ctx* c, int vec) {
 
 uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
+// Frees a request's buffers on every early return of submit_queries, after the device has
+// finished whatever was already enqueued on them; keep() hands them to the context instead.
+class RequestGuard {
+ public:
+  RequestGuard(ipc_ctx* c, Request* r) : c_(c), r_(r) {}
+  ~RequestGuard();
+  void keep() { r_ = nullptr; }
+
+ private:
+  ipc_ctx* c_;
+  Request* r_;
+};
+
+void free_request(ipc_ctx* c, Request& r);
+
+RequestGuard::~RequestGuard() {
+  if (!r_) return;
+  cudaDeviceSynchronize();
+  cudaGetLastError();
+  free_request(c_, *r_);
+}
+
 void free_request(ipc_ctx* c, Request& r) {
   cudaFree(r.bq);
   cudaFree(r.qstage);
@@ -307,6 +329,9 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   int rc = ensure_zbuf(c, n_pad);
   if (rc) return rc;
 
+  // declared before the request guard, so that an early return synchronises before the host
+  // source of the tag copy goes away
+  std::vector<uint32_t> tags(2ull * N);
   Request r;
   {
     std::lock_guard<std::mutex> lock(c->id_mu);
@@ -329,13 +354,12 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
     r.zkeep_rows = round_up(static_cast<uint32_t>(c->chunks.size() * c->cfg.db_chunk_rows), 8);
     ok = cudaMalloc(&r.zkeep, 2ull * 3 * N * r.zkeep_rows * c->zsz) == cudaSuccess;
   }
+  RequestGuard guard(c, &r);  // from here on every early return frees the request
   if (!ok) {
     cudaGetLastError();
-    free_request(c, r);
     return fail(c, IPC_ENOMEM, "submit_queries: not enough device memory for the request");
   }
   // column tags: (request id, q << 5 | rho)
-  std::vector<uint32_t> tags(2ull * N);
   for (uint32_t q = 0; q < Q; ++q)
     for (uint32_t rho = 0; rho < R; ++rho) {
       tags[2 * (q * R + rho)] = static_cast<uint32_t>(r.id);
@@ -343,10 +367,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
     }
   if (src_is_device) {
     rc = order_after_input(c);
-    if (rc) {
-      free_request(c, r);
-      return rc;
-    }
+    if (rc) return rc;
   }
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CTX_TRY(c, cudaMemcpyAsync(r.tags, tags.data(), tags.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
@@ -487,6 +508,7 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   CTX_TRY(c, cudaMemcpyAsync(r.shares_host, r.shares_dev, 3ull * Q, cudaMemcpyDeviceToHost, c->sc));
   CTX_TRY(c, cudaEventRecord(r.done, c->sc));
   CTX_TRY(c, cudaEventSynchronize(c->ev_setup));  // the tag vector above is a host temporary
+  guard.keep();
   c->reqs[r.id] = r;
   *req_id = r.id;
   return IPC_OK;

@@ -220,11 +220,13 @@ extern "C" int ipc_check_persons(ipc_ctx* const ctx[2], const uint16_t* const co
   }
   // database bits (waits for the requests), then the per-person OR on the device
   std::vector<uint8_t> host(6ull * P);
-  for (int e = 0; e < 2; ++e) {
-    int rc = fetch_bit_shares(ctx[e], rid[e], host.data() + 3ull * P * e, P, timeout_ms);
+  int fetch_rc = IPC_OK;
+  for (int e = 0; e < 2; ++e) {  // both requests are released whatever happens
+    const int rc = fetch_rc ? fetch_rc : fetch_bit_shares(ctx[e], rid[e], host.data() + 3ull * P * e, P, timeout_ms);
     ipc_release(ctx[e], rid[e]);
-    if (rc) return rc;
+    fetch_rc = rc;
   }
+  if (fetch_rc) return fetch_rc;
   uint8_t* dev = nullptr;
   if (cudaMalloc(&dev, 12ull * P) != cudaSuccess) {
     cudaGetLastError();
