@@ -107,26 +107,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     my_items = n_items > blockIdx.x ? (n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     if (my_items == 0) return;  // uniform for the CTA, before any barrier or allocation
   }
+  // Tiles are taken in linear order (blocks are dispatched in blockIdx order; a persistent CTA
+  // takes items blockIdx.x + i gridDim.x). The order walks bands of up to kBand column tiles,
+  // all row tiles of a band before the next, so that the tiles in flight at once (one CTA per
+  // SM) cover about 19 row tiles x 8 column tiles: each database tile is read by the band's
+  // CTAs together and the band's query tiles stay in L2 while the rows stream past (with many
+  // query columns the whole query operand is several times the L2).
+  constexpr uint32_t kBand = 8;
   auto coords = [&](uint32_t i, uint32_t& q0, uint32_t& d0) {
-    if (LIST) {
-      const uint32_t w = blockIdx.x + i * gridDim.x;
-      q0 = p.col_tiles[w % n_ct] * TN;
-      d0 = (w / n_ct) * TM;
-    } else {
-      // Blocks are dispatched in linear order. Walk the tiles in bands of up to kBand column
-      // tiles, all row tiles of a band before the next, so that a wave of one CTA per SM covers
-      // about 19 row tiles x 8 column tiles: each database tile is read by the band's CTAs
-      // together and the band's query tiles stay in L2 while the rows stream past (with many
-      // query columns the whole query operand is several times the L2).
-      constexpr uint32_t kBand = 8;
-      const uint32_t n_ct_all = gridDim.x, n_rt = gridDim.y;
-      const uint32_t lin = blockIdx.x + n_ct_all * blockIdx.y;
-      const uint32_t band = lin / (kBand * n_rt), c0 = band * kBand;
-      const uint32_t width = n_ct_all - c0 < kBand ? n_ct_all - c0 : kBand;
-      const uint32_t in_band = lin - band * kBand * n_rt;
-      q0 = (c0 + in_band % width) * TN;
-      d0 = (in_band / width) * TM;
-    }
+    const uint32_t n_cols_t = LIST ? n_ct : gridDim.x;
+    const uint32_t n_rt = LIST ? p.n_row_tiles : gridDim.y;
+    const uint32_t lin = LIST ? blockIdx.x + i * gridDim.x : blockIdx.x + gridDim.x * blockIdx.y;
+    const uint32_t band = lin / (kBand * n_rt), c0 = band * kBand;
+    const uint32_t width = n_cols_t - c0 < kBand ? n_cols_t - c0 : kBand;
+    const uint32_t in_band = lin - band * kBand * n_rt;
+    const uint32_t ct = c0 + in_band % width;
+    q0 = (LIST ? p.col_tiles[ct] : ct) * TN;
+    d0 = (in_band / width) * TM;
   };
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t tiles = smem_addr(smem);
