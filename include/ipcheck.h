@@ -407,6 +407,15 @@ int ipc_compare_or_noalloc(const uint16_t* const z_code[3], const uint16_t* cons
  * synchronising it: IPC_OK, or IPC_EDEVICE if a kernel gave up a bounded wait. */
 int ipc_status(void);
 
+/*
+ * A test aid for the error path (no counterpart in the paper): runs, on the calling device and
+ * stream, a one-thread kernel that waits for a device flag that nothing sets, gives up after
+ * limit_us microseconds of global time (1..1,000,000) and raises the status word as a pipeline
+ * kernel's bounded wait does. Returns when the kernel has finished; the next ipc_status (or
+ * the next fetch of a context on this device) then reports IPC_EDEVICE.
+ */
+int ipc_selftest_bounded_wait(uint32_t limit_us, void* stream);
+
 /* ======================================================================== */
 /* Context-level API: resident database, request submission and fetch.      */
 /* ======================================================================== */

@@ -118,6 +118,7 @@ _SIGS = {
     "fetch_bit_shares": [_vp, _u64, _vp, _sz, _int],
     "fetch_distances": [_vp, _u64, _u32, _u32, _sz, _sz, _vp, _vp],
     "fetch_transcript_hash": [_vp, _u64, ctypes.POINTER(_u64), _int],
+    "ipc_selftest_bounded_wait": [_u32, _vp],
     "ipc_release": [_vp, _u64],
     "ipc_db_rows": [_vp],
     "ipc_destroy": [_vp],
@@ -320,6 +321,10 @@ def ipc_compare_or_noalloc(z_code, z_mask, ldz, Q, R, n_rows, col_tags, seeds, t
 
 def ipc_status():
     _check(lib.ipc_status())
+
+
+def ipc_selftest_bounded_wait(limit_us, stream=None):
+    _check(lib.ipc_selftest_bounded_wait(limit_us, _stream(stream)))
 
 
 # ---------------------------------------------------------------------------------------------

@@ -35,7 +35,44 @@ uint32_t* status_ptr() {
   return g_status[dev];
 }
 
+namespace {
+
+// Waits for *flag to become non-zero, giving up after limit_ns of global time; on giving up it
+// raises the status word exactly as a pipeline kernel's bounded wait does.
+__global__ void bounded_wait_kernel(const volatile uint32_t* flag, uint64_t limit_ns, uint32_t* status) {
+  if (threadIdx.x != 0) return;
+  const uint64_t t0 = global_ns();
+  while (*flag == 0u) {
+    if (global_ns() - t0 > limit_ns) {
+      raise_status(status, ST_WAIT_TIMEOUT);
+      return;
+    }
+  }
+}
+
+}  // namespace
 }  // namespace ipc
+
+extern "C" int ipc_selftest_bounded_wait(uint32_t limit_us, void* stream) {
+  if (limit_us == 0 || limit_us > 1000000) {
+    ipc::set_error("ipc_selftest_bounded_wait: limit_us must be in 1..1000000");
+    return IPC_EINVAL;
+  }
+  uint32_t* status = ipc::status_ptr();
+  if (!status) return ipc::cuda_fail(cudaErrorMemoryAllocation, "status word");
+  cudaStream_t st = ipc::as_stream(stream);
+  uint32_t* flag = nullptr;
+  IPC_CUDA_TRY(cudaMalloc(&flag, sizeof(uint32_t)));
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(uint32_t), st);  // nothing ever sets it
+  if (e == cudaSuccess) {
+    ipc::bounded_wait_kernel<<<1, 32, 0, st>>>(flag, 1000ull * limit_us, status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(flag);
+  if (e != cudaSuccess) return ipc::cuda_fail(e, "ipc_selftest_bounded_wait");
+  return IPC_OK;
+}
 
 extern "C" int ipc_status(void) {
   IPC_CUDA_TRY(cudaDeviceSynchronize());
