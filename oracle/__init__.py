@@ -117,6 +117,7 @@ def _declare(L):
     L.orc_mpc_compare.argtypes = [C, _p(u16), _p(u16), u32, u32, u32, _p(u8), _p(u32), _p(u32), S]
     L.orc_bit_extract.argtypes = [C, _p(u32), u32, u32, u32, u32, u32, _p(u8), _p(u8), S]
     L.orc_or_tree.argtypes = [C, _p(u8), u32, u32, u32, _p(u8), S]
+    L.orc_bit_extract_batch.argtypes = [C, _p(u32), u32, u32, u32, _p(u8), _p(u8)]
     L.orc_gr_mul.argtypes = [_p(u16), _p(u16), _p(u16)]
     L.orc_gr_inv.argtypes = [_p(u16), _p(u16)]
     L.orc_gr_inv.restype = ctypes.c_int
@@ -256,6 +257,17 @@ def bit_extract(cfg: MpcCfg, x, m: int, q: int = 0, rho: int = 0, i: int = 0, ga
     st = stats if stats is not None else Stats()
     lib().orc_bit_extract(ctypes.byref(cfg), _ptr(xx, ctypes.c_uint32), m, q, rho, i, gate0,
                           _ptr(top, ctypes.c_uint8), _ptr(below, ctypes.c_uint8), ctypes.byref(st))
+    return top, below
+
+
+def bit_extract_batch(cfg: MpcCfg, x, m: int, gate0: int = 0):
+    """orc_bit_extract over rows of x [n][3] (row i at counter row i) -> (top [n][3], below [n][3])."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    n = x.shape[0]
+    top = np.zeros((n, 3), np.uint8)
+    below = np.zeros((n, 3), np.uint8)
+    lib().orc_bit_extract_batch(ctypes.byref(cfg), _ptr(x, ctypes.c_uint32), n, m, gate0,
+                                _ptr(top, ctypes.c_uint8), _ptr(below, ctypes.c_uint8))
     return top, below
 
 

@@ -501,6 +501,14 @@ void orc_mpc_compare(const orc_mpc_cfg* cfg, const uint16_t dot[3], const uint16
   st->depth_total = top.depth;
 }
 
+void orc_bit_extract_batch(const orc_mpc_cfg* cfg, const uint32_t* x, uint32_t n, uint32_t m, uint32_t gate0,
+                           uint8_t* top, uint8_t* below) {
+  orc_stats st;
+  memset(&st, 0, sizeof st);
+  for (uint32_t i = 0; i < n; i++)
+    orc_bit_extract(cfg, x + 3 * (size_t)i, m, 0, 0, i, gate0, top + 3 * (size_t)i, below + 3 * (size_t)i, &st);
+}
+
 /* OR of two boolean sharings (Sec. 4.2): x OR y = x + y + x*y. */
 static rss_t bor(rss_t a, rss_t b, uint32_t F[3], orc_stats* st) {
   return bxor(bxor(a, b), band(a, b, F, st));

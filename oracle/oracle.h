@@ -119,6 +119,11 @@ void orc_bit_extract(const orc_mpc_cfg* cfg, const uint32_t x[3], uint32_t m,
                      uint32_t q, uint32_t rho, uint32_t i, uint32_t gate0,
                      uint8_t top[3], uint8_t below[3], orc_stats* st);
 
+/* orc_bit_extract over n independent sharings x[n][3] (row i uses counter row i), writing
+ * top[n][3] and below[n][3]: a loop, for pins over many values. */
+void orc_bit_extract_batch(const orc_mpc_cfg* cfg, const uint32_t* x, uint32_t n, uint32_t m, uint32_t gate0,
+                           uint8_t* top, uint8_t* below);
+
 /* OR tree of one query over its MSB bit components msb[3][R][s] -> bit[3]. */
 void orc_or_tree(const orc_mpc_cfg* cfg, const uint8_t* msb, uint32_t R, uint32_t s,
                  uint32_t q, uint8_t bit[3], orc_stats* st);

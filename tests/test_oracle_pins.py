@@ -250,6 +250,26 @@ def test_bit_extract_msb_edges_and_random():
         assert oracle.reconstruct_bits(below) == (v >> 30) & 1
 
 
+def test_bit_extract_million_random_and_every_16bit_value():
+    """MSB and the bit below it of a million random 32-bit sharings (App. D), and of every 16-bit
+    value under four random share triples each (Sec. 4.3.1)."""
+    rng = np.random.default_rng(15)
+    cfg = oracle.mpc_cfg((7, 8, 9))
+    n = 1_000_000
+    v = rng.integers(0, 2**32, n, dtype=np.uint64)
+    a = rng.integers(0, 2**32, (n, 2), dtype=np.uint64)
+    x = np.stack([a[:, 0], a[:, 1], (v - a[:, 0] - a[:, 1]) & 0xFFFFFFFF], axis=1).astype(np.uint32)
+    top, below = oracle.bit_extract_batch(cfg, x, 31, oracle.MSB_GATE0)
+    assert (oracle.reconstruct_bits(top.T) == (v >> 31)).all()
+    assert (oracle.reconstruct_bits(below.T) == ((v >> 30) & 1)).all()
+    v16 = np.tile(np.arange(1 << 16, dtype=np.uint64), 4)
+    a16 = rng.integers(0, 1 << 16, (v16.size, 2), dtype=np.uint64)
+    x16 = np.stack([a16[:, 0], a16[:, 1], (v16 - a16[:, 0] - a16[:, 1]) & 0xFFFF], axis=1).astype(np.uint32)
+    top16, below16 = oracle.bit_extract_batch(cfg, x16, 15)
+    assert (oracle.reconstruct_bits(top16.T) == (v16 >> 15)).all()
+    assert (oracle.reconstruct_bits(below16.T) == ((v16 >> 14) & 1)).all()
+
+
 def test_bit_extract_counts_match_paper(golden):
     counts = {r[0]: r[1] for r in golden("paper_counts.txt")}
     cfg = oracle.mpc_cfg()
