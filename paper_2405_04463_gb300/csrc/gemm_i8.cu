@@ -213,7 +213,7 @@ __device__ __forceinline__ void dp4a_consumer(const Params& p, const Work<LIST>&
   const uint32_t ra7 = tq & 7u, rb7 = td & 7u;  // swizzle phase of this thread's rows
   for (uint32_t i = 0; i < wk.items(); ++i) {
     uint32_t q0, d0;
-    wk.coords<128>(p, i, q0, d0);
+    wk.template coords<128>(p, i, q0, d0);
     int accL[8][4], accC[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreads<MODE>, 1)
   auto issue = [&](uint32_t G) {
     const uint32_t i = G / p.ktiles, kt = G % p.ktiles;
     uint32_t q0, d0;
-    wk.coords<BQ>(p, i, q0, d0);
+    wk.template coords<BQ>(p, i, q0, d0);
     const uint32_t s = G % STAGES;
     const uint32_t full = bars + 8 * s;
     const uint32_t base = tiles + s * SB;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kThreads<MODE>, 1)
 
   for (uint32_t i = 0; i < wk.items(); ++i) {
     uint32_t q0, d0;
-    wk.coords<BQ>(p, i, q0, d0);
+    wk.template coords<BQ>(p, i, q0, d0);
     int accL[MF][4][4], accC[MF][4][4];
 #pragma unroll
     for (int m = 0; m < MF; ++m)
