@@ -1,8 +1,8 @@
 // A4-A8 -- the comparison phase of Alg. 3 on reshared dot products, bit-sliced.
 //
-// One thread simulates the three parties for one query column and a block of
-// 32-row words: 32 comparisons share one 32-bit word per bit position and share
-// component. The arithmetic-to-boolean steps (ShareSplit, full-adder layer,
+// A small group of threads simulates the three parties for one query column and one
+// block of 32-row words (each thread a part of the block, joined by the block's upper OR
+// gates): 32 comparisons share one 32-bit word per bit position and share component. The arithmetic-to-boolean steps (ShareSplit, full-adder layer,
 // ripple-carry BinAdd; App. D) then run 32 comparisons per logic instruction.
 // Party p only ever combines its own pair of components (c_p, c_{p-1}) and the
 // PRF outputs of its two seeds, as in the App. C product.
@@ -137,10 +137,17 @@ struct CmpParams {
 
 constexpr int MODE_LIFT = 0, MODE_PLAIN = 1, MODE_LIFTFREE = 2;
 
-// Shared memory per thread (index [slot][threadIdx.x], conflict-free):
-//   raw ml / dot: 3 x 16 words each (two u16 per word), X (lift input words, later v words): 96,
-//   OR stack: 3 x 6.
-constexpr int S_RAWML = 0, S_RAWDOT = 48, S_X = 96, S_STK = 192, S_WORDS = 210;
+// 2^ks threads share one (column, OR block), ks = min(LOG2_SPLIT, p): thread t takes the t-th
+// part of the block's words (a level sub_p = p - ks subtree) and the group joins the parts
+// pairwise with the block's upper ks levels of OR gates. Gate indices are global node indices
+// at each level, so the tree and every share are the same as one thread walking the whole
+// block. With 1,024-row blocks each thread takes 4 words.
+constexpr uint32_t LOG2_SPLIT = 3;
+
+// Shared memory per thread (index [slot][threadIdx.x], conflict-free): X, 3 x 32 words (per
+// component: the lift input bit-slices in words 0..15 and the raw ml pairs in words 16..31,
+// then the 32 rows of v and their bit-slices); the OR stack, 3 x (levels 0..5 - LOG2_SPLIT).
+constexpr int S_X = 0, S_STK = 96, S_WORDS = S_STK + 3 * (6 - static_cast<int>(LOG2_SPLIT));
 
 __device__ __forceinline__ B3 bor(const Seeds& sd, const B3& a, const B3& b, uint32_t j, uint32_t tag, uint32_t req,
                                   uint32_t c3) {
@@ -148,6 +155,32 @@ __device__ __forceinline__ B3 bor(const Seeds& sd, const B3& a, const B3& b, uin
   const uint32_t F1 = philox(j, tag, req, c3, sd.s[1]).x;
   const uint32_t F2 = philox(j, tag, req, c3, sd.s[2]).x;
   return bx(bx(a, b), band(a, b, F0, F1, F2));
+}
+
+// The 32 u16 values of rows 0..31 of a column as 16 words of two (rows past nvalid read 0).
+__device__ __forceinline__ void load_pairs(const uint16_t* p, uint32_t nvalid, uint32_t (&w)[16]) {
+  if (nvalid == 32) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const uint4 q = reinterpret_cast<const uint4*>(p)[v];
+      w[4 * v + 0] = q.x;
+      w[4 * v + 1] = q.y;
+      w[4 * v + 2] = q.z;
+      w[4 * v + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 16; ++v) {
+      const uint32_t r0 = 2 * v, r1 = 2 * v + 1;
+      w[v] = (r0 < nvalid ? static_cast<uint32_t>(p[r0]) : 0u) | ((r1 < nvalid ? static_cast<uint32_t>(p[r1]) : 0u) << 16);
+    }
+  }
+}
+
+// Rows l and l+1 of a column as one word (rows past nvalid read 0).
+__device__ __forceinline__ uint32_t load_pair(const uint16_t* p, uint32_t l, uint32_t nvalid) {
+  if (nvalid == 32) return *reinterpret_cast<const uint32_t*>(p + l);
+  return (l < nvalid ? static_cast<uint32_t>(p[l]) : 0u) | ((l + 1 < nvalid ? static_cast<uint32_t>(p[l + 1]) : 0u) << 16);
 }
 
 // MODE_LIFT (Alg. 3): Lift of ml, ConstLift of dot, v = a ml' - 2^16 dot', BitExtract(v, {31}).
@@ -162,11 +195,15 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
   const uint32_t tid = threadIdx.x;
   auto S = [&](int slot) -> uint32_t& { return sm[slot * CT + tid]; };
   const uint64_t gtid = blockIdx.x * static_cast<uint64_t>(CT) + tid;
-  if (gtid >= static_cast<uint64_t>(P.n_cols) * P.n_blocks) return;
-  uint32_t n = static_cast<uint32_t>(gtid % P.n_cols);
-  const uint32_t blk = static_cast<uint32_t>(gtid / P.n_cols);
+  // all threads of a unit leave together, so the group stays complete for the final shuffles
+  const uint32_t ks = P.p < LOG2_SPLIT ? P.p : LOG2_SPLIT;
+  const uint64_t unit = gtid >> ks;
+  const uint32_t part = static_cast<uint32_t>(gtid & ((1u << ks) - 1u));
+  if (unit >= static_cast<uint64_t>(P.n_cols) * P.n_blocks) return;
+  uint32_t n = static_cast<uint32_t>(unit % P.n_cols);
+  const uint32_t blk = static_cast<uint32_t>(unit / P.n_cols);
   if (P.col_tiles) {
-    // the first (listed tiles x tile_cols) threads of each block row take the listed columns
+    // the first (listed tiles x tile_cols) units of each block row take the listed columns
     const uint32_t active = *P.n_col_list * P.tile_cols;
     if (n >= active) return;
     n = P.col_tiles[n / P.tile_cols] * P.tile_cols + n % P.tile_cols;
@@ -176,50 +213,29 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
   const uint32_t words_per_block = 1u << P.p;
   const uint64_t blk_row = static_cast<uint64_t>(blk) << (5 + P.p);  // local first row of this block
   const uint64_t rem_words = (P.n_rows - blk_row + 31) >> 5;
-  const uint32_t nwords = static_cast<uint32_t>(rem_words < words_per_block ? rem_words : words_per_block);
-  const uint64_t gword0 = (P.row0 + blk_row) >> 5;  // global index of the first word
+  const uint32_t blk_words = static_cast<uint32_t>(rem_words < words_per_block ? rem_words : words_per_block);
+  const uint64_t bword0 = (P.row0 + blk_row) >> 5;  // global index of the block's first word
+  // this thread's part: words [w_begin, w_end) of the block, a level sub_p subtree
+  const uint32_t sub_p = P.p - ks;
+  const uint32_t w_begin = part << sub_p;
+  const uint32_t w_lim = (part + 1) << sub_p;
+  const uint32_t w_end = blk_words < w_lim ? blk_words : w_lim;
+  const uint32_t nwords = w_end > w_begin ? w_end - w_begin : 0u;
+  const uint64_t gword0 = bword0 + w_begin;
 
   uint32_t valid_levels = 0;
   for (uint32_t w = 0; w < nwords; ++w) {
-    const uint64_t lrow = blk_row + 32ull * w;
+    const uint64_t lrow = blk_row + 32ull * (w_begin + w);
     const uint64_t grow = P.row0 + lrow;
     const uint32_t nvalid = static_cast<uint32_t>(P.n_rows - lrow < 32 ? P.n_rows - lrow : 32);
     const uint32_t lane_mask = nvalid == 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-    // ---- load the 32 rows of this word (3 components of ml and of dot) ----
-#pragma unroll
-    for (int j = 0; j < (MODE == MODE_LIFTFREE ? 0 : 3); ++j) {
-      const uint16_t* pm = P.zm[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
-      const uint16_t* pd = P.zc[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
-      if (nvalid == 32) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const uint4 a = reinterpret_cast<const uint4*>(pm)[v];
-          const uint4 b = reinterpret_cast<const uint4*>(pd)[v];
-          S(S_RAWML + 16 * j + 4 * v + 0) = a.x;
-          S(S_RAWML + 16 * j + 4 * v + 1) = a.y;
-          S(S_RAWML + 16 * j + 4 * v + 2) = a.z;
-          S(S_RAWML + 16 * j + 4 * v + 3) = a.w;
-          S(S_RAWDOT + 16 * j + 4 * v + 0) = b.x;
-          S(S_RAWDOT + 16 * j + 4 * v + 1) = b.y;
-          S(S_RAWDOT + 16 * j + 4 * v + 2) = b.z;
-          S(S_RAWDOT + 16 * j + 4 * v + 3) = b.w;
-        }
-      } else {
-        for (int v = 0; v < 16; ++v) {
-          const uint32_t r0 = 2 * v, r1 = 2 * v + 1;
-          const uint32_t m0 = r0 < nvalid ? pm[r0] : 0u, m1 = r1 < nvalid ? pm[r1] : 0u;
-          const uint32_t d0 = r0 < nvalid ? pd[r0] : 0u, d1 = r1 < nvalid ? pd[r1] : 0u;
-          S(S_RAWML + 16 * j + v) = m0 | (m1 << 16);
-          S(S_RAWDOT + 16 * j + v) = d0 | (d1 << 16);
-        }
-      }
-    }
+    const uint64_t coff = static_cast<uint64_t>(n) * P.ldz + lrow;
     B3 msb, b30;
     if constexpr (MODE == MODE_LIFTFREE) {
       // ---- v = a ml - b dot over Z_{2^32}, straight from the loads; bit-slice; MSB ----
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const uint32_t* pm = P.zm32[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+        const uint32_t* pm = P.zm32[j] + coff;
         if (nvalid == 32) {
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
           for (uint32_t l = 0; l < 32; ++l) S(S_X + 32 * j + l) = l < nvalid ? P.thr_a * pm[l] : 0u;
         }
         if (P.zc32[0]) {  // NoLift: dot components over Z_{2^32}, times b
-          const uint32_t* pd = P.zc32[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
+          const uint32_t* pd = P.zc32[j] + coff;
           if (nvalid == 32) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
@@ -247,20 +263,12 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
             for (uint32_t l = 0; l < nvalid; ++l) S(S_X + 32 * j + l) -= P.thr_b * pd[l];
           }
         } else {  // ConstLift: each Z_{2^16} component read as an integer, times 2^16
-          const uint16_t* pd = P.zc[j] + static_cast<uint64_t>(n) * P.ldz + lrow;
-          if (nvalid == 32) {
+          uint32_t d[16];
+          load_pairs(P.zc[j] + coff, nvalid, d);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const uint4 d = reinterpret_cast<const uint4*>(pd)[v];
-              const uint32_t w[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                S(S_X + 32 * j + 8 * v + 2 * e) -= w[e] << 16;
-                S(S_X + 32 * j + 8 * v + 2 * e + 1) -= w[e] & 0xFFFF0000u;
-              }
-            }
-          } else {
-            for (uint32_t l = 0; l < nvalid; ++l) S(S_X + 32 * j + l) -= static_cast<uint32_t>(pd[l]) << 16;
+          for (int v = 0; v < 16; ++v) {
+            S(S_X + 32 * j + 2 * v) -= d[v] << 16;
+            S(S_X + 32 * j + 2 * v + 1) -= d[v] & 0xFFFF0000u;
           }
         }
       }
@@ -278,22 +286,19 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
                                  b30);
     } else if constexpr (MODE == MODE_PLAIN) {
       // ---- v = t - dot, t = floor(a ml / 2^16) public (component 0); bit-slice; MSB of 16 bits ----
-      for (uint32_t l = 0; l < 32; ++l) {
-        const uint32_t mlw = S(S_RAWML + (l >> 1));
-        const uint32_t ml = (mlw >> (16 * (l & 1))) & 0xFFFFu;
-        const uint32_t t = (P.thr_a * ml) >> 16;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const uint32_t dw = S(S_RAWDOT + 16 * j + (l >> 1));
-          const uint32_t dt = (dw >> (16 * (l & 1))) & 0xFFFFu;
-          S(S_X + 32 * j + l) = ((j == 0 ? t : 0u) - dt) & 0xFFFFu;
-        }
-      }
+      uint32_t mlw[16];
+      load_pairs(P.zm[0] + coff, nvalid, mlw);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
+        uint32_t dw[16];
+        load_pairs(P.zc[j] + coff, nvalid, dw);
         uint32_t a[32];
 #pragma unroll
-        for (int v = 0; v < 32; ++v) a[v] = S(S_X + 32 * j + v);
+        for (int l = 0; l < 32; ++l) {
+          const uint32_t ml = (mlw[l >> 1] >> (16 * (l & 1))) & 0xFFFFu;
+          const uint32_t dt = (dw[l >> 1] >> (16 * (l & 1))) & 0xFFFFu;
+          a[l] = ((j == 0 ? (P.thr_a * ml) >> 16 : 0u) - dt) & 0xFFFFu;
+        }
         transpose32(a);
 #pragma unroll
         for (int v = 0; v < 16; ++v) S(S_X + 32 * j + v) = a[v];
@@ -301,59 +306,82 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
       GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
       bit_extract<15, 0>(P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return S(S_X + 32 * j + b); }, msb, b30);
     } else {
-      // ---- ShareSplit of ml: bit-slice each component (bits 0..15) ----
+      // ---- ShareSplit of ml: bit-slice each component (bits 0..15); keep its raw pairs ----
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
+        uint32_t raw[16];
+        load_pairs(P.zm[j] + coff, nvalid, raw);
         uint32_t a[32];
 #pragma unroll
         for (int v = 0; v < 16; ++v) {
-          const uint32_t x = S(S_RAWML + 16 * j + v);
-          a[2 * v] = x & 0xFFFFu;
-          a[2 * v + 1] = x >> 16;
+          S(S_X + 32 * j + 16 + v) = raw[v];
+          a[2 * v] = raw[v] & 0xFFFFu;
+          a[2 * v + 1] = raw[v] >> 16;
         }
         transpose32(a);
 #pragma unroll
-        for (int b = 0; b < 16; ++b) S(S_X + 16 * j + b) = a[b];
+        for (int b = 0; b < 16; ++b) S(S_X + 32 * j + b) = a[b];
       }
+      // the dot is read from global one row pair ahead of its use
+      const uint16_t* pd[3] = {P.zc[0] + coff, P.zc[1] + coff, P.zc[2] + coff};
+      uint32_t dnext[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dnext[j] = load_pair(pd[j], 0u, nvalid);
       GateRng fa{static_cast<uint32_t>(grow >> 5), tag, req, {}}, rc{static_cast<uint32_t>(grow >> 5), tag, req, {}};
       B3 r17, r16;
       bit_extract<17, LIFT_GATE0>(
-          P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return b < 16 ? S(S_X + 16 * j + b) : 0u; }, r17, r16);
+          P.seeds, fa, rc, [&](int j, int b) -> uint32_t { return b < 16 ? S(S_X + 32 * j + b) : 0u; }, r17, r16);
       // ---- per comparison: BitInject (3-party OT), ConstLift, v = a*ml' - 2^16*dot ----
+      // Row pair (l, l+1) reads raw ml word 16 + l/2 of each component before writing v to
+      // words l and l+1; those overwrite raw words l-16 and l-15 <= l/2 only once they are read.
       uint4 q0w = make_uint4(0u, 0u, 0u, 0u);  // D_INJ0 words: one Philox call per 4 rows
-      for (uint32_t l = 0; l < 32; ++l) {
-        const uint64_t g = grow + l;
-        if ((l & 3u) == 0) q0w = philox(static_cast<uint32_t>(g >> 2), tag, req, IPC_D_INJ0 << 24, P.seeds.s[0]);
-        const uint32_t inj0 = word_of(q0w, l & 3u);
-        const uint4 w2 = philox(static_cast<uint32_t>(g), tag, req, IPC_D_INJ2 << 24, P.seeds.s[2]);
-        uint32_t A[3], Bv[3];
-#pragma unroll
-        for (int which = 0; which < 2; ++which) {
-          const uint32_t k = which == 0 ? 15u : 16u;
-          const uint32_t mask = (1u << k) - 1u;
-          const uint32_t sh = which == 0 ? 0u : 16u;
-          const B3& bit = which == 0 ? r17 : r16;
-          const uint32_t x0 = (bit.c0 >> l) & 1u, x1 = (bit.c1 >> l) & 1u, x2 = (bit.c2 >> l) & 1u;
-          const uint32_t c0 = (inj0 >> sh) & mask, c2 = (w2.x >> sh) & mask;
-          const uint32_t w0 = (w2.y >> sh) & mask, w1 = (w2.z >> sh) & mask;
-          // party 0 (OT sender): m_beta = (beta ^ x_0 ^ x_2) - c_0 - c_2, masked k_beta = w_beta ^ m_beta
-          const uint32_t m0 = ((0u ^ x0 ^ x2) - c0 - c2) & mask;
-          const uint32_t m1 = ((1u ^ x0 ^ x2) - c0 - c2) & mask;
-          const uint32_t k0 = w0 ^ m0, k1 = w1 ^ m1;
-          // party 2 (helper) sends w_{x_1}; party 1 (receiver) unmasks k_{x_1}
-          const uint32_t wsel = x1 ? w1 : w0;
-          const uint32_t c1 = (wsel ^ (x1 ? k1 : k0)) & mask;
-          uint32_t* out = which == 0 ? A : Bv;
-          out[0] = c0;
-          out[1] = c1;
-          out[2] = c2;
-        }
+#pragma unroll 1
+      for (uint32_t l = 0; l < 32; l += 2) {
+        uint32_t dcur[3], mlw[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-          const uint32_t mlw = S(S_RAWML + 16 * j + (l >> 1)), dw = S(S_RAWDOT + 16 * j + (l >> 1));
-          const uint32_t ml = (mlw >> (16 * (l & 1))) & 0xFFFFu, dt = (dw >> (16 * (l & 1))) & 0xFFFFu;
-          const uint32_t mll = ml - (A[j] << 17) - (Bv[j] << 16);
-          S(S_X + 32 * j + l) = P.thr_a * mll - (dt << 16);
+          dcur[j] = dnext[j];
+          mlw[j] = S(S_X + 32 * j + 16 + (l >> 1));
+        }
+        if (l + 2 < 32) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dnext[j] = load_pair(pd[j], l + 2, nvalid);
+        }
+#pragma unroll
+        for (uint32_t e = 0; e < 2; ++e) {
+          const uint32_t r = l + e;
+          const uint64_t g = grow + r;
+          if ((r & 3u) == 0) q0w = philox(static_cast<uint32_t>(g >> 2), tag, req, IPC_D_INJ0 << 24, P.seeds.s[0]);
+          const uint32_t inj0 = word_of(q0w, r & 3u);
+          const uint4 w2 = philox(static_cast<uint32_t>(g), tag, req, IPC_D_INJ2 << 24, P.seeds.s[2]);
+          uint32_t A[3], Bv[3];
+#pragma unroll
+          for (int which = 0; which < 2; ++which) {
+            const uint32_t k = which == 0 ? 15u : 16u;
+            const uint32_t mask = (1u << k) - 1u;
+            const uint32_t sh = which == 0 ? 0u : 16u;
+            const B3& bit = which == 0 ? r17 : r16;
+            const uint32_t x0 = (bit.c0 >> r) & 1u, x1 = (bit.c1 >> r) & 1u, x2 = (bit.c2 >> r) & 1u;
+            const uint32_t c0 = (inj0 >> sh) & mask, c2 = (w2.x >> sh) & mask;
+            const uint32_t w0 = (w2.y >> sh) & mask, w1 = (w2.z >> sh) & mask;
+            // party 0 (OT sender): m_beta = (beta ^ x_0 ^ x_2) - c_0 - c_2, masked k_beta = w_beta ^ m_beta
+            const uint32_t m0 = ((0u ^ x0 ^ x2) - c0 - c2) & mask;
+            const uint32_t m1 = ((1u ^ x0 ^ x2) - c0 - c2) & mask;
+            const uint32_t k0 = w0 ^ m0, k1 = w1 ^ m1;
+            // party 2 (helper) sends w_{x_1}; party 1 (receiver) unmasks k_{x_1}
+            const uint32_t wsel = x1 ? w1 : w0;
+            const uint32_t c1 = (wsel ^ (x1 ? k1 : k0)) & mask;
+            uint32_t* out = which == 0 ? A : Bv;
+            out[0] = c0;
+            out[1] = c1;
+            out[2] = c2;
+          }
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const uint32_t ml = (mlw[j] >> (16 * e)) & 0xFFFFu, dt = (dcur[j] >> (16 * e)) & 0xFFFFu;
+            const uint32_t mll = ml - (A[j] << 17) - (Bv[j] << 16);
+            S(S_X + 32 * j + r) = P.thr_a * mll - (dt << 16);
+          }
         }
       }
       // ---- MSB: bit-slice v and BitExtract(v, {31}) ----
@@ -389,11 +417,11 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
         P.msb_out[2 * plane + at] = (msb.c2 >> l) & 1u;
       }
     }
-    // ---- OR tree inside the aligned block (binary counter over word indices) ----
+    // ---- OR tree inside this part (binary counter over word indices) ----
     B3 cur = msb;
     uint64_t idx = gword0 + w;
     uint32_t lvl = 0;
-    while (lvl < P.p && (idx & 1u) && (valid_levels >> lvl & 1u)) {
+    while (lvl < sub_p && (idx & 1u) && (valid_levels >> lvl & 1u)) {
       const B3 left = {S(S_STK + 3 * lvl), S(S_STK + 3 * lvl + 1), S(S_STK + 3 * lvl + 2)};
       cur = bor(P.seeds, left, cur, static_cast<uint32_t>(idx >> 1), tag, req,
                 (IPC_D_OR << 24) | (1u << 16) | (lvl + 1));
@@ -406,14 +434,14 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
     S(S_STK + 3 * lvl + 2) = cur.c2;
     valid_levels |= 1u << lvl;
   }
-  // ---- block root: a full block ends at level p; a ragged block is flushed upwards ----
+  // ---- root of this part: a full part ends at level sub_p; a ragged one is flushed upwards ----
   B3 root = {0u, 0u, 0u};
-  if (valid_levels >> P.p & 1u) {
-    root = {S(S_STK + 3 * P.p), S(S_STK + 3 * P.p + 1), S(S_STK + 3 * P.p + 2)};
+  if (valid_levels >> sub_p & 1u) {
+    root = {S(S_STK + 3 * sub_p), S(S_STK + 3 * sub_p + 1), S(S_STK + 3 * sub_p + 2)};
   } else {
     bool have = false;
     uint64_t idx = 0;
-    for (uint32_t lvl = 0; lvl < P.p; ++lvl) {
+    for (uint32_t lvl = 0; lvl < sub_p; ++lvl) {
       if (have) {
         if (valid_levels >> lvl & 1u) {
           const B3 left = {S(S_STK + 3 * lvl), S(S_STK + 3 * lvl + 1), S(S_STK + 3 * lvl + 2)};
@@ -423,7 +451,7 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
         idx >>= 1;
       } else if (valid_levels >> lvl & 1u) {
         root = {S(S_STK + 3 * lvl), S(S_STK + 3 * lvl + 1), S(S_STK + 3 * lvl + 2)};
-        // index of this entry at level lvl: its words start after the higher entries of the block
+        // index of this entry at level lvl: its words start after the higher entries of the part
         const uint64_t cnt = nwords;
         const uint64_t start = gword0 + (cnt & ~((2ull << lvl) - 1ull));
         idx = start >> lvl;
@@ -432,6 +460,26 @@ __global__ void __launch_bounds__(CT) compare_kernel(const CmpParams P) {
       }
     }
   }
+  // ---- join the parts: at step s, part t (t a multiple of 2^s) is the left child and part
+  // t + 2^(s-1) the right child of the level sub_p + s node; a part without words is carried
+  // (words fill the parts from the first, so a right child with words has a left one). ----
+  const uint32_t group_mask = ((1u << (1u << ks)) - 1u) << (tid & (32u - (1u << ks)));
+  uint32_t has = nwords > 0 ? 1u : 0u;
+  for (uint32_t s = 1; s <= ks; ++s) {
+    const uint32_t d = 1u << (s - 1);
+    B3 right;
+    right.c0 = __shfl_xor_sync(group_mask, root.c0, d);
+    right.c1 = __shfl_xor_sync(group_mask, root.c1, d);
+    right.c2 = __shfl_xor_sync(group_mask, root.c2, d);
+    const uint32_t right_has = __shfl_xor_sync(group_mask, has, d);
+    if ((part & ((2u << (s - 1)) - 1u)) == 0 && right_has) {
+      const uint32_t lvl = sub_p + s;
+      root = bor(P.seeds, root, right, static_cast<uint32_t>((bword0 >> lvl) + (part >> s)), tag, req,
+                 (IPC_D_OR << 24) | (1u << 16) | lvl);
+    }
+    has |= right_has;
+  }
+  if (part != 0) return;
   const uint64_t bglob = (P.row0 >> (5 + P.p)) + blk;
   const uint64_t plane = static_cast<uint64_t>(P.n_cols) * P.ld_roots;
   const uint64_t at = static_cast<uint64_t>(n) * P.ld_roots + bglob;
@@ -502,8 +550,12 @@ __global__ void or_queries_kernel(const uint32_t* roots, uint64_t ld_roots, uint
 }
 
 int launch_compare(CmpParams& P, int mode, cudaStream_t st) {
+  if (P.p > 5) {  // a part's OR stack holds levels 0..5 - LOG2_SPLIT
+    set_error("compare: log2_block_words must be <= 5");
+    return IPC_EINVAL;
+  }
   P.n_blocks = static_cast<uint32_t>((P.n_rows + (32ull << P.p) - 1) >> (5 + P.p));
-  const uint64_t threads = static_cast<uint64_t>(P.n_cols) * P.n_blocks;
+  const uint64_t threads = (static_cast<uint64_t>(P.n_cols) * P.n_blocks) << (P.p < LOG2_SPLIT ? P.p : LOG2_SPLIT);
   const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
