@@ -195,6 +195,66 @@ def test_compare_and_or_tree_match_oracle_shares(small, torch):
     assert (oracle.reconstruct_bits(small["ref"]["bits"]) == small["match"]).all()
 
 
+def test_compare_multiblock_ragged_matches_oracle(torch):
+    """The comparison kernel over several full OR blocks and a ragged last one. With
+    1,024-row blocks, eight threads take four words each: the last block's parts hold
+    4, 4, 4, 4, 4, 2 (the second ragged), 0 and 0 words. Block sizes of 8 and 2 words
+    split down to single words. MSB shares are compared with the oracle at a row offset
+    (global PRF counters), and opened-query bit shares with the oracle's OR tree from row 0."""
+    ipc = lib()
+    Q, R = 1, 31
+    N, s = Q * R, 2 * 1024 + 21 * 32 + 9
+    ldz = (s + 7) // 8 * 8
+    rng = np.random.default_rng(2729)
+    ml = rng.integers(0, 12801, size=(N, s))
+    dot = rng.integers(-(ml // 8), ml // 8 + 1)  # hd / ml near 1/2: no match
+    dot[7, 1100:1164] = ml[7, 1100:1164]  # identical codes: matches in one block of rotation 7
+
+    def share(v):
+        c0 = rng.integers(0, 65536, size=v.shape)
+        c1 = rng.integers(0, 65536, size=v.shape)
+        return np.stack([c0, c1, (v - c0 - c1) & 0xFFFF]).astype(np.uint16)
+
+    zc_h, zm_h = share(dot), share(ml)
+    zc = torch.zeros((3, N, ldz), dtype=torch.int16, device="cuda")
+    zm = torch.zeros((3, N, ldz), dtype=torch.int16, device="cuda")
+    zc[:, :, :s] = torch.from_numpy(zc_h.view(np.int16)).cuda()
+    zm[:, :, :s] = torch.from_numpy(zm_h.view(np.int16)).cuda()
+    seeds = (0x5EED0, 0x5EED1, 0x5EED2)
+    tags = torch.from_numpy(tags_for(REQ, Q, R).view(np.int32)).cuda()
+    cfg = oracle.mpc_cfg(seeds, req=REQ)
+
+    def ref_msb(row0):
+        out = np.zeros((3, N, s), np.uint8)
+        for n in range(N):
+            for i in range(s):
+                out[:, n, i] = oracle.mpc_compare(cfg, zc_h[:, n, i], zm_h[:, n, i], 0, n, row0 + i)[0]
+        return out
+
+    for row0 in (65536, 0):
+        want = ref_msb(row0)
+        for p in (5, 3, 1):
+            nb = (s + (32 << p) - 1) >> (5 + p)
+            ld_roots = (row0 >> (5 + p)) + nb
+            roots = torch.zeros((3, N, ld_roots), dtype=torch.int32, device="cuda")
+            msb = torch.zeros((3, N, s), dtype=torch.uint8, device="cuda")
+            ipc.ipc_compare([zc[j] for j in range(3)], [zm[j] for j in range(3)], ldz, N, s, row0, tags, seeds,
+                            16384, p, roots, ld_roots, msb, s)
+            torch.cuda.synchronize()
+            ipc.ipc_status()
+            assert (msb.cpu().numpy() == want).all(), (row0, p)
+            if row0 == 0:
+                bits = torch.zeros((3, Q), dtype=torch.uint8, device="cuda")
+                ipc.ipc_or_finalize(roots, ld_roots, nb, p, Q, R, tags, seeds, bits)
+                torch.cuda.synchronize()
+                ipc.ipc_status()
+                assert (bits.cpu().numpy()[:, 0] == oracle.or_tree(cfg, want, 0)).all(), p
+                assert oracle.reconstruct_bits(bits.cpu().numpy())[0] == 1  # the planted matches
+    # the opened MSBs are the plaintext rule: only the planted rows with ml > 0 match
+    opened = want[0] ^ want[1] ^ want[2]
+    assert opened.sum() == opened[7, 1100:1164].sum() == (ml[7, 1100:1164] > 0).sum()
+
+
 @pytest.mark.parametrize("path", ["i8mma", "i8mix", "i32", "tc"])
 def test_context_end_to_end_small(small, torch, path):
     ipc = lib()
