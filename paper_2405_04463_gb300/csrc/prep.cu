@@ -143,6 +143,71 @@ __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint64_t plane
   }
 }
 
+// A2 with eight consecutive elements of one row n of B_i per thread (l a multiple of 8, so a
+// group never straddles a row or the two halves): one 16-byte store per limb plane for bf16
+// limbs, 8 bytes for int8. The first element's (r, j, c) takes the divisions; the next ones
+// step c, then the rotated column js (mod cols) and the row.
+template <typename T>
+__global__ void prep_query_vec_kernel(const uint16_t* __restrict__ y, uint64_t plane, uint32_t Q, ipc_geom g,
+                                      uint32_t party, T* __restrict__ b_lo, T* __restrict__ b_hi, uint32_t n_pad) {
+  const uint32_t l = g.rows * g.cols * g.cell;
+  const uint32_t groups = (2 * l) / 8;  // per output row
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (tid >= static_cast<uint64_t>(n_pad) * groups) return;
+  const uint32_t n = static_cast<uint32_t>(tid / groups);
+  const uint32_t k0 = static_cast<uint32_t>(tid % groups) * 8;
+  uint32_t val[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  if (n < Q * g.R) {
+    const uint32_t q = n / g.R, rho = n % g.R;
+    const int32_t shift = g.rot_lo + static_cast<int32_t>(rho);
+    const bool sum = k0 < l;  // first half: y_i + y_{i-1}; second half: y_i
+    const uint32_t kk = sum ? k0 : k0 - l;
+    uint32_t c = kk % g.cell;
+    const uint32_t cidx = kk / g.cell;
+    uint32_t j = cidx % g.cols, r = cidx / g.cols;
+    int32_t jsi = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
+    uint32_t js = static_cast<uint32_t>(jsi < 0 ? jsi + static_cast<int32_t>(g.cols) : jsi);
+    const uint32_t prev = (party + 2) % 3;
+    const uint16_t* yi = y + party * plane + static_cast<uint64_t>(q) * l;
+    const uint16_t* yp = y + prev * plane + static_cast<uint64_t>(q) * l;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t src = (r * g.cols + js) * g.cell + c;
+      val[e] = sum ? static_cast<uint32_t>(yi[src]) + yp[src] : yi[src];
+      if (++c == g.cell) {
+        c = 0;
+        if (++js == g.cols) js = 0;
+        if (++j == g.cols) {
+          j = 0;
+          ++r;
+        }
+      }
+    }
+  }
+  int8_t a[8], b[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) limbs(val[e] & 0xFFFFu, a[e], b[e]);
+  if constexpr (sizeof(T) == 1) {
+    uint32_t l2[2] = {0u, 0u}, h2[2] = {0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      l2[e >> 2] |= static_cast<uint32_t>(static_cast<uint8_t>(a[e])) << (8 * (e & 3));
+      h2[e >> 2] |= static_cast<uint32_t>(static_cast<uint8_t>(b[e])) << (8 * (e & 3));
+    }
+    *reinterpret_cast<uint2*>(b_lo + tid * 8) = make_uint2(l2[0], l2[1]);
+    *reinterpret_cast<uint2*>(b_hi + tid * 8) = make_uint2(h2[0], h2[1]);
+  } else {
+    uint32_t l4[4], h4[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      l4[v] = bf16_of(a[2 * v]) | (static_cast<uint32_t>(bf16_of(a[2 * v + 1])) << 16);
+      h4[v] = bf16_of(b[2 * v]) | (static_cast<uint32_t>(bf16_of(b[2 * v + 1])) << 16);
+    }
+    *reinterpret_cast<uint4*>(b_lo + tid * 8) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+    *reinterpret_cast<uint4*>(b_hi + tid * 8) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
+  }
+}
+
 // ---- Galois-ring Shamir sharing (Sec. 4.3.2): GR = Z_{2^16}[X]/(X^2 - X - 1) ----
 // An element c0 + c1 X holds two consecutive code bits 2e, 2e+1; in a share vector its
 // coefficients sit at indices 2e, 2e+1, so share vectors keep the bit layout (and a rotation
@@ -292,8 +357,15 @@ int prep_query_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, const ip
     set_error(std::string(who) + ": component stride shorter than Q * l");
     return IPC_EINVAL;
   }
-  prep_query_kernel<T><<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
-      y, y_plane, Q, *g, party, b_lo, b_hi, n_pad);
+  const uintptr_t align = 8 * sizeof(T) - 1;  // one group's store: 16 bytes (bf16) or 8 (int8)
+  if (l % 8 == 0 && !(reinterpret_cast<uintptr_t>(b_lo) & align) && !(reinterpret_cast<uintptr_t>(b_hi) & align)) {
+    const uint64_t threads = total / 8;
+    prep_query_vec_kernel<T><<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+        y, y_plane, Q, *g, party, b_lo, b_hi, n_pad);
+  } else {
+    prep_query_kernel<T><<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+        y, y_plane, Q, *g, party, b_lo, b_hi, n_pad);
+  }
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
