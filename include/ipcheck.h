@@ -103,6 +103,16 @@ int ipc_encode_share(const uint64_t* code_bits, const uint64_t* mask_bits, uint3
                      uint16_t* mask_sh, void* stream);
 
 /*
+ * A0 of protocol 1 (Sec. 4.3, Alg. 2: the client secret-shares the code but sends the mask in
+ * the clear): the public mask operand. mask_bits: [n][ceil(l/64)] uint64 packed as in
+ * ipc_encode_share; mask_out: [n][l] uint16 with mask_out[r][b] = bit b of row r (0 or 1),
+ * 16-byte aligned. This is the mask[0] input of load_db_shares and submit_queries for a
+ * context with plain_mask set. Errors: IPC_EINVAL if l is 0 or not a multiple of 8, a pointer
+ * is null or mask_out is unaligned.
+ */
+int ipc_encode_plain_mask(const uint64_t* mask_bits, uint32_t n, uint32_t l, uint16_t* mask_out, void* stream);
+
+/*
  * A1 -- resident limb planes. Splits each Z_{2^16} element x into balanced
  * signed bytes lo = (int8)(x & 0xFF), hi = (int8)((x - lo) >> 8) so that
  * x = 256*hi + lo (mod 2^16) (the operand decomposition of Sec. 6.1, here
@@ -448,43 +458,53 @@ typedef struct {
                                in 1..2^16 (0 meaning 2^16) */
 } ipc_config;
 
-/* Creates a context on cfg->device with per-party streams. Ownership of *out
- * passes to the caller (release with ipc_destroy). Errors: IPC_EINVAL for an
- * invalid geometry or path, IPC_ECUDA if the device cannot be used. */
+/* Creates a context on cfg->device: the three MPC parties of Alg. 3 (Sec. 2, App. C: 3-party
+ * replicated sharing, pairwise PRF seeds cfg->seeds), each with its own stream, plus a control
+ * stream on which the comparison phase runs. The geometry is the iris code layout of Sec. 3
+ * (l = 12800 bits, 31 rotations) and thr_a the numerator a of the threshold a/b ~ 1 - 2
+ * MATCH_RATIO (Sec. 5, Lemma 2). Ownership of *out passes to the caller (release with
+ * ipc_destroy). Errors: IPC_EINVAL for an invalid geometry or path, IPC_ECUDA if the device
+ * cannot be used. */
 int ipc_create(const ipc_config* cfg, ipc_ctx** out);
 
-/* Device inputs of load_db_shares and submit_queries (src_is_device != 0) are read on the
- * library's own non-blocking streams, ordered after all work enqueued so far on `stream`
- * (a cudaStream_t; NULL, the default, means the legacy default stream). Set it to the
- * stream on which the caller produces those inputs. */
+/* Stream ordering only (no counterpart in the paper). Device inputs of load_db_shares and
+ * submit_queries (src_is_device != 0) are read on the library's own non-blocking streams,
+ * ordered after all work enqueued so far on `stream` (a cudaStream_t; NULL, the default,
+ * means the legacy default stream). Set it to the stream on which the caller produces those
+ * inputs. */
 int ipc_set_input_stream(ipc_ctx* ctx, void* stream);
 
-/* Appends n_rows database rows. code[j], mask[j]: [n_rows][l] uint16, the j-th
- * additive components (A0 output layout per component); host memory if
- * src_is_device == 0, else device memory. The library copies them into its
- * resident int8 limb planes (A1); the caller keeps ownership. Returns IPC_OK,
- * IPC_ENOMEM when the device cannot hold the rows (nothing is appended). */
+/* Appends n_rows rows to the shared database [[C_DB]], [[M_DB]] of Alg. 3 (Sec. 4.3: the MPC
+ * nodes hold every enrolled code as shares of its masked bitvector, Sec. 4.1.1; Sec. 5 shares
+ * the masks too). code[j], mask[j]: [n_rows][l] uint16, the j-th additive components (A0
+ * output layout per component); host memory if src_is_device == 0, else device memory. The
+ * library copies them into its resident limb planes (A1; the limb decomposition of the dot
+ * products, Sec. 6.1); the caller keeps ownership. Returns IPC_OK, IPC_ENOMEM when the device
+ * cannot hold the rows (nothing is appended). */
 int load_db_shares(ipc_ctx* ctx, const uint16_t* const code[3], const uint16_t* const mask[3], size_t n_rows,
                    int src_is_device);
 /* (load_db_shares returns after the rows are copied: the inputs may be freed on return.) */
 
-/* Submits n_queries unrotated queries, code[j]/mask[j]: [n_queries][l] uint16
- * (host if src_is_device == 0, else device). Non-blocking: the inputs may be
- * reused on return; the request runs on the device against every resident
- * row and all R rotations. *req_id receives the request id (also the PRF
- * request tag). Errors: IPC_EINVAL (0 or > max_queries), IPC_ENOMEM. */
+/* Submits a batch of n_queries new codes, each secret-shared by the capturing client (Sec.
+ * 4.3: the orb shares the code, and under Sec. 5 the mask, to the MPC nodes), for one run of
+ * Alg. 3 per query against every resident row, at each of the R rotations of Sec. 3; several
+ * persons per batch as in the deployed system (Sec. 6.4). code[j]/mask[j]: [n_queries][l]
+ * uint16 unrotated components (host if src_is_device == 0, else device). Non-blocking: the
+ * inputs may be reused on return. *req_id receives the request id (also the PRF request tag).
+ * Errors: IPC_EINVAL (0 or > max_queries), IPC_ENOMEM, IPC_EAGAIN (every request slot of the
+ * context is in use; fetch or release one first). */
 int submit_queries(ipc_ctx* ctx, const uint16_t* const code[3], const uint16_t* const mask[3], size_t n_queries,
                    int src_is_device, uint64_t* req_id);
 
-/* Waits up to timeout_ms (< 0: forever) for request req_id and writes the
- * opened match bit of each query to host bits_out[n_queries] (1 = a database
- * row matched at some rotation, i.e. the query is not unique). The request is
- * released afterwards. Errors: IPC_ETIMEOUT (request kept), IPC_ENOTFOUND,
- * IPC_EINVAL (n_queries mismatch), IPC_EDEVICE. */
+/* Waits up to timeout_ms (< 0: forever) for request req_id and opens each query's shared
+ * result bit, as the output node of Sec. 4.3 does: the XOR of its three boolean components.
+ * Writes host bits_out[n_queries], 1 = a database row matched at some rotation (Alg. 1 returns
+ * true), i.e. the query is not unique. The request is released afterwards. Errors:
+ * IPC_ETIMEOUT (request kept), IPC_ENOTFOUND, IPC_EINVAL (n_queries mismatch), IPC_EDEVICE. */
 int fetch_match_bits(ipc_ctx* ctx, uint64_t req_id, uint8_t* bits_out, size_t n_queries, int timeout_ms);
 
-/* As fetch_match_bits but writes the three boolean components [3][n_queries]
- * (host) without opening them, and keeps the request. */
+/* As fetch_match_bits but writes the three boolean components [3][n_queries] (host) of the
+ * OrTree output of Alg. 3 without opening them (Sec. 4.2, Sec. 4.3), and keeps the request. */
 int fetch_bit_shares(ipc_ctx* ctx, uint64_t req_id, uint8_t* shares_out, size_t n_queries, int timeout_ms);
 
 /*
@@ -499,29 +519,33 @@ int fetch_bit_shares(ipc_ctx* ctx, uint64_t req_id, uint8_t* shares_out, size_t 
  */
 int fetch_transcript_hash(ipc_ctx* ctx, uint64_t req_id, uint64_t* hash_out, int timeout_ms);
 
-/* Debug: reconstructed code dot (int16, i.e. ml - 2 hd) and mask length ml of
- * query q at rotation rho for database rows [row_begin, row_end), host
- * outputs. Needs keep_distances. Waits for the request. Errors: IPC_EINVAL,
- * IPC_ENOTFOUND, IPC_ENOSYS (distances not kept). */
+/* Debug: reconstructed masked dot product <c', C'> = ml - 2 hd (App. B; int16) and mask
+ * length ml (Alg. 1) of query q at rotation rho for database rows [row_begin, row_end), from
+ * the kept A4 messages; host outputs. Needs keep_distances. Waits for the request. Errors:
+ * IPC_EINVAL, IPC_ENOTFOUND, IPC_ENOSYS (distances not kept). */
 int fetch_distances(ipc_ctx* ctx, uint64_t req_id, uint32_t q, uint32_t rho, size_t row_begin, size_t row_end,
                     int16_t* dot, uint16_t* ml);
 
-/* Releases a request that will not be fetched. */
+/* Resource management (no counterpart in the paper): releases a request that will not be
+ * fetched, returning its slot to the context; waits for its device work first. */
 int ipc_release(ipc_ctx* ctx, uint64_t req_id);
 
-/* Number of resident database rows. */
+/* Number of resident database rows: s of Alg. 3. */
 size_t ipc_db_rows(const ipc_ctx* ctx);
 
-/* The context's control stream (cudaStream_t): every request's work is joined into it
- * before its completion event, so events recorded on it before submit_queries and after it
- * bracket the request's device time. Owned by the context. */
+/* Measurement aid (no counterpart in the paper). The context's control stream (cudaStream_t):
+ * every request's work is joined into it before its completion event, so events recorded on
+ * it before submit_queries and after it bracket the request's device time. Owned by the
+ * context. */
 void* ipc_ctx_stream(const ipc_ctx* ctx);
 
-/* Frees every device and host resource of the context. */
+/* Resource management (no counterpart in the paper): frees every device and host resource
+ * of the context, after its device work has finished. */
 void ipc_destroy(ipc_ctx* ctx);
 
-/* Text of the last error on this context (or of the last stage-level error
- * of the calling thread when ctx is NULL). Valid until the next call. */
+/* Error reporting (no counterpart in the paper): text of the last error on this context (or
+ * of the last stage-level error of the calling thread when ctx is NULL). Valid until the next
+ * call. */
 const char* ipc_last_error(const ipc_ctx* ctx);
 
 /* ======================================================================== */

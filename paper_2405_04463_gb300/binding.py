@@ -83,6 +83,7 @@ _VP4, _VP8 = _vp * 4, _vp * 8
 
 _SIGS = {
     "ipc_encode_share": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
+    "ipc_encode_plain_mask": [_vp, _u32, _u32, _vp, _vp],
     "ipc_split_limbs": [_vp, _sz, _vp, _vp, _vp],
     "ipc_prep_query": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_split_limbs_bf16": [_vp, _sz, _vp, _vp, _vp],
@@ -187,6 +188,10 @@ def _check(rc: int, ctx=None):
 def ipc_encode_share(code_bits, mask_bits, n, l, client_seed, side, idx0, code_sh, mask_sh, stream=None):
     _check(lib.ipc_encode_share(ptr(code_bits), ptr(mask_bits), n, l, client_seed & (2**64 - 1), side, idx0,
                                 ptr(code_sh), ptr(mask_sh), _stream(stream)))
+
+
+def ipc_encode_plain_mask(mask_bits, n, l, mask_out, stream=None):
+    _check(lib.ipc_encode_plain_mask(ptr(mask_bits), n, l, ptr(mask_out), _stream(stream)))
 
 
 def ipc_split_limbs(x, count, lo, hi, stream=None):

@@ -13,6 +13,23 @@ __device__ __forceinline__ void limbs(uint32_t x, int8_t& lo, int8_t& hi) {
   hi = static_cast<int8_t>(((x - static_cast<uint32_t>(l)) & 0xFFFFu) >> 8);
 }
 
+// A0 of protocol 1 (Sec. 4.3, Alg. 2): the client sends the mask in the clear, so the mask
+// operand is the 0/1 element of each mask bit. One thread per (row, 8 consecutive bits), one
+// 16-byte store.
+__global__ void encode_plain_mask_kernel(const uint64_t* __restrict__ mask_bits, uint32_t n, uint32_t l,
+                                         uint16_t* __restrict__ out) {
+  const uint32_t groups = l >> 3;
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (tid >= static_cast<uint64_t>(n) * groups) return;
+  const uint32_t r = static_cast<uint32_t>(tid / groups), b0 = static_cast<uint32_t>(tid % groups) << 3;
+  const uint32_t nw = (l + 63) >> 6;
+  const uint32_t m = static_cast<uint32_t>(mask_bits[static_cast<uint64_t>(r) * nw + (b0 >> 6)] >> (b0 & 63)) & 0xFFu;
+  uint32_t w[4];
+#pragma unroll
+  for (uint32_t e = 0; e < 4; ++e) w[e] = ((m >> (2 * e)) & 1u) | (((m >> (2 * e + 1)) & 1u) << 16);
+  *reinterpret_cast<uint4*>(out + static_cast<uint64_t>(r) * l + b0) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // A0: one thread per (row, 4 consecutive elements); one Philox call per vector covers them.
 __global__ void encode_share_kernel(const uint64_t* __restrict__ code_bits, const uint64_t* __restrict__ mask_bits,
                                     uint32_t n, uint32_t l, uint64_t seed, uint32_t side, uint32_t idx0,
@@ -324,6 +341,21 @@ extern "C" int ipc_encode_share(const uint64_t* code_bits, const uint64_t* mask_
   const uint32_t bs = 256;
   encode_share_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
       code_bits, mask_bits, n, l, client_seed, side, idx0, code_sh, mask_sh);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+
+extern "C" int ipc_encode_plain_mask(const uint64_t* mask_bits, uint32_t n, uint32_t l, uint16_t* mask_out,
+                                     void* stream) {
+  if (l == 0 || l % 8 != 0 || !mask_bits || !mask_out || (reinterpret_cast<uintptr_t>(mask_out) & 15)) {
+    set_error("ipc_encode_plain_mask: l must be a positive multiple of 8, pointers non-null, mask_out 16-byte aligned");
+    return IPC_EINVAL;
+  }
+  if (n == 0) return IPC_OK;
+  const uint64_t threads = static_cast<uint64_t>(n) * (l / 8);
+  const uint32_t bs = 256;
+  encode_plain_mask_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+      mask_bits, n, l, mask_out);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }

@@ -92,13 +92,13 @@ def db_bits_device(w: synth.Workload, row0: int, n: int):
 
 
 def plain_mask_u16(mask_bits, l: int):
-    """Packed mask bits [n][words] (bit k of an iris in word k >> 6, bit k & 63; numpy or device
-    int64) -> device int16 [n][l] of 0/1: the public mask operand of protocol 1."""
+    """Packed mask bits [n][words] (numpy or device int64) -> device int16 [n][l] of 0/1 through
+    ipc_encode_plain_mask: the public mask operand of protocol 1."""
     torch = torch_mod()
     mb = mask_bits if hasattr(mask_bits, "data_ptr") else dev_u64(mask_bits)
-    shifts = torch.arange(64, device=mb.device, dtype=torch.int64)
-    bits = (mb.unsqueeze(-1) >> shifts) & 1
-    return bits.reshape(mb.shape[0], -1)[:, :l].to(torch.int16).contiguous()
+    out = torch.empty((mb.shape[0], l), dtype=torch.int16, device="cuda")
+    lib().ipc_encode_plain_mask(mb, mb.shape[0], l, out)
+    return out
 
 
 def load_workload(ctx, w: synth.Workload, chunk: int = 16384, galois_shares=False, plain_mask=False, lift=None):

@@ -36,6 +36,24 @@ def wl(torch):
     return dict(w=w, dc=dc, dm=dm, qc=qc, qm=qm, match=match, ml=ml, hd=hd)
 
 
+def test_encode_plain_mask_matches_oracle(torch, wl):
+    """ipc_encode_plain_mask gives the public mask operand of Alg. 2: element b of row r is mask
+    bit b, the value the oracle's mask shares reconstruct to (Sec. 4.1.1). Also a code length
+    that ends inside a 64-bit word (l = 136) and a single row."""
+    w = wl["w"]
+    _, om = oracle.encode_share(wl["dc"], wl["dm"], w.l, w.db_share_seed, 0)
+    got = plain_mask_u16(wl["dm"], w.l)
+    torch.cuda.synchronize()
+    assert (u16(got) == oracle.reconstruct_u16(om)).all()
+    rng = np.random.default_rng(0x9A54)
+    bits = rng.integers(0, 2**63, (3, 3), dtype=np.int64).view(np.uint64)
+    for n, l in ((3, 136), (1, 8)):
+        _, om = oracle.encode_share(bits[:n], bits[:n], l, 0x1234, 1)
+        got = plain_mask_u16(bits[:n], l)
+        torch.cuda.synchronize()
+        assert (u16(got) == oracle.reconstruct_u16(om)).all(), (n, l)
+
+
 def _boundary_cases(rng, n):
     """(ml, dot) pairs on and around the threshold 4 dot = ml, plus the extremes."""
     ml = rng.integers(0, 12801, n)

@@ -55,9 +55,14 @@ def test_noalloc_matches_caller_allocated_path_twice():
     ref = ref.cpu().numpy()
     assert ((ref[0] ^ ref[1] ^ ref[2]) & 1).tolist() == [1, 0, 1]
 
-    for _ in range(2):   # two calls in a row share the fixed scratch
+    # two calls in a row share the fixed scratch: the first on the current stream, the second
+    # on an explicit non-default stream
+    side = torch.cuda.Stream()
+    for st in (None, side):
         out = torch.full((3, Q), 7, dtype=torch.uint8, device="cuda")
-        ipc.ipc_compare_or_noalloc(zcs, zms, ldz, Q, R, rows, tags, SEEDS, THR_A, out)
+        if st is not None:
+            st.wait_stream(torch.cuda.current_stream())
+        ipc.ipc_compare_or_noalloc(zcs, zms, ldz, Q, R, rows, tags, SEEDS, THR_A, out, stream=st)
         torch.cuda.synchronize()
         ipc.ipc_status()
         assert (out.cpu().numpy() == ref).all()
