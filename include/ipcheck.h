@@ -57,7 +57,7 @@ extern "C" {
 #define IPC_PATH_I8MMA 0  /* int8 limb GEMM on the tensor cores (mma.sync s8, TMA-fed) */
 #define IPC_PATH_I32 1    /* plain int32 CUDA-core ring GEMM (IMAD) */
 #define IPC_PATH_I8MIX 2  /* int8 limb GEMM split between mma.sync s8 and dp4a in every tile */
-#define IPC_PATH_TC 3     /* the same limbs as bf16 on tcgen05 (TMEM accumulators, exact) */
+#define IPC_PATH_TC 3     /* the same limbs on tcgen05 as fp16 operands (TMEM accumulators, exact) */
 #define IPC_PATH_TCG 4    /* tcgen05, dot products on Galois-ring Shamir shares (Sec. 4.3.2) */
 
 /* PRF domains: high byte of Philox counter word 3. */
@@ -122,13 +122,6 @@ int ipc_encode_plain_mask(const uint64_t* mask_bits, uint32_t n, uint32_t l, uin
 int ipc_split_limbs(const uint16_t* x, size_t count, int8_t* lo, int8_t* hi, void* stream);
 
 /*
- * A1 for IPC_PATH_TC: the same limbs, each written as the bf16 bit pattern of
- * its integer value (exact: |limb| <= 128). lo, hi: count uint16 each.
- * Errors: IPC_EINVAL if count is 0 or a pointer is not 16-byte aligned.
- */
-int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* lo, uint16_t* hi, void* stream);
-
-/*
  * A2 -- query preparation for one party. y: [3][Q][l] uint16, the additive
  * components of one query vector (code or mask), unrotated. For party i and
  * column n = q*R + rho it writes the row
@@ -142,9 +135,10 @@ int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* lo, uint16_t
 int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, int8_t* b_lo,
                    int8_t* b_hi, uint32_t n_pad, void* stream);
 
-/* A2 for IPC_PATH_TC: as ipc_prep_query, limbs written as bf16 bit patterns. */
-int ipc_prep_query_bf16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
-                        uint16_t* b_hi, uint32_t n_pad, void* stream);
+/* A2 for IPC_PATH_TC: as ipc_prep_query, each limb written as the fp16 bit pattern of its
+ * integer value (exact: |limb| <= 128), the operand type of the tcgen05 GEMM. */
+int ipc_prep_query_f16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
+                       uint16_t* b_hi, uint32_t n_pad, void* stream);
 
 /*
  * A0 and A2 for Galois-ring Shamir dot products (Sec. 4.3.2; IPC_PATH_TCG).
@@ -161,8 +155,8 @@ int ipc_encode_share_galois(const uint64_t* code_bits, const uint64_t* mask_bits
                             uint16_t* mask_sh, void* stream);
 
 /*
- * Party p's query operand for Galois-ring shares: B[n][k] (K = l, bf16 limbs as in
- * ipc_prep_query_bf16) holds coefficient k & 1 of lambda_p * y_p[e] for the element e that
+ * Party p's query operand for Galois-ring shares: B[n][k] (K = l, fp16 limbs as in
+ * ipc_prep_query_f16; b_lo, b_hi 16-byte aligned) holds coefficient k & 1 of lambda_p * y_p[e] for the element e that
  * rotation rho = n % R brings to position k / 2, lambda_p the Lagrange coefficient at 0 of
  * party p's point for polynomials of degree <= 2. Then the constant term of the product with
  * party p's database share, summed over elements, is sum_k B[n][k] * x_p[k]: a plain dot
@@ -220,29 +214,21 @@ int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], const int8_t* 
 
 /*
  * A3 on the tcgen05 tensor cores (IPC_PATH_TC): the same ring GEMM and the same
- * z as ipc_ring_gemm, with operands from ipc_split_limbs_bf16 and
- * ipc_prep_query_bf16 (bf16 bit patterns of the int8 limbs; x planes
- * [x_rows][l], b planes [n_pad][2l]). The products run as bf16 MMAs with fp32
- * accumulators in tensor memory; each accumulator is drained and restarts at
- * 1.5 * 2^23 after at most 256 products, so all partial sums stay integers
- * inside [2^23, 2^24], where fp32 addition is exact, and the result is
- * bit-identical to the integer paths.
+ * z as ipc_ring_gemm. The database operand is the same int8 limb planes as the
+ * integer paths (ipc_split_limbs; x planes [x_rows][l], the size of the u16
+ * shares); the query operand comes from ipc_prep_query_f16 (fp16 bit patterns
+ * of the int8 limbs, b planes [n_pad][2l]). Each k-block of the database tile is
+ * widened from int8 to fp16 in shared memory inside the kernel. The products run
+ * as fp16 MMAs with fp32 accumulators in tensor memory; each accumulator is
+ * drained and restarts at 1.5 * 2^23 after at most 256 products, so all partial
+ * sums stay integers inside [2^23, 2^24], where fp32 addition is exact, and the
+ * result is bit-identical to the integer paths.
  * Arguments, alignment rules and errors as ipc_ring_gemm.
  */
-int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+int ipc_ring_gemm_tc(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows,
                      const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
                      const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
                      size_t ldz, uint64_t row0, void* stream);
-
-/*
- * ipc_ring_gemm_tc on CTA pairs (tcgen05 cta_group::2): same arguments, same z, bit for bit.
- * One cluster of two CTAs computes a 256-row x 256-column tile as one M = 256 MMA, each CTA
- * holding its 128 database rows and half of the query columns in its shared memory.
- */
-int ipc_ring_gemm_tc_pair(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
-                          const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
-                          const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
-                          uint16_t* z, size_t ldz, uint64_t row0, void* stream);
 
 /*
  * IPC_PATH_TC with a tile width and an optional list of column tiles (the form the serving
@@ -252,7 +238,7 @@ int ipc_ring_gemm_tc_pair(const uint16_t* const x_lo[2], const uint16_t* const x
  * computed, one CTA per tile. With a list the launch is persistent (one CTA per SM walking the
  * list), so its grid does not depend on the list. Other arguments and errors as ipc_ring_gemm_tc.
  */
-int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2],
+int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const int8_t* const x_lo[2], const int8_t* const x_hi[2],
                            size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols,
                            uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
                            uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
@@ -261,11 +247,11 @@ int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const x_lo[2], co
 /*
  * A3 for Galois-ring Shamir shares (IPC_PATH_TCG): party p's GEMM over its own database
  * share only, K = l: z[n][r] = sum_k B[n][k] x_p[r][k] + r_p(n, r) (mod 2^16), with B from
- * ipc_prep_query_galois and r_p the zero share of ipc_ring_gemm. x_lo, x_hi: bf16 limb planes
- * [x_rows][l] of party p's share. l must be a multiple of 256. tile_cols, col_tiles and
+ * ipc_prep_query_galois and r_p the zero share of ipc_ring_gemm. x_lo, x_hi: int8 limb planes
+ * [x_rows][l] of party p's share (ipc_split_limbs). l must be a multiple of 256. tile_cols, col_tiles and
  * n_col_list as in ipc_ring_gemm_tc_tiles. Other arguments and errors as ipc_ring_gemm_tc.
  */
-int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const uint16_t* x_lo, const uint16_t* x_hi, size_t x_rows,
+int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const int8_t* x_lo, const int8_t* x_hi, size_t x_rows,
                             const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
                             const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
                             uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
@@ -316,35 +302,34 @@ int ipc_encode_share32(const uint64_t* code_bits, const uint64_t* mask_bits, uin
 
 /*
  * A1 over Z_2^32: x = l0 + 2^8 l1 + 2^16 l2 + 2^24 l3 (mod 2^32) with balanced limbs in
- * [-128, 127], written as bf16 bit patterns (exact) to limbs[0..3] ([count] each, 8-byte
- * aligned; x 16-byte aligned).
+ * [-128, 127], written as int8 planes limbs[0..3] ([count] each, 4-byte aligned; x 16-byte
+ * aligned): the resident database keeps the size of its u32 shares.
  */
-int ipc_split_limbs32_bf16(const uint32_t* x, size_t count, uint16_t* const limbs[4], void* stream);
+int ipc_split_limbs32(const uint32_t* x, size_t count, int8_t* const limbs[4], void* stream);
 
 /*
- * A2 over Z_2^32: party's query operand, four bf16 limb planes b[0..3] of [n_pad][K]: with
+ * A2 over Z_2^32: party's query operand, four fp16 limb planes b[0..3] of [n_pad][K] (16-byte
+ * aligned), each limb the fp16 pattern of its integer value: with
  * segments = 2, K = 2l and row n = q R + rho holds [rot(Y_p + Y_{p-1}) | rot(Y_p)] (the ABY3
  * product, as ipc_prep_query); with segments = 1, K = l and rot(Y_p) alone. y: [3][Q][l] uint32
  * components. Rows Q R .. n_pad - 1 are zero.
  */
-int ipc_prep_query32_bf16(const uint32_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint32_t segments,
-                          uint16_t* const b[4], uint32_t n_pad, void* stream);
+int ipc_prep_query32_f16(const uint32_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint32_t segments,
+                         uint16_t* const b[4], uint32_t n_pad, void* stream);
 
 /*
  * A3 over Z_2^32 on tcgen05 (the ring product of ipc_ring_gemm_tc with four limbs: ten limb
  * products, exact): z[n][r] = sum_k X[r][k] B[n][k] + F(seed_own) - F(seed_prev) (mod 2^32),
- * X = [x[0..3] | x[4..7]] (segments = 2; limb planes [x_rows][l] of this party's and the
- * previous party's components) or x[0..3] (segments = 1), B from ipc_prep_query32_bf16. The
- * zero share of row g (global, row0 + r) and column n is word g & 3 of Philox(seed,
- * (g >> 2, col_tags[2n+1], col_tags[2n], IPC_D_ZA32<<24 | vec)). z: [n_cols][ldz] uint32,
- * 16-byte aligned, ldz % 4 == 0. Requires segments * l % 256 == 0, n_pad % 128 == 0,
- * n_cols <= n_pad. pair != 0: CTA pairs (cta_group::2, 256-row tiles), the same z bit for bit.
- * Errors: IPC_EINVAL for bad sizes or unaligned pointers.
+ * X = [x[0..3] | x[4..7]] (segments = 2; int8 limb planes [x_rows][l] of this party's and the
+ * previous party's components, from ipc_split_limbs32) or x[0..3] (segments = 1), B from
+ * ipc_prep_query32_f16. The zero share of row g (global, row0 + r) and column n is word g & 3
+ * of Philox(seed, (g >> 2, col_tags[2n+1], col_tags[2n], IPC_D_ZA32<<24 | vec)). z:
+ * [n_cols][ldz] uint32, 16-byte aligned, ldz % 4 == 0. Requires segments * l % 256 == 0,
+ * n_pad % 128 == 0, n_cols <= n_pad. Errors: IPC_EINVAL for bad sizes or unaligned pointers.
  */
-int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows, const uint16_t* const b[4],
+int ipc_ring_gemm_tc32(uint32_t segments, const int8_t* const x[8], size_t x_rows, const uint16_t* const b[4],
                        uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
-                       uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, uint32_t pair,
-                       void* stream);
+                       uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, void* stream);
 
 /*
  * A5-A7 without Lift (ConstLift and NoLift): ml32: [3] components over Z_2^32 of ml,
@@ -456,6 +441,9 @@ typedef struct {
                                pointer arrays, cast; the others stay uint16. */
   uint32_t thr_b;           /* b of the threshold a/b: 0 or 2^16, or with IPC_LIFT_NONE any value
                                in 1..2^16 (0 meaning 2^16) */
+  uint32_t max_requests;    /* request slots: requests submitted and not yet fetched or released,
+                               at most 64; 0 = 4. Each slot holds every per-request buffer for
+                               max_queries queries, allocated by the first submit_queries. */
 } ipc_config;
 
 /* Creates a context on cfg->device: the three MPC parties of Alg. 3 (Sec. 2, App. C: 3-party

@@ -47,7 +47,8 @@ class ipc_config(ctypes.Structure):
     _fields_ = [("geom", ipc_geom), ("thr_a", ctypes.c_uint32), ("path", ctypes.c_int32),
                 ("db_chunk_rows", ctypes.c_uint32), ("max_queries", ctypes.c_uint32),
                 ("seeds", ctypes.c_uint64 * 3), ("keep_distances", ctypes.c_uint32), ("device", ctypes.c_int32),
-                ("plain_mask", ctypes.c_uint32), ("lift", ctypes.c_uint32), ("thr_b", ctypes.c_uint32)]
+                ("plain_mask", ctypes.c_uint32), ("lift", ctypes.c_uint32), ("thr_b", ctypes.c_uint32),
+                ("max_requests", ctypes.c_uint32)]
 
 
 LIFTS = {"mpc": 0, "const": 1, "none": 2}
@@ -86,22 +87,18 @@ _SIGS = {
     "ipc_encode_plain_mask": [_vp, _u32, _u32, _vp, _vp],
     "ipc_split_limbs": [_vp, _sz, _vp, _vp, _vp],
     "ipc_prep_query": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
-    "ipc_split_limbs_bf16": [_vp, _sz, _vp, _vp, _vp],
     "ipc_encode_share32": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
-    "ipc_split_limbs32_bf16": [_vp, _sz, _VP4, _vp],
-    "ipc_prep_query32_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _u32, _VP4, _u32, _vp],
-    "ipc_ring_gemm_tc32": [_u32, _VP8, _sz, _VP4, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _u32,
-                           _vp],
+    "ipc_split_limbs32": [_vp, _sz, _VP4, _vp],
+    "ipc_prep_query32_f16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _u32, _VP4, _u32, _vp],
+    "ipc_ring_gemm_tc32": [_u32, _VP8, _sz, _VP4, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
     "ipc_compare_liftfree": [_vp, _vp, _VP3, _sz, _u32, _sz, _u64, _vp, _U64x3, _u32, _u32, _u32, _vp, _sz, _vp,
                              _sz, _vp],
     "ipc_encode_share_galois": [_vp, _vp, _u32, _u32, _u64, _u32, _u32, _vp, _vp, _vp],
     "ipc_prep_query_galois": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_ring_gemm_tc_galois": [_u32, _vp, _vp, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
                                 _u64, _vp, _vp, _vp],
-    "ipc_prep_query_bf16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
+    "ipc_prep_query_f16": [_vp, _u32, ctypes.POINTER(ipc_geom), _u32, _vp, _vp, _u32, _vp],
     "ipc_ring_gemm_tc": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
-    "ipc_ring_gemm_tc_pair": [_VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64,
-                              _vp],
     "ipc_ring_gemm_tc_tiles": [_u32, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz,
                                _u64, _vp, _vp, _vp],
     "ipc_ring_gemm": [_int, _VP2, _VP2, _sz, _vp, _vp, _u32, _u32, _u32, _vp, _u64, _u64, _u32, _vp, _sz, _u64, _vp],
@@ -210,13 +207,9 @@ def ipc_ring_gemm(path, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_ta
                              seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
 
 
-def ipc_split_limbs_bf16(x, count, lo, hi, stream=None):
-    _check(lib.ipc_split_limbs_bf16(ptr(x), count, ptr(lo), ptr(hi), _stream(stream)))
-
-
-def ipc_prep_query_bf16(y, Q, geom: ipc_geom, party, b_lo, b_hi, n_pad, stream=None):
-    _check(lib.ipc_prep_query_bf16(ptr(y), Q, ctypes.byref(geom), party, ptr(b_lo), ptr(b_hi), n_pad,
-                                   _stream(stream)))
+def ipc_prep_query_f16(y, Q, geom: ipc_geom, party, b_lo, b_hi, n_pad, stream=None):
+    _check(lib.ipc_prep_query_f16(ptr(y), Q, ctypes.byref(geom), party, ptr(b_lo), ptr(b_hi), n_pad,
+                                  _stream(stream)))
 
 
 def ipc_encode_share32(code_bits, mask_bits, n, l, client_seed, side, idx0, code_sh, mask_sh, stream=None):
@@ -224,21 +217,21 @@ def ipc_encode_share32(code_bits, mask_bits, n, l, client_seed, side, idx0, code
                                   ptr(code_sh), ptr(mask_sh), _stream(stream)))
 
 
-def ipc_split_limbs32_bf16(x, count, limbs, stream=None):
-    _check(lib.ipc_split_limbs32_bf16(ptr(x), count, _VP4(*[ptr(a) for a in limbs]), _stream(stream)))
+def ipc_split_limbs32(x, count, limbs, stream=None):
+    _check(lib.ipc_split_limbs32(ptr(x), count, _VP4(*[ptr(a) for a in limbs]), _stream(stream)))
 
 
-def ipc_prep_query32_bf16(y, Q, geom: ipc_geom, party, segments, b, n_pad, stream=None):
-    _check(lib.ipc_prep_query32_bf16(ptr(y), Q, ctypes.byref(geom), party, segments, _VP4(*[ptr(a) for a in b]),
-                                     n_pad, _stream(stream)))
+def ipc_prep_query32_f16(y, Q, geom: ipc_geom, party, segments, b, n_pad, stream=None):
+    _check(lib.ipc_prep_query32_f16(ptr(y), Q, ctypes.byref(geom), party, segments, _VP4(*[ptr(a) for a in b]),
+                                    n_pad, _stream(stream)))
 
 
 def ipc_ring_gemm_tc32(segments, x, x_rows, b, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz, row0,
-                       pair=False, stream=None):
+                       stream=None):
     xs = list(x) + [None] * (8 - len(x))
     _check(lib.ipc_ring_gemm_tc32(segments, _VP8(*[ptr(a) for a in xs]), x_rows, _VP4(*[ptr(a) for a in b]), n_cols,
                                   n_pad, l, ptr(col_tags), seed_own & (2**64 - 1), seed_prev & (2**64 - 1), vec,
-                                  ptr(z), ldz, row0, 1 if pair else 0, _stream(stream)))
+                                  ptr(z), ldz, row0, _stream(stream)))
 
 
 def ipc_compare_liftfree(z16, z32, ml32, ldz, n_cols, n_rows, row0, col_tags, seeds, thr_a, thr_b,
@@ -271,13 +264,6 @@ def ipc_ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags,
     _check(lib.ipc_ring_gemm_tc(_VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
                                 ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
                                 seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
-
-
-def ipc_ring_gemm_tc_pair(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z,
-                          ldz, row0, stream=None):
-    _check(lib.ipc_ring_gemm_tc_pair(_VP2(*[ptr(a) for a in x_lo]), _VP2(*[ptr(a) for a in x_hi]), x_rows, ptr(b_lo),
-                                     ptr(b_hi), n_cols, n_pad, l, ptr(col_tags), seed_own & (2**64 - 1),
-                                     seed_prev & (2**64 - 1), vec, ptr(z), ldz, row0, _stream(stream)))
 
 
 def ipc_ring_gemm_tc_tiles(tile_cols, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
@@ -338,7 +324,8 @@ def ipc_selftest_bounded_wait(limit_us, stream=None):
 
 def make_config(geom: ipc_geom | None = None, thr_a: int = 16384, path="i8mma", db_chunk_rows: int = 0,
                 max_queries: int = 0, seeds=(0x51EED0, 0x51EED1, 0x51EED2), keep_distances: bool = False,
-                device: int = 0, plain_mask: bool = False, lift="mpc", thr_b: int = 0) -> ipc_config:
+                device: int = 0, plain_mask: bool = False, lift="mpc", thr_b: int = 0,
+                max_requests: int = 0) -> ipc_config:
     c = ipc_config()
     c.geom = geom if geom is not None else iris_geom()
     c.thr_a = thr_a
@@ -352,6 +339,7 @@ def make_config(geom: ipc_geom | None = None, thr_a: int = 16384, path="i8mma", 
     c.plain_mask = 1 if plain_mask else 0
     c.lift = LIFTS.get(lift, lift)
     c.thr_b = thr_b
+    c.max_requests = max_requests
     return c
 
 

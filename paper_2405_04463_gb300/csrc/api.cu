@@ -30,18 +30,14 @@ int compare_launch_liftfree(const uint16_t* const zc16[3], const uint32_t* const
                             const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a, uint32_t thr_b,
                             uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
                             cudaStream_t st);
-int ring_gemm_tc_pair(uint32_t segments, const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
-                      const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
-                      const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z,
-                      size_t ldz, uint64_t row0, cudaStream_t stream);
 int or_finalize_launch(uint32_t* roots, size_t ld_roots, uint32_t n_blocks, uint32_t p, uint32_t Q, uint32_t R,
                        const uint32_t* col_tags, const uint64_t seeds[3], uint8_t* bit_shares, cudaStream_t st);
-int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+int ring_gemm_tc(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream);
-int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* const x_lo[2],
-                         const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
+int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const int8_t* const x_lo[2],
+                         const int8_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
                          uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
                          uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                          const uint32_t* col_tiles, const uint32_t* n_col_list, cudaStream_t stream);
@@ -84,8 +80,9 @@ extern "C" int ipc_ring_gemm(int path, const int8_t* const x_lo[2], const int8_t
 }
 
 namespace {
-int check_gemm_args(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const int8_t* b_lo,
-                    const int8_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
+// b_lo, b_hi: int8 limb planes (mma.sync and int32 paths) or their fp16 patterns (tcgen05).
+int check_gemm_args(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const void* b_lo,
+                    const void* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                     uint32_t vec, const uint16_t* z, size_t ldz, uint64_t row0, const char* who) {
   auto fail = [&](const char* what) { return bad((std::string(who) + ": " + what).c_str()); };
   if (!x_lo || !x_hi || !b_lo || !b_hi || !col_tags || !z) return fail("null pointer");
@@ -119,46 +116,25 @@ extern "C" int ipc_ring_gemm_tiles(int variant, const int8_t* const x_lo[2], con
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
 }
 
-namespace {
-int check_tc_args(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
-                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
-                  uint32_t vec, const uint16_t* z, size_t ldz, uint64_t row0, const char* who) {
-  auto fail = [&](const char* what) { return bad((std::string(who) + ": " + what).c_str()); };
-  if (!x_lo || !x_hi || !b_lo || !b_hi || !col_tags || !z) return fail("null pointer");
-  for (int i = 0; i < 2; ++i)
-    if (!x_lo[i] || !x_hi[i] || !aligned(x_lo[i], 16) || !aligned(x_hi[i], 16))
-      return fail("database planes must be non-null and 16-byte aligned");
-  if (!aligned(b_lo, 16) || !aligned(b_hi, 16) || !aligned(z, 16)) return fail("unaligned operand");
-  if (l == 0 || l % 128 != 0 || l > 16384) return fail("l must be a multiple of 128, at most 16384");
-  if (ldz % 8 != 0 || ldz < x_rows) return fail("ldz must be a multiple of 8 and >= x_rows");
-  if (n_pad < n_cols || n_pad % 128 != 0) return fail("n_pad must be >= n_cols and a multiple of 128");
-  if (row0 % 8 != 0) return fail("row0 must be a multiple of 8");
-  if (vec > 1) return fail("vec is 0 (code) or 1 (mask)");
-  if (x_rows > IPC_MAX_GEMM_ROWS) return fail("too many rows in one call");
-  return IPC_OK;
-}
-}  // namespace
-
-extern "C" int ipc_ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
+extern "C" int ipc_ring_gemm_tc(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows,
                                 const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
                                 uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
                                 uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, void* stream) {
-  int rc = check_tc_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
-                         "ipc_ring_gemm_tc");
+  int rc = check_gemm_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                           "ipc_ring_gemm_tc");
   if (rc) return rc;
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
   return ring_gemm_tc(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz,
                       row0, as_stream(stream));
 }
 
-extern "C" int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const x_lo[2],
-                                      const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
-                                      const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l,
-                                      const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
-                                      uint16_t* z, size_t ldz, uint64_t row0, const uint32_t* col_tiles,
-                                      const uint32_t* n_col_list, void* stream) {
-  int rc = check_tc_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
-                         "ipc_ring_gemm_tc_tiles");
+extern "C" int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const int8_t* const x_lo[2], const int8_t* const x_hi[2],
+                                      size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols,
+                                      uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
+                                      uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
+                                      const uint32_t* col_tiles, const uint32_t* n_col_list, void* stream) {
+  int rc = check_gemm_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                           "ipc_ring_gemm_tc_tiles");
   if (rc) return rc;
   if (tile_cols != 128 && tile_cols != 256) return bad("ipc_ring_gemm_tc_tiles: tile_cols must be 128 or 256");
   if ((col_tiles == nullptr) != (n_col_list == nullptr))
@@ -168,15 +144,15 @@ extern "C" int ipc_ring_gemm_tc_tiles(uint32_t tile_cols, const uint16_t* const 
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
 }
 
-extern "C" int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const uint16_t* x_lo, const uint16_t* x_hi, size_t x_rows,
+extern "C" int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const int8_t* x_lo, const int8_t* x_hi, size_t x_rows,
                                        const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
                                        uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
                                        uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                                        const uint32_t* col_tiles, const uint32_t* n_col_list, void* stream) {
-  const uint16_t* xl[2] = {x_lo, x_lo};
-  const uint16_t* xh[2] = {x_hi, x_hi};
-  int rc = check_tc_args(xl, xh, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
-                         "ipc_ring_gemm_tc_galois");
+  const int8_t* xl[2] = {x_lo, x_lo};
+  const int8_t* xh[2] = {x_hi, x_hi};
+  int rc = check_gemm_args(xl, xh, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
+                           "ipc_ring_gemm_tc_galois");
   if (rc) return rc;
   if (l % 256 != 0) return bad("ipc_ring_gemm_tc_galois: l must be a multiple of 256");
   if (tile_cols != 128 && tile_cols != 256) return bad("ipc_ring_gemm_tc_galois: tile_cols must be 128 or 256");
@@ -185,18 +161,6 @@ extern "C" int ipc_ring_gemm_tc_galois(uint32_t tile_cols, const uint16_t* x_lo,
   if (x_rows == 0 || n_cols == 0) return IPC_OK;
   return ring_gemm_tc_variant(tile_cols, 1, xl, xh, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own,
                               seed_prev, vec, z, ldz, row0, col_tiles, n_col_list, as_stream(stream));
-}
-
-extern "C" int ipc_ring_gemm_tc_pair(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows,
-                                     const uint16_t* b_lo, const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad,
-                                     uint32_t l, const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev,
-                                     uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0, void* stream) {
-  int rc = check_tc_args(x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, vec, z, ldz, row0,
-                         "ipc_ring_gemm_tc_pair");
-  if (rc != IPC_OK) return rc;
-  if (x_rows == 0 || n_cols == 0) return IPC_OK;
-  return ring_gemm_tc_pair(2, x_lo, x_hi, x_rows, b_lo, b_hi, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec,
-                           z, ldz, row0, as_stream(stream));
 }
 
 extern "C" int ipc_compare(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,

@@ -6,6 +6,12 @@
 //   compare stream     : wait(all three parties), A4-A8 per comparison + in-block OR -> roots
 // then A8 (rest of the OR tree) and the copy of the three bit components to pinned host memory.
 // Queries are prepared once per request on the party streams (A2).
+//
+// Memory: the database chunks are allocated by load_db_shares; every per-request buffer lives in
+// one of max_requests request slots, allocated for max_queries queries by the first
+// submit_queries, so that submitting, fetching and releasing allocate and free nothing (only a
+// database grown since a slot was last used makes that slot's OR-tree roots grow once, and
+// keep_distances requests allocate their kept messages, a test aid).
 #include "context.cuh"
 
 using namespace ipc;
@@ -38,11 +44,8 @@ int cfail(ipc_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 uint8_t* plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb) {
-  return ch.planes + static_cast<size_t>((comp * 2 + vec) * c->nlimb + limb) * ch.cap * c->l * c->esz;
+  return ch.planes + static_cast<size_t>((comp * 2 + vec) * c->nlimb + limb) * ch.cap * c->l;
 }
-
-// The Z_2^32 ring GEMM on one CTA per tile: its CTA-pair form gives the same z in the same time.
-constexpr bool kTc32Pair = false;
 
 // Whether a vector (0 code, 1 mask) is shared over Z_2^32 (lifting variants) rather than Z_2^16.
 bool wide(const ipc_ctx* c, int vec) {
@@ -51,38 +54,20 @@ bool wide(const ipc_ctx* c, int vec) {
 
 uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
-// Frees a request's buffers on every early return of submit_queries, after the device has
-// finished whatever was already enqueued on them; keep() hands them to the context instead.
-class RequestGuard {
- public:
-  RequestGuard(ipc_ctx* c, Request* r) : c_(c), r_(r) {}
-  ~RequestGuard();
-  void keep() { r_ = nullptr; }
-
- private:
-  ipc_ctx* c_;
-  Request* r_;
-};
-
-void free_request(ipc_ctx* c, Request& r);
-
-RequestGuard::~RequestGuard() {
-  if (!r_) return;
-  cudaDeviceSynchronize();
-  cudaGetLastError();
-  free_request(c_, *r_);
+size_t total_blocks(const ipc_ctx* c) {
+  return (c->chunks.size() * c->cfg.db_chunk_rows) >> (5 + kLog2BlockWords);
 }
 
-void free_request(ipc_ctx* c, Request& r) {
-  cudaFree(r.bq);
-  cudaFree(r.qstage);
-  cudaFree(r.tags);
-  cudaFree(r.roots);
-  cudaFree(r.shares_dev);
-  cudaFree(r.zkeep);
-  if (r.shares_host) cudaFreeHost(r.shares_host);
-  if (r.done) cudaEventDestroy(r.done);
-  (void)c;
+void free_slot(Slot& s) {
+  cudaFree(s.bq);
+  cudaFree(s.qstage);
+  cudaFree(s.tags);
+  cudaFree(s.roots);
+  cudaFree(s.shares_dev);
+  if (s.tags_host) cudaFreeHost(s.tags_host);
+  if (s.shares_host) cudaFreeHost(s.shares_host);
+  if (s.done) cudaEventDestroy(s.done);
+  s = Slot();
 }
 
 int ensure_zbuf(ipc_ctx* c, uint32_t n_pad) {
@@ -99,6 +84,42 @@ int ensure_zbuf(ipc_ctx* c, uint32_t n_pad) {
   }
   c->zbuf_cols = n_pad;
   return IPC_OK;
+}
+
+// Creates the request slots and the dot-product scratch for max_queries queries (once).
+int ensure_slots(ipc_ctx* c) {
+  if (!c->slots.empty()) return IPC_OK;
+  const uint32_t Qm = c->cfg.max_queries, n_pad = round_up(Qm * c->cfg.geom.R, 128);
+  int rc = ensure_zbuf(c, n_pad);
+  if (rc) return rc;
+  const size_t qes = c->cfg.lift ? 4 : 2;  // bytes per staged query element
+  std::vector<Slot> slots(c->cfg.max_requests);
+  bool ok = true;
+  for (auto& s : slots) {
+    ok = ok && cudaMalloc(&s.bq, 6ull * c->nlimb * n_pad * c->kq * c->qsz) == cudaSuccess &&
+         cudaMalloc(&s.qstage, 2ull * 3 * Qm * c->l * qes) == cudaSuccess &&
+         cudaMalloc(&s.tags, 2ull * n_pad * sizeof(uint32_t)) == cudaSuccess &&
+         cudaMallocHost(&s.tags_host, 2ull * n_pad * sizeof(uint32_t)) == cudaSuccess &&
+         cudaMalloc(&s.shares_dev, 3ull * Qm) == cudaSuccess && cudaMallocHost(&s.shares_host, 3ull * Qm) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    for (auto& s : slots) free_slot(s);
+    return fail(c, IPC_ENOMEM, "cannot allocate " + std::to_string(c->cfg.max_requests) + " request slots for " +
+                                   std::to_string(Qm) + " queries each");
+  }
+  c->slots = std::move(slots);
+  c->n_pad_max = n_pad;
+  return IPC_OK;
+}
+
+// Frees a request's own buffers (kept messages) and returns its slot; its device work is done.
+void release_request(ipc_ctx* c, Request& r) {
+  cudaFree(r.zkeep);
+  r.zkeep = nullptr;
+  if (r.slot >= 0) c->slots[r.slot].busy = false;
+  r.slot = -1;
 }
 
 uint8_t* zslot(ipc_ctx* c, int set, int vec, int party) {
@@ -170,12 +191,14 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
   if (cfg->thr_b > 65536 || (cfg->lift != IPC_LIFT_NONE && cfg->thr_b != 0 && cfg->thr_b != 65536))
     return fail(nullptr, IPC_EINVAL, "ipc_create: thr_b is 2^16 unless lift is IPC_LIFT_NONE (then 1..2^16)");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
+  if (cfg->max_requests > 64) return fail(nullptr, IPC_EINVAL, "ipc_create: max_requests is at most 64");
   ipc_ctx* c = new ipc_ctx();
   c->cfg = *cfg;
   if (c->cfg.db_chunk_rows == 0) c->cfg.db_chunk_rows = 65536;
   if (c->cfg.max_queries == 0) c->cfg.max_queries = 256;
+  if (c->cfg.max_requests == 0) c->cfg.max_requests = 4;
   c->l = static_cast<uint32_t>(l);
-  c->esz = (cfg->path == IPC_PATH_TC || cfg->path == IPC_PATH_TCG) ? 2 : 1;
+  c->qsz = (cfg->path == IPC_PATH_TC || cfg->path == IPC_PATH_TCG) ? 2 : 1;
   c->kq = cfg->path == IPC_PATH_TCG ? c->l : 2 * c->l;
   c->nlimb = cfg->lift ? 4 : 2;
   c->zsz = cfg->lift ? 4 : 2;
@@ -206,7 +229,8 @@ extern "C" void ipc_destroy(ipc_ctx* c) {
   serve_shutdown(c);
   cudaSetDevice(c->cfg.device);
   cudaDeviceSynchronize();
-  for (auto& kv : c->reqs) free_request(c, kv.second);
+  for (auto& kv : c->reqs) release_request(c, kv.second);
+  for (auto& s : c->slots) free_slot(s);
   for (auto& ch : c->chunks) cudaFree(ch.planes);
   cudaFree(c->zbuf);
   cudaFree(c->stage);
@@ -260,7 +284,7 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
     Chunk ch;
     ch.cap = cap;
     ch.row0 = next_row0;
-    if (cudaMalloc(&ch.planes, 6 * c->nlimb * cap * l * c->esz) != cudaSuccess) {
+    if (cudaMalloc(&ch.planes, 6 * c->nlimb * cap * l) != cudaSuccess) {
       cudaGetLastError();
       for (auto& f : fresh) cudaFree(f.planes);
       return fail(c, IPC_ENOMEM, "load_db_shares: device memory exhausted");
@@ -289,19 +313,15 @@ extern "C" int load_db_shares(ipc_ctx* c, const uint16_t* const code[3], const u
         const size_t es = wide(c, vec) ? 4 : 2;  // bytes per input element
         const uint8_t* src = reinterpret_cast<const uint8_t*>(vec == 0 ? code[j] : mask[j]) + done * l * es;
         CTX_TRY(c, cudaMemcpyAsync(c->stage, src, take * l * es, kind, c->sc));
-        uint8_t* lo = plane(c, *ch, j, vec, 0) + ch->rows * l * c->esz;
-        uint8_t* hi = plane(c, *ch, j, vec, 1) + ch->rows * l * c->esz;
         if (es == 4) {
-          uint16_t* out[4];
-          for (int t = 0; t < 4; ++t)
-            out[t] = reinterpret_cast<uint16_t*>(plane(c, *ch, j, vec, t) + ch->rows * l * c->esz);
-          CTX_RC(c, ipc_split_limbs32_bf16(reinterpret_cast<const uint32_t*>(c->stage), take * l, out, c->sc));
-        } else if (c->esz == 2)
-          CTX_RC(c, ipc_split_limbs_bf16(reinterpret_cast<const uint16_t*>(c->stage), take * l, reinterpret_cast<uint16_t*>(lo),
-                                         reinterpret_cast<uint16_t*>(hi), c->sc));
-        else
-          CTX_RC(c, ipc_split_limbs(reinterpret_cast<const uint16_t*>(c->stage), take * l, reinterpret_cast<int8_t*>(lo), reinterpret_cast<int8_t*>(hi),
-                                    c->sc));
+          int8_t* out[4];
+          for (int t = 0; t < 4; ++t) out[t] = reinterpret_cast<int8_t*>(plane(c, *ch, j, vec, t) + ch->rows * l);
+          CTX_RC(c, ipc_split_limbs32(reinterpret_cast<const uint32_t*>(c->stage), take * l, out, c->sc));
+        } else {
+          CTX_RC(c, ipc_split_limbs(reinterpret_cast<const uint16_t*>(c->stage), take * l,
+                                    reinterpret_cast<int8_t*>(plane(c, *ch, j, vec, 0) + ch->rows * l),
+                                    reinterpret_cast<int8_t*>(plane(c, *ch, j, vec, 1) + ch->rows * l), c->sc));
+        }
       }
     ch->rows += take;
     done += take;
@@ -323,91 +343,125 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   for (int j = 0; j < 3; ++j)
     if (!code[j] || (j < mask_parts && !mask[j])) return fail(c, IPC_EINVAL, "submit_queries: null component");
   CTX_TRY(c, cudaSetDevice(c->cfg.device));
+  int rc = ensure_slots(c);
+  if (rc) return rc;
+  int si = -1;
+  for (size_t k = 0; k < c->slots.size(); ++k)
+    if (!c->slots[k].busy) {
+      si = static_cast<int>(k);
+      break;
+    }
+  if (si < 0)
+    return fail(c, IPC_EAGAIN, "submit_queries: all " + std::to_string(c->slots.size()) +
+                                   " request slots are in use; fetch or release a request first");
+  Slot& sl = c->slots[si];
   const ipc_geom& g = c->cfg.geom;
   const uint32_t l = c->l, Q = static_cast<uint32_t>(n_queries), R = g.R, N = Q * R;
   const uint32_t n_pad = round_up(N, 128);
-  int rc = ensure_zbuf(c, n_pad);
-  if (rc) return rc;
-
-  // declared before the request guard, so that an early return synchronises before the host
-  // source of the tag copy goes away
-  std::vector<uint32_t> tags(2ull * N);
+  // the OR-tree roots cover every resident block; they grow only after the database has grown
+  const size_t ld_roots = total_blocks(c), roots_words = 3ull * N * ld_roots;
+  const size_t roots_cap = 3ull * c->n_pad_max * ld_roots;
+  if (sl.roots_words < roots_words) {
+    CTX_TRY(c, cudaEventSynchronize(sl.done));
+    cudaFree(sl.roots);
+    sl.roots = nullptr;
+    sl.roots_words = 0;
+    if (cudaMalloc(&sl.roots, roots_cap * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, IPC_ENOMEM, "submit_queries: not enough device memory for the OR-tree roots");
+    }
+    sl.roots_words = roots_cap;
+  }
   Request r;
+  r.Q = Q;
+  r.N = N;
+  r.n_pad = n_pad;
+  r.ld_roots = ld_roots;
+  if (c->cfg.keep_distances) {
+    r.zkeep_rows = round_up(static_cast<uint32_t>(c->chunks.size() * c->cfg.db_chunk_rows), 8);
+    if (cudaMalloc(&r.zkeep, 2ull * 3 * N * r.zkeep_rows * c->zsz) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, IPC_ENOMEM, "submit_queries: not enough device memory to keep the messages");
+    }
+  }
   {
     std::lock_guard<std::mutex> lock(c->id_mu);
     r.id = c->next_id++;
   }
-  r.Q = Q;
-  r.N = N;
-  r.n_pad = n_pad;
-  const size_t total_blocks = (c->chunks.size() * c->cfg.db_chunk_rows) >> (5 + kLog2BlockWords);
-  r.ld_roots = total_blocks;
-  const size_t qes = c->cfg.lift ? 4 : 2;  // bytes per staged query element
-  bool ok = cudaMalloc(&r.bq, 6ull * c->nlimb * n_pad * c->kq * c->esz) == cudaSuccess &&
-            cudaMalloc(&r.qstage, 2ull * 3 * Q * l * qes) == cudaSuccess &&
-            cudaMalloc(&r.tags, 2ull * N * sizeof(uint32_t)) == cudaSuccess &&
-            cudaMalloc(&r.roots, 3ull * N * r.ld_roots * sizeof(uint32_t)) == cudaSuccess &&
-            cudaMalloc(&r.shares_dev, 3ull * Q) == cudaSuccess &&
-            cudaMallocHost(&r.shares_host, 3ull * Q) == cudaSuccess &&
-            cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) == cudaSuccess;
-  if (ok && c->cfg.keep_distances) {
-    r.zkeep_rows = round_up(static_cast<uint32_t>(c->chunks.size() * c->cfg.db_chunk_rows), 8);
-    ok = cudaMalloc(&r.zkeep, 2ull * 3 * N * r.zkeep_rows * c->zsz) == cudaSuccess;
-  }
-  RequestGuard guard(c, &r);  // from here on every early return frees the request
-  if (!ok) {
+  // From here on the request owns the slot; an error releases it after the device has finished
+  // whatever was enqueued on its buffers.
+  r.slot = si;
+  sl.busy = true;
+  auto abandon = [&](int code) {
+    cudaDeviceSynchronize();
     cudaGetLastError();
-    return fail(c, IPC_ENOMEM, "submit_queries: not enough device memory for the request");
-  }
+    release_request(c, r);
+    return code;
+  };
+#define SUB_TRY(expr)                                     \
+  do {                                                    \
+    cudaError_t e__ = (expr);                             \
+    if (e__ != cudaSuccess) return abandon(cfail(c, e__, #expr)); \
+  } while (0)
+#define SUB_RC(expr)                           \
+  do {                                         \
+    int rc__ = (expr);                         \
+    if (rc__ != IPC_OK) {                      \
+      c->err = ipc::thread_last_error();       \
+      return abandon(rc__);                    \
+    }                                          \
+  } while (0)
+  // The slot's pinned tag buffer may still feed the copy of the request that used it last:
+  // that request's completion event covers the copy.
+  SUB_TRY(cudaEventSynchronize(sl.done));
   // column tags: (request id, q << 5 | rho)
   for (uint32_t q = 0; q < Q; ++q)
     for (uint32_t rho = 0; rho < R; ++rho) {
-      tags[2 * (q * R + rho)] = static_cast<uint32_t>(r.id);
-      tags[2 * (q * R + rho) + 1] = (q << 5) | rho;
+      sl.tags_host[2 * (q * R + rho)] = static_cast<uint32_t>(r.id);
+      sl.tags_host[2 * (q * R + rho) + 1] = (q << 5) | rho;
     }
   if (src_is_device) {
     rc = order_after_input(c);
-    if (rc) return rc;
+    if (rc) return abandon(rc);
   }
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CTX_TRY(c, cudaMemcpyAsync(r.tags, tags.data(), tags.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
-  auto qvec = [&](int vec) { return r.qstage + static_cast<size_t>(vec) * 3 * Q * l * qes; };
+  SUB_TRY(cudaMemcpyAsync(sl.tags, sl.tags_host, 2ull * N * sizeof(uint32_t), cudaMemcpyHostToDevice, c->sc));
+  const size_t qes = c->cfg.lift ? 4 : 2;  // bytes per staged query element
+  auto qvec = [&](int vec) { return sl.qstage + static_cast<size_t>(vec) * 3 * Q * l * qes; };
   for (int vec = 0; vec < 2; ++vec)
     for (int j = 0; j < (vec == 0 ? 3 : mask_parts); ++j) {
       const size_t es = wide(c, vec) ? 4 : 2;
-      CTX_TRY(c, cudaMemcpyAsync(qvec(vec) + static_cast<size_t>(j) * Q * l * es, vec == 0 ? code[j] : mask[j],
-                                 static_cast<size_t>(Q) * l * es, kind, c->sc));
+      SUB_TRY(cudaMemcpyAsync(qvec(vec) + static_cast<size_t>(j) * Q * l * es, vec == 0 ? code[j] : mask[j],
+                              static_cast<size_t>(Q) * l * es, kind, c->sc));
     }
-  CTX_TRY(c, cudaEventRecord(c->ev_setup, c->sc));
-  // the host tags vector dies at return: make the copy complete before that
-  const size_t qplane = static_cast<size_t>(n_pad) * c->kq * c->esz;
-  auto bq = [&](int party, int vec, int limb) { return r.bq + ((party * 2 + vec) * c->nlimb + limb) * qplane; };
+  SUB_TRY(cudaEventRecord(c->ev_setup, c->sc));
+  const size_t qplane = static_cast<size_t>(n_pad) * c->kq * c->qsz;
+  auto bq = [&](int party, int vec, int limb) { return sl.bq + ((party * 2 + vec) * c->nlimb + limb) * qplane; };
+  auto f16p = [](uint8_t* p) { return reinterpret_cast<uint16_t*>(p); };
   for (int i = 0; i < 3; ++i) {
-    CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
+    SUB_TRY(cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
     for (int vec = 0; vec < 2; ++vec) {
       const uint16_t* y = reinterpret_cast<const uint16_t*>(qvec(vec));
       if (wide(c, vec)) {
         uint16_t* b4[4];
-        for (int t = 0; t < 4; ++t) b4[t] = reinterpret_cast<uint16_t*>(bq(i, vec, t));
-        CTX_RC(c, prep_query32(reinterpret_cast<const uint32_t*>(qvec(vec)), static_cast<uint64_t>(Q) * l, Q, &g, i, 2,
-                               b4, n_pad, c->sp[i]));
+        for (int t = 0; t < 4; ++t) b4[t] = f16p(bq(i, vec, t));
+        SUB_RC(prep_query32(reinterpret_cast<const uint32_t*>(qvec(vec)), static_cast<uint64_t>(Q) * l, Q, &g, i, 2,
+                            b4, n_pad, c->sp[i]));
       } else if (plain && vec == 1) {
         // protocol 1: the rotated public query mask, prepared once (party 0's stream runs the ml GEMM)
-        if (i == 0)
-          CTX_RC(c, prep_query_rotate_plain(y, Q, &g, reinterpret_cast<uint16_t*>(bq(0, 1, 0)),
-                                            reinterpret_cast<uint16_t*>(bq(0, 1, 1)), n_pad, c->sp[0]));
+        if (i == 0) SUB_RC(prep_query_rotate_plain(y, Q, &g, f16p(bq(0, 1, 0)), f16p(bq(0, 1, 1)), n_pad, c->sp[0]));
       } else if (c->cfg.path == IPC_PATH_TCG)
-        CTX_RC(c, prep_query_galois_strided(y, static_cast<uint64_t>(Q) * l, Q, &g, i,
-                                            reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
-                                            reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
-      else if (c->esz == 2)
-        CTX_RC(c, ipc_prep_query_bf16(y, Q, &g, i, reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
-                                      reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
+        SUB_RC(prep_query_galois_strided(y, static_cast<uint64_t>(Q) * l, Q, &g, i, f16p(bq(i, vec, 0)),
+                                         f16p(bq(i, vec, 1)), n_pad, c->sp[i]));
+      else if (c->cfg.path == IPC_PATH_TC)
+        SUB_RC(ipc_prep_query_f16(y, Q, &g, i, f16p(bq(i, vec, 0)), f16p(bq(i, vec, 1)), n_pad, c->sp[i]));
       else
-        CTX_RC(c, ipc_prep_query(y, Q, &g, i, reinterpret_cast<int8_t*>(bq(i, vec, 0)),
-                                 reinterpret_cast<int8_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
+        SUB_RC(ipc_prep_query(y, Q, &g, i, reinterpret_cast<int8_t*>(bq(i, vec, 0)),
+                              reinterpret_cast<int8_t*>(bq(i, vec, 1)), n_pad, c->sp[i]));
     }
   }
+  auto i8p = [](const uint8_t* p) { return reinterpret_cast<const int8_t*>(p); };
+  auto cf16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const Chunk& ch = c->chunks[ci];
     if (ch.rows == 0) continue;
@@ -430,57 +484,52 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
     }
     for (int i = 0; i < 3; ++i) {
       const int prev = (i + 2) % 3;
-      CTX_TRY(c, cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
+      SUB_TRY(cudaStreamWaitEvent(c->sp[i], c->ev_cmp[set], 0));
       for (int vec = 0; vec < 2; ++vec) {
         uint16_t* zo = reinterpret_cast<uint16_t*>(vec == 0 ? zc[i] : zm[i]);
         if (wide(c, vec)) {
           // lifting variants: the ring product over Z_2^32, four limbs, K = 2l
-          const uint16_t* x8[8];
+          const int8_t* x8[8];
           const uint16_t* b4[4];
           for (int t = 0; t < 4; ++t) {
-            x8[t] = reinterpret_cast<const uint16_t*>(plane(c, ch, i, vec, t));
-            x8[4 + t] = reinterpret_cast<const uint16_t*>(plane(c, ch, prev, vec, t));
-            b4[t] = reinterpret_cast<const uint16_t*>(bq(i, vec, t));
+            x8[t] = i8p(plane(c, ch, i, vec, t));
+            x8[4 + t] = i8p(plane(c, ch, prev, vec, t));
+            b4[t] = cf16(bq(i, vec, t));
           }
-          CTX_RC(c, ring_gemm_tc32(2, x8, ch.rows, b4, N, n_pad, l, r.tags, c->cfg.seeds[i], c->cfg.seeds[prev],
-                                   static_cast<uint32_t>(vec), reinterpret_cast<uint32_t*>(zo), ldz, ch.row0,
-                                   c->sp[i], kTc32Pair));
+          SUB_RC(ring_gemm_tc32(2, x8, ch.rows, b4, N, n_pad, l, sl.tags, c->cfg.seeds[i], c->cfg.seeds[prev],
+                                static_cast<uint32_t>(vec), reinterpret_cast<uint32_t*>(zo), ldz, ch.row0, c->sp[i]));
         } else if (plain && vec == 1) {
           // protocol 1: ml = <rotated query mask, database mask> in the clear, K = l; equal seeds
           // make the zero share vanish
           if (i != 0) continue;
-          auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
-          const uint16_t* xl[2] = {p16(plane(c, ch, 0, 1, 0)), p16(plane(c, ch, 0, 1, 0))};
-          const uint16_t* xh[2] = {p16(plane(c, ch, 0, 1, 1)), p16(plane(c, ch, 0, 1, 1))};
-          CTX_RC(c, ring_gemm_tc_variant(256, 1, xl, xh, ch.rows, p16(bq(0, 1, 0)), p16(bq(0, 1, 1)), N, n_pad, l,
-                                         r.tags, c->cfg.seeds[0], c->cfg.seeds[0], 1u, zo, ldz, ch.row0, nullptr,
-                                         nullptr, c->sp[0]));
+          const int8_t* xl[2] = {i8p(plane(c, ch, 0, 1, 0)), i8p(plane(c, ch, 0, 1, 0))};
+          const int8_t* xh[2] = {i8p(plane(c, ch, 0, 1, 1)), i8p(plane(c, ch, 0, 1, 1))};
+          SUB_RC(ring_gemm_tc_variant(256, 1, xl, xh, ch.rows, cf16(bq(0, 1, 0)), cf16(bq(0, 1, 1)), N, n_pad, l,
+                                      sl.tags, c->cfg.seeds[0], c->cfg.seeds[0], 1u, zo, ldz, ch.row0, nullptr,
+                                      nullptr, c->sp[0]));
         } else if (c->cfg.path == IPC_PATH_TCG) {
           // Galois-ring Shamir: party i's own share only, K = l
-          auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
-          const uint16_t* xl[2] = {p16(plane(c, ch, i, vec, 0)), p16(plane(c, ch, i, vec, 0))};
-          const uint16_t* xh[2] = {p16(plane(c, ch, i, vec, 1)), p16(plane(c, ch, i, vec, 1))};
-          CTX_RC(c, ring_gemm_tc_variant(256, 1, xl, xh, ch.rows, p16(bq(i, vec, 0)), p16(bq(i, vec, 1)), N, n_pad, l,
-                                         r.tags, c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo,
-                                         ldz, ch.row0, nullptr, nullptr, c->sp[i]));
+          const int8_t* xl[2] = {i8p(plane(c, ch, i, vec, 0)), i8p(plane(c, ch, i, vec, 0))};
+          const int8_t* xh[2] = {i8p(plane(c, ch, i, vec, 1)), i8p(plane(c, ch, i, vec, 1))};
+          SUB_RC(ring_gemm_tc_variant(256, 1, xl, xh, ch.rows, cf16(bq(i, vec, 0)), cf16(bq(i, vec, 1)), N, n_pad, l,
+                                      sl.tags, c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo,
+                                      ldz, ch.row0, nullptr, nullptr, c->sp[i]));
         } else if (c->cfg.path == IPC_PATH_TC) {
-          auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
-          const uint16_t* xl[2] = {p16(plane(c, ch, i, vec, 0)), p16(plane(c, ch, prev, vec, 0))};
-          const uint16_t* xh[2] = {p16(plane(c, ch, i, vec, 1)), p16(plane(c, ch, prev, vec, 1))};
-          CTX_RC(c, ipc_ring_gemm_tc(xl, xh, ch.rows, p16(bq(i, vec, 0)), p16(bq(i, vec, 1)), N, n_pad, l, r.tags,
-                                     c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz,
-                                     ch.row0, c->sp[i]));
+          const int8_t* xl[2] = {i8p(plane(c, ch, i, vec, 0)), i8p(plane(c, ch, prev, vec, 0))};
+          const int8_t* xh[2] = {i8p(plane(c, ch, i, vec, 1)), i8p(plane(c, ch, prev, vec, 1))};
+          SUB_RC(ipc_ring_gemm_tc(xl, xh, ch.rows, cf16(bq(i, vec, 0)), cf16(bq(i, vec, 1)), N, n_pad, l, sl.tags,
+                                  c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz, ch.row0,
+                                  c->sp[i]));
         } else {
-          auto p8 = [](const uint8_t* p) { return reinterpret_cast<const int8_t*>(p); };
-          const int8_t* xl[2] = {p8(plane(c, ch, i, vec, 0)), p8(plane(c, ch, prev, vec, 0))};
-          const int8_t* xh[2] = {p8(plane(c, ch, i, vec, 1)), p8(plane(c, ch, prev, vec, 1))};
-          CTX_RC(c, ipc_ring_gemm(c->cfg.path, xl, xh, ch.rows, p8(bq(i, vec, 0)), p8(bq(i, vec, 1)), N, n_pad, l,
-                                  r.tags, c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz,
-                                  ch.row0, c->sp[i]));
+          const int8_t* xl[2] = {i8p(plane(c, ch, i, vec, 0)), i8p(plane(c, ch, prev, vec, 0))};
+          const int8_t* xh[2] = {i8p(plane(c, ch, i, vec, 1)), i8p(plane(c, ch, prev, vec, 1))};
+          SUB_RC(ipc_ring_gemm(c->cfg.path, xl, xh, ch.rows, i8p(bq(i, vec, 0)), i8p(bq(i, vec, 1)), N, n_pad, l,
+                               sl.tags, c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz,
+                               ch.row0, c->sp[i]));
         }
       }
-      CTX_TRY(c, cudaEventRecord(c->ev_gemm[i][set], c->sp[i]));
-      CTX_TRY(c, cudaStreamWaitEvent(c->sc, c->ev_gemm[i][set], 0));
+      SUB_TRY(cudaEventRecord(c->ev_gemm[i][set], c->sp[i]));
+      SUB_TRY(cudaStreamWaitEvent(c->sc, c->ev_gemm[i][set], 0));
     }
     auto u16p = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
     auto u32p = [](const uint8_t* p) { return reinterpret_cast<const uint32_t*>(p); };
@@ -489,26 +538,26 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
       const uint32_t* zc32[3] = {u32p(zc[0]), u32p(zc[1]), u32p(zc[2])};
       const uint16_t* zc16[3] = {u16p(zc[0]), u16p(zc[1]), u16p(zc[2])};
       const bool nolift = c->cfg.lift == IPC_LIFT_NONE;
-      CTX_RC(c, compare_launch_liftfree(nolift ? nullptr : zc16, nolift ? zc32 : nullptr, ml32, ldz, N, ch.rows,
-                                        ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a, c->cfg.thr_b, kLog2BlockWords,
-                                        r.roots, r.ld_roots, nullptr, 0, c->sc));
+      SUB_RC(compare_launch_liftfree(nolift ? nullptr : zc16, nolift ? zc32 : nullptr, ml32, ldz, N, ch.rows, ch.row0,
+                                     sl.tags, c->cfg.seeds, c->cfg.thr_a, c->cfg.thr_b, kLog2BlockWords, sl.roots,
+                                     r.ld_roots, nullptr, 0, c->sc));
     } else {
       const uint16_t* zcc[3] = {u16p(zc[0]), u16p(zc[1]), u16p(zc[2])};
       const uint16_t* zmc[3] = {u16p(zm[0]), u16p(plain ? zm[0] : zm[1]), u16p(plain ? zm[0] : zm[2])};
-      CTX_RC(c, compare_launch_tiles(zcc, zmc, ldz, N, ch.rows, ch.row0, r.tags, c->cfg.seeds, c->cfg.thr_a,
-                                     kLog2BlockWords, r.roots, r.ld_roots, nullptr, 0, nullptr, nullptr, 0, c->sc,
-                                     nullptr, plain));
+      SUB_RC(compare_launch_tiles(zcc, zmc, ldz, N, ch.rows, ch.row0, sl.tags, c->cfg.seeds, c->cfg.thr_a,
+                                  kLog2BlockWords, sl.roots, r.ld_roots, nullptr, 0, nullptr, nullptr, 0, c->sc,
+                                  nullptr, plain));
     }
-    CTX_TRY(c, cudaEventRecord(c->ev_cmp[set], c->sc));
+    SUB_TRY(cudaEventRecord(c->ev_cmp[set], c->sc));
   }
   const uint32_t n_blocks =
       static_cast<uint32_t>((c->rows + (32ull << kLog2BlockWords) - 1) >> (5 + kLog2BlockWords));
-  CTX_RC(c, ipc_or_finalize(r.roots, r.ld_roots, n_blocks, kLog2BlockWords, Q, R, r.tags, c->cfg.seeds, r.shares_dev,
-                            c->sc));
-  CTX_TRY(c, cudaMemcpyAsync(r.shares_host, r.shares_dev, 3ull * Q, cudaMemcpyDeviceToHost, c->sc));
-  CTX_TRY(c, cudaEventRecord(r.done, c->sc));
-  CTX_TRY(c, cudaEventSynchronize(c->ev_setup));  // the tag vector above is a host temporary
-  guard.keep();
+  SUB_RC(ipc_or_finalize(sl.roots, r.ld_roots, n_blocks, kLog2BlockWords, Q, R, sl.tags, c->cfg.seeds, sl.shares_dev,
+                         c->sc));
+  SUB_TRY(cudaMemcpyAsync(sl.shares_host, sl.shares_dev, 3ull * Q, cudaMemcpyDeviceToHost, c->sc));
+  SUB_TRY(cudaEventRecord(sl.done, c->sc));
+#undef SUB_TRY
+#undef SUB_RC
   c->reqs[r.id] = r;
   *req_id = r.id;
   return IPC_OK;
@@ -523,11 +572,12 @@ extern "C" int fetch_bit_shares(ipc_ctx* c, uint64_t req_id, uint8_t* shares_out
   }
   Request& r = it->second;
   if (n_queries != r.Q) return fail(c, IPC_EINVAL, "n_queries does not match the request");
-  int rc = wait_event(c, r.done, timeout_ms);
+  const Slot& sl = c->slots[r.slot];
+  int rc = wait_event(c, sl.done, timeout_ms);
   if (rc) return rc;
   rc = check_device_status(c);
   if (rc) return rc;
-  std::memcpy(shares_out, r.shares_host, 3ull * r.Q);
+  std::memcpy(shares_out, sl.shares_host, 3ull * r.Q);
   return IPC_OK;
 }
 
@@ -550,7 +600,7 @@ extern "C" int fetch_distances(ipc_ctx* c, uint64_t req_id, uint32_t q, uint32_t
   if (!r.zkeep) return fail(c, IPC_ENOSYS, "fetch_distances needs keep_distances");
   if (q >= r.Q || rho >= c->cfg.geom.R || row_begin > row_end || row_end > c->rows)
     return fail(c, IPC_EINVAL, "fetch_distances: range");
-  int rc = wait_event(c, r.done, -1);
+  int rc = wait_event(c, c->slots[r.slot].done, -1);
   if (rc) return rc;
   const size_t n = static_cast<size_t>(q) * c->cfg.geom.R + rho, cnt = row_end - row_begin;
   std::vector<uint8_t> tmp(cnt * 4);
@@ -622,7 +672,8 @@ extern "C" int fetch_transcript_hash(ipc_ctx* c, uint64_t req_id, uint64_t* hash
   if (it == c->reqs.end()) return fail(c, IPC_ENOTFOUND, "unknown request id");
   Request& r = it->second;
   if (!r.zkeep) return fail(c, IPC_ENOSYS, "fetch_transcript_hash needs keep_distances");
-  int rc = wait_event(c, r.done, timeout_ms);
+  const Slot& sl = c->slots[r.slot];
+  int rc = wait_event(c, sl.done, timeout_ms);
   if (rc) return rc;
   rc = check_device_status(c);
   if (rc) return rc;
@@ -648,7 +699,7 @@ extern "C" int fetch_transcript_hash(ipc_ctx* c, uint64_t req_id, uint64_t* hash
   cudaFree(acc);
   if (e != cudaSuccess) return cfail(c, e, "fetch_transcript_hash");
   for (uint32_t p = 0; p < 3; ++p)
-    for (uint32_t q = 0; q < r.Q; ++q) h ^= msg_hash(2, p, q, 0, r.shares_host[static_cast<size_t>(p) * r.Q + q]);
+    for (uint32_t q = 0; q < r.Q; ++q) h ^= msg_hash(2, p, q, 0, sl.shares_host[static_cast<size_t>(p) * r.Q + q]);
   *hash_out = h;
   return IPC_OK;
 }
@@ -660,8 +711,8 @@ extern "C" int ipc_release(ipc_ctx* c, uint64_t req_id) {
     const int rc = serve_release(c, req_id);
     return rc == IPC_ENOTFOUND ? fail(c, IPC_ENOTFOUND, "unknown request id") : rc;
   }
-  cudaEventSynchronize(it->second.done);
-  free_request(c, it->second);
+  cudaEventSynchronize(c->slots[it->second.slot].done);
+  release_request(c, it->second);
   c->reqs.erase(it);
   return IPC_OK;
 }

@@ -1,10 +1,10 @@
-// A3 on the 5th-generation tensor cores: tcgen05.mma (kind::f16) with bf16 operands carrying the
+// A3 on the 5th-generation tensor cores: tcgen05.mma (kind::f16) with fp16 operands carrying the
 // balanced int8 limbs, fp32 accumulators in tensor memory.
 //
 // The ring product is the same three limb products as the int8 paths (Sec. 6.1):
 //     z = L + 256 C + r  (mod 2^16),  L = sum lo*lo',  C = sum (lo*hi' + hi*lo').
-// sm_103a has no integer tcgen05 kind, but the arithmetic stays exact on the bf16 kind:
-//   * every limb is an integer in [-128, 127], exactly a bf16 value;
+// sm_103a has no integer tcgen05 kind, but the arithmetic stays exact on the f16 kind:
+//   * every limb is an integer in [-128, 127], exactly an fp16 value;
 //   * every product is an integer with |p| <= 2^14, exact in fp32;
 //   * an accumulator starts at M = 1.5 * 2^23 and is drained and reset to M after at most 256
 //     products (C every 128 k: two per k; L every 256 k), so every partial sum, in any order or
@@ -14,10 +14,17 @@
 //     0 mod 2^16, so the raw bits of the two accumulators, added as integers (L + (C << 8)) over
 //     all chunks, give z - r mod 2^16 with no conversion instruction.
 //
-// Pipeline (one CTA per tile of 128 database rows x TN query columns, 10 warps):
-//   warp 0 lane 0  TMA producer: per k-block of 32 elements, four tiles (database lo/hi 128 x 32,
-//                  query lo/hi 256 x 32, 64-byte swizzle) into a 4-stage ring.
-//   warp 1 lane 0  MMA issuer: per chunk of four k-blocks, the C products (2 MMAs of 128x256x16
+// The database stays resident as int8 limb planes (the size of its u16 shares): TMA brings each
+// k-block's raw int8 tiles into shared memory and two widening warps rewrite them as fp16 tiles
+// in the MMA's swizzled layout, next to the query tiles (already fp16, prepared per request).
+//
+// Pipeline (one CTA per tile of 128 database rows x TN query columns, 12 warps):
+//   warp 0 lane 0  TMA producer: per k-block of 32 elements, four tiles (raw database lo/hi
+//                  128 x 32 int8, query lo/hi TN x 32 fp16 with 64-byte swizzle) into a 4-stage
+//                  ring.
+//   warps 10-11    widening: per k-block, once the stage's copies have landed, the two raw
+//                  database tiles become 128 x 32 fp16 tiles in the same stage.
+//   warp 1 lane 0  MMA issuer: per chunk of four k-blocks, the C products (2 MMAs of 128xTNx16
 //                  per 16 k) with the L products (1 MMA per 16 k) one k-block behind, committing
 //                  C-full after the last C k-block, stage-empty after each L k-block, and L-full
 //                  after every second chunk.
@@ -38,32 +45,38 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;          // database rows per tile (MMA M = TMEM lanes)
-constexpr int KB = 32;           // bf16 elements of K per stage: one 64-byte swizzled row
+constexpr int KB = 32;           // elements of K per stage: one 64-byte swizzled fp16 row
 constexpr int STAGES = 4;
 constexpr int KB_PER_CHUNK = 4;  // k-blocks per accumulator chunk (128 k)
 static_assert(KB_PER_CHUNK >= 2, "the L products lag the C products by one k-block");
-constexpr int A_BYTES = TM * KB * 2;  // 8 KiB
-constexpr int THREADS = 10 * 32;
+constexpr int A_BYTES = TM * KB * 2;  // 8 KiB widened (fp16) database tile
+constexpr int A_RAW = TM * KB;        // 4 KiB raw (int8) database tile
+constexpr int THREADS = 12 * 32;
 constexpr int DRAIN_THREADS = 8 * 32;
-// full[S], empty[S], c_full, c_empty, l_full, l_empty, done, epi_done
-constexpr int NUM_BARS = 2 * STAGES + 6;
+constexpr int WIDEN_WARP0 = 10, WIDEN_THREADS = 2 * 32;
+// full[S], empty[S], wide[S], c_full, c_empty, l_full, l_empty, done, epi_done
+constexpr int NUM_BARS = 3 * STAGES + 6;
 constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
 
-// Tile shape: TN query columns per tile (MMA N = 256 or 128).
+// Tile shape: TN query columns per tile (MMA N = 256 or 128). A stage holds, 1024-byte aligned:
+// widened database lo, hi (A_BYTES each), query lo, hi (B_BYTES each), raw database lo, hi.
 template <int TN>
 struct Shape {
   static_assert(TN == 256 || TN == 128, "tile width");
   static constexpr int B_BYTES = TN * KB * 2;
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 48 or 32 KiB
+  static constexpr int RAW_OFF = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGE_BYTES = RAW_OFF + 2 * A_RAW;  // 56 or 40 KiB
+  static_assert(STAGE_BYTES % 1024 == 0, "stage tiles stay 1024-byte aligned");
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NUM_BARS;
+  static_assert(SMEM_BYTES <= 232448, "dynamic shared memory per block");
   static constexpr uint32_t TMEM_COLS = 2 * TN;  // L in [0, TN), C in [TN, 2 TN)
   static constexpr uint32_t TMEM_C = TN;
   static constexpr int DCOLS = TN / 2;       // columns per drain thread (two drain warps per lane quarter)
   static constexpr int GROUPS = DCOLS / 32;  // 32-column TMEM loads per accumulator and drain
-  // Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1), B bf16
-  // (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
-                                    (static_cast<uint32_t>(TM >> 4) << 24);
+  // Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B f16 (bits 7-9, 10-12 = 0),
+  // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (static_cast<uint32_t>(TN >> 3) << 17) | (static_cast<uint32_t>(TM >> 4) << 24);
   // z of one tile, [TN][TM] uint16, staged in the (then idle) stage ring
   static_assert(TN * TM * 2 <= STAGES * STAGE_BYTES, "z tile must fit the stage ring");
 };
@@ -128,8 +141,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t tiles = smem_addr(smem);
   const uint32_t bars = tiles + STAGES * STAGE_BYTES;
-  const uint32_t full0 = bars, empty0 = bars + 8 * STAGES;
-  const uint32_t c_full = bars + 16 * STAGES, c_empty = c_full + 8, l_full = c_full + 16, l_empty = c_full + 24,
+  const uint32_t full0 = bars, empty0 = bars + 8 * STAGES, wide0 = bars + 16 * STAGES;
+  const uint32_t c_full = bars + 24 * STAGES, c_empty = c_full + 8, l_full = c_full + 16, l_empty = c_full + 24,
                  done_bar = c_full + 32, epi_done = c_full + 40;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,6 +152,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
+      mbar_init(wide0 + 8 * s, WIDEN_THREADS / 32);
     }
     mbar_init(c_full, 1);
     mbar_init(c_empty, DRAIN_THREADS / 32);
@@ -176,11 +190,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           const uint32_t full = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
-          mbar_expect_tx(full, STAGE_BYTES);
+          mbar_expect_tx(full, 2 * A_RAW + 2 * B_BYTES);
           const bool first = kb < p.kb_half;
           const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
-          tma_load(base, first ? &ta0_lo : &ta1_lo, kx, static_cast<int32_t>(d0), full);
-          tma_load(base + A_BYTES, first ? &ta0_hi : &ta1_hi, kx, static_cast<int32_t>(d0), full);
+          tma_load(base + S::RAW_OFF, first ? &ta0_lo : &ta1_lo, kx, static_cast<int32_t>(d0), full);
+          tma_load(base + S::RAW_OFF + A_RAW, first ? &ta0_hi : &ta1_hi, kx, static_cast<int32_t>(d0), full);
           tma_load(base + 2 * A_BYTES, &tb_lo, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
           tma_load(base + 2 * A_BYTES + B_BYTES, &tb_hi, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
           issued = G + 1;
@@ -202,7 +216,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       auto issue_c = [&](uint32_t base) {
 #pragma unroll
         for (uint32_t ks = 0; ks < KB / 16; ++ks) {
-          const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
+          const uint32_t o = 32u * ks;  // 16 fp16 = 32 bytes along K inside the swizzled row
           umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o), S::IDESC);  // lo * hi'
           umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o), S::IDESC);  // hi * lo'
         }
@@ -227,7 +241,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (uint32_t kb = 0; kb < KB_PER_CHUNK; ++kb) {
           const uint32_t G = G0 + kb, s = G % STAGES;
-          if (!mbar_wait(full0 + 8 * s, (G / STAGES) & 1u, p.status, abort)) {
+          // the query tiles landed (TMA) and the database tiles were widened
+          if (!mbar_wait(full0 + 8 * s, (G / STAGES) & 1u, p.status, abort) ||
+              !mbar_wait(wide0 + 8 * s, (G / STAGES) & 1u, p.status, abort)) {
             ok = false;
             break;
           }
@@ -250,6 +266,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       // every MMA issued above completes before the tensor memory is freed
       umma_commit(done_bar);
       mbar_wait(done_bar, 0, p.status, nullptr);
+    }
+  } else if (warp >= WIDEN_WARP0) {
+    // ---------------------------------- widening ---------------------------------
+    // Per k-block, after the stage's copies have landed: the raw int8 database tiles become the
+    // fp16 operand tiles of the same stage. The stage's previous MMAs are complete by then (the
+    // producer waited for stage-empty before these copies).
+    const uint32_t ct = threadIdx.x - WIDEN_WARP0 * 32;
+    const uint32_t total = my_items * p.kb_total;
+    for (uint32_t G = 0; G < total; ++G) {
+      const uint32_t s = G % STAGES, base = tiles + s * STAGE_BYTES;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(full0 + 8 * s, (G / STAGES) & 1u, p.status, abort))) break;
+      widen_tiles<2, WIDEN_THREADS>(base + S::RAW_OFF, A_RAW, base, A_BYTES, ct);
+      fence_proxy_async();  // the MMAs read these tiles through the async proxy
+      __syncwarp();
+      if (lane == 0) mbar_arrive(wide0 + 8 * s);
     }
   } else {
     // ----------------------------------- drain ----------------------------------
@@ -370,26 +401,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-int sm_count_tc() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
 template <int TN, bool LIST>
 int launch_tc(const CUtensorMap* m, const TcParams& p, dim3 grid, cudaStream_t stream) {
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(gemm_tc_kernel<TN, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static PerDevice attr;
+  IPC_CUDA_TRY(attr.run([] {
+    return cudaFuncSetAttribute(gemm_tc_kernel<TN, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 Shape<TN>::SMEM_BYTES);
-  });
-  IPC_CUDA_TRY(attr);
+  }));
   gemm_tc_kernel<TN, LIST><<<grid, THREADS, Shape<TN>::SMEM_BYTES, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
@@ -402,8 +420,8 @@ int launch_tc(const CUtensorMap* m, const TcParams& p, dim3 grid, cudaStream_t s
 // per SM; otherwise every tile of [0, n_cols), one CTA each. segments: 2 for K = 2l over the
 // planes [x_lo[0] | x_lo[1]] (replicated sharing), 1 for K = l over x_lo[0] alone (Galois-ring
 // Shamir shares; l a multiple of 256 so that L's 256-k drains tile K).
-int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* const x_lo[2],
-                         const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
+int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const int8_t* const x_lo[2],
+                         const int8_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
                          uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
                          uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                          const uint32_t* col_tiles, const uint32_t* n_col_list, cudaStream_t stream) {
@@ -421,10 +439,10 @@ int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* 
   }
   CUtensorMap m[6];
   int rc;
-  if ((rc = make_map_bf16(&m[0], b_lo, static_cast<uint64_t>(segments) * l, n_pad, tile_cols)) ||
-      (rc = make_map_bf16(&m[1], b_hi, static_cast<uint64_t>(segments) * l, n_pad, tile_cols)) ||
-      (rc = make_map_bf16(&m[2], x_lo[0], l, x_rows, TM)) || (rc = make_map_bf16(&m[3], x_hi[0], l, x_rows, TM)) ||
-      (rc = make_map_bf16(&m[4], x_lo[1], l, x_rows, TM)) || (rc = make_map_bf16(&m[5], x_hi[1], l, x_rows, TM)))
+  if ((rc = make_map_f16(&m[0], b_lo, static_cast<uint64_t>(segments) * l, n_pad, tile_cols)) ||
+      (rc = make_map_f16(&m[1], b_hi, static_cast<uint64_t>(segments) * l, n_pad, tile_cols)) ||
+      (rc = make_map_i8(&m[2], x_lo[0], l, x_rows, TM)) || (rc = make_map_i8(&m[3], x_hi[0], l, x_rows, TM)) ||
+      (rc = make_map_i8(&m[4], x_lo[1], l, x_rows, TM)) || (rc = make_map_i8(&m[5], x_hi[1], l, x_rows, TM)))
     return rc;
   TcParams p;
   p.n_cols = n_cols;
@@ -443,14 +461,14 @@ int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const uint16_t* 
   p.row0 = row0;
   p.status = status_ptr();
   if (col_tiles) {
-    const dim3 grid(static_cast<unsigned>(sm_count_tc()));
+    const dim3 grid(static_cast<unsigned>(sm_count_current()));
     return tile_cols == 256 ? launch_tc<256, true>(m, p, grid, stream) : launch_tc<128, true>(m, p, grid, stream);
   }
   const dim3 grid((n_cols + tile_cols - 1) / tile_cols, p.n_row_tiles);
   return tile_cols == 256 ? launch_tc<256, false>(m, p, grid, stream) : launch_tc<128, false>(m, p, grid, stream);
 }
 
-int ring_gemm_tc(const uint16_t* const x_lo[2], const uint16_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
+int ring_gemm_tc(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,
                  const uint16_t* b_hi, uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags,
                  uint64_t seed_own, uint64_t seed_prev, uint32_t vec, uint16_t* z, size_t ldz, uint64_t row0,
                  cudaStream_t stream) {

@@ -80,9 +80,9 @@ int batch_part(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const 
   const uint32_t n_pad = (N + 127) / 128 * 128;
   const size_t ldz = (P + 7) / 8 * 8;
   const uint32_t nb = (P + 1023) / 1024;  // 1024-row OR blocks
-  const size_t esz = c->esz, kq = c->kq;
-  const size_t plane_bytes = static_cast<size_t>(P) * l * esz;
-  const size_t qplane = static_cast<size_t>(n_pad) * kq * esz;
+  const size_t qsz = c->qsz, kq = c->kq;
+  const size_t plane_bytes = (static_cast<size_t>(P) * l + 15) / 16 * 16;  // int8 limb planes
+  const size_t qplane = static_cast<size_t>(n_pad) * kq * qsz;
   const bool ok = cudaMalloc(&bb.y, 6ull * P * l * sizeof(uint16_t)) == cudaSuccess &&
                   cudaMalloc(&bb.planes, 12 * plane_bytes) == cudaSuccess &&
                   cudaMalloc(&bb.bq, 12 * qplane) == cudaSuccess &&
@@ -119,12 +119,8 @@ int batch_part(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const 
   for (int vec = 0; vec < 2; ++vec)
     for (int j = 0; j < 3; ++j) {
       const uint16_t* x = bb.y + (static_cast<size_t>(vec) * 3 + j) * P * l;
-      if (esz == 2)
-        P_RC(ipc_split_limbs_bf16(x, static_cast<size_t>(P) * l, reinterpret_cast<uint16_t*>(pl(j, vec, 0)),
-                                  reinterpret_cast<uint16_t*>(pl(j, vec, 1)), st));
-      else
-        P_RC(ipc_split_limbs(x, static_cast<size_t>(P) * l, reinterpret_cast<int8_t*>(pl(j, vec, 0)),
-                             reinterpret_cast<int8_t*>(pl(j, vec, 1)), st));
+      P_RC(ipc_split_limbs(x, static_cast<size_t>(P) * l, reinterpret_cast<int8_t*>(pl(j, vec, 0)),
+                           reinterpret_cast<int8_t*>(pl(j, vec, 1)), st));
     }
   // A2 and A3 per party and vector
   uint16_t* zc[3];
@@ -143,16 +139,16 @@ int batch_part(ipc_ctx* c, const uint16_t* const code[3], const uint16_t* const 
       if (c->cfg.path == IPC_PATH_TCG) {
         P_RC(ipc_prep_query_galois(y, P, &g, i, reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
                                    reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, st));
-        const uint16_t* xl[2] = {p16(pl(i, vec, 0)), p16(pl(i, vec, 0))};
-        const uint16_t* xh[2] = {p16(pl(i, vec, 1)), p16(pl(i, vec, 1))};
+        const int8_t* xl[2] = {p8(pl(i, vec, 0)), p8(pl(i, vec, 0))};
+        const int8_t* xh[2] = {p8(pl(i, vec, 1)), p8(pl(i, vec, 1))};
         P_RC(ring_gemm_tc_variant(256, 1, xl, xh, P, p16(bq(i, vec, 0)), p16(bq(i, vec, 1)), N, n_pad, l, bb.tags,
                                   c->cfg.seeds[i], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz, 0,
                                   nullptr, nullptr, st));
       } else if (c->cfg.path == IPC_PATH_TC) {
-        P_RC(ipc_prep_query_bf16(y, P, &g, i, reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
-                                 reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, st));
-        const uint16_t* xl[2] = {p16(pl(i, vec, 0)), p16(pl(prev, vec, 0))};
-        const uint16_t* xh[2] = {p16(pl(i, vec, 1)), p16(pl(prev, vec, 1))};
+        P_RC(ipc_prep_query_f16(y, P, &g, i, reinterpret_cast<uint16_t*>(bq(i, vec, 0)),
+                                reinterpret_cast<uint16_t*>(bq(i, vec, 1)), n_pad, st));
+        const int8_t* xl[2] = {p8(pl(i, vec, 0)), p8(pl(prev, vec, 0))};
+        const int8_t* xh[2] = {p8(pl(i, vec, 1)), p8(pl(prev, vec, 1))};
         P_RC(ipc_ring_gemm_tc(xl, xh, P, p16(bq(i, vec, 0)), p16(bq(i, vec, 1)), N, n_pad, l, bb.tags, c->cfg.seeds[i],
                               c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz, 0, st));
       } else {

@@ -1,4 +1,6 @@
 // A0 (client encoding and sharing), A1 (limb planes) and A2 (query preparation).
+#include <cuda_fp16.h>
+
 #include <string>
 
 #include "common.cuh"
@@ -66,37 +68,9 @@ __global__ void encode_share_kernel(const uint64_t* __restrict__ code_bits, cons
   }
 }
 
-// bf16 bit pattern of a limb (an integer in [-128, 127]: exact in bf16, so the high half of the
-// fp32 value is the bf16 value).
-__device__ __forceinline__ uint16_t bf16_of(int8_t v) {
-  return static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);
-}
-
-// A1 for the bf16 tensor-core path: 8 elements per thread, limbs written as bf16.
-__global__ void split_limbs_bf16_kernel(const uint16_t* __restrict__ x, size_t count, uint16_t* __restrict__ lo,
-                                        uint16_t* __restrict__ hi) {
-  const size_t i8 = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) * 8;
-  if (i8 >= count) return;
-  const size_t n = count - i8 < 8 ? count - i8 : 8;
-  uint16_t l8[8], h8[8];
-  for (size_t e = 0; e < n; ++e) {
-    int8_t a, b;
-    limbs(x[i8 + e], a, b);
-    l8[e] = bf16_of(a);
-    h8[e] = bf16_of(b);
-  }
-  if (n == 8) {
-    *reinterpret_cast<uint4*>(lo + i8) = make_uint4(l8[0] | (uint32_t(l8[1]) << 16), l8[2] | (uint32_t(l8[3]) << 16),
-                                                    l8[4] | (uint32_t(l8[5]) << 16), l8[6] | (uint32_t(l8[7]) << 16));
-    *reinterpret_cast<uint4*>(hi + i8) = make_uint4(h8[0] | (uint32_t(h8[1]) << 16), h8[2] | (uint32_t(h8[3]) << 16),
-                                                    h8[4] | (uint32_t(h8[5]) << 16), h8[6] | (uint32_t(h8[7]) << 16));
-  } else {
-    for (size_t e = 0; e < n; ++e) {
-      lo[i8 + e] = l8[e];
-      hi[i8 + e] = h8[e];
-    }
-  }
-}
+// fp16 bit pattern of a limb (an integer in [-128, 127], exactly an fp16 value): the operand
+// encoding of the tcgen05 paths' query side.
+__device__ __forceinline__ uint16_t f16_of(int8_t v) { return __half_as_ushort(__short2half_rn(v)); }
 
 // A1: 8 elements per thread.
 __global__ void split_limbs_kernel(const uint16_t* __restrict__ x, size_t count, int8_t* __restrict__ lo,
@@ -122,7 +96,7 @@ __global__ void split_limbs_kernel(const uint16_t* __restrict__ x, size_t count,
 }
 
 // A2: one thread per output element of B_i (row n, position k of 2l). Limb type T: int8_t, or
-// uint16_t for the bf16 bit patterns of the same limbs.
+// uint16_t for the fp16 bit patterns of the same limbs.
 template <typename T>
 __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint64_t plane, uint32_t Q, ipc_geom g,
                                   uint32_t party, T* __restrict__ b_lo, T* __restrict__ b_hi, uint32_t n_pad) {
@@ -155,13 +129,13 @@ __global__ void prep_query_kernel(const uint16_t* __restrict__ y, uint64_t plane
     b_lo[tid] = a;
     b_hi[tid] = b;
   } else {
-    b_lo[tid] = bf16_of(a);
-    b_hi[tid] = bf16_of(b);
+    b_lo[tid] = f16_of(a);
+    b_hi[tid] = f16_of(b);
   }
 }
 
 // A2 with eight consecutive elements of one row n of B_i per thread (l a multiple of 8, so a
-// group never straddles a row or the two halves): one 16-byte store per limb plane for bf16
+// group never straddles a row or the two halves): one 16-byte store per limb plane for fp16
 // limbs, 8 bytes for int8. The first element's (r, j, c) takes the divisions; the next ones
 // step c, then the rotated column js (mod cols) and the row.
 template <typename T>
@@ -217,8 +191,8 @@ __global__ void prep_query_vec_kernel(const uint16_t* __restrict__ y, uint64_t p
     uint32_t l4[4], h4[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      l4[v] = bf16_of(a[2 * v]) | (static_cast<uint32_t>(bf16_of(a[2 * v + 1])) << 16);
-      h4[v] = bf16_of(b[2 * v]) | (static_cast<uint32_t>(bf16_of(b[2 * v + 1])) << 16);
+      l4[v] = f16_of(a[2 * v]) | (static_cast<uint32_t>(f16_of(a[2 * v + 1])) << 16);
+      h4[v] = f16_of(b[2 * v]) | (static_cast<uint32_t>(f16_of(b[2 * v + 1])) << 16);
     }
     *reinterpret_cast<uint4*>(b_lo + tid * 8) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
     *reinterpret_cast<uint4*>(b_hi + tid * 8) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
@@ -290,32 +264,56 @@ __global__ void encode_share_galois_kernel(const uint64_t* __restrict__ code_bit
 }
 
 // A2 for Galois-ring shares: B_p[n][k] = coefficient k & 1 of lambda_p * y_p[e'] where e' is the
-// element of the unrotated query that rotation rho brings to position k / 2. K = l.
+// element of the unrotated query that rotation rho brings to position k / 2. K = l. Eight
+// consecutive k (four elements) of one row n per thread, one 16-byte store per limb plane; the
+// cell size is even, so an element's two coefficients stay in one cell and move together.
 __global__ void prep_query_galois_kernel(const uint16_t* __restrict__ y, uint64_t plane, uint32_t Q, ipc_geom g,
                                          uint32_t party, Gr lambda, uint16_t* __restrict__ b_lo,
                                          uint16_t* __restrict__ b_hi, uint32_t n_pad) {
   const uint32_t l = g.rows * g.cols * g.cell;
+  const uint32_t groups = l / 8;
   const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
-  const uint64_t total = static_cast<uint64_t>(n_pad) * l;
-  if (tid >= total) return;
-  const uint32_t n = static_cast<uint32_t>(tid / l);
-  const uint32_t k = static_cast<uint32_t>(tid % l);
-  uint32_t val = 0;
+  if (tid >= static_cast<uint64_t>(n_pad) * groups) return;
+  const uint32_t n = static_cast<uint32_t>(tid / groups);
+  const uint32_t k0 = static_cast<uint32_t>(tid % groups) * 8;
+  uint32_t val[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   if (n < Q * g.R) {
     const uint32_t q = n / g.R, rho = n % g.R;
     const int32_t shift = g.rot_lo + static_cast<int32_t>(rho);
-    const uint32_t c = k % g.cell, j = (k / g.cell) % g.cols, r = k / (g.cell * g.cols);
-    int32_t js = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
-    if (js < 0) js += g.cols;
-    const uint32_t src = (r * g.cols + static_cast<uint32_t>(js)) * g.cell + c;  // same parity as k
-    const uint16_t* yp = y + party * plane + static_cast<uint64_t>(q) * l + (src & ~1u);
-    const Gr a = gr_mul(lambda, Gr{yp[0], yp[1]});
-    val = (k & 1u) ? a.c1 : a.c0;
+    uint32_t c = k0 % g.cell;
+    const uint32_t cidx = k0 / g.cell;
+    uint32_t j = cidx % g.cols, r = cidx / g.cols;
+    int32_t jsi = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
+    uint32_t js = static_cast<uint32_t>(jsi < 0 ? jsi + static_cast<int32_t>(g.cols) : jsi);
+    const uint16_t* yq = y + party * plane + static_cast<uint64_t>(q) * l;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t src = (r * g.cols + js) * g.cell + c;  // even: c is even
+      const Gr a = gr_mul(lambda, Gr{yq[src], yq[src + 1]});
+      val[2 * e] = a.c0;
+      val[2 * e + 1] = a.c1;
+      c += 2;
+      if (c == g.cell) {
+        c = 0;
+        if (++js == g.cols) js = 0;
+        if (++j == g.cols) {
+          j = 0;
+          ++r;
+        }
+      }
+    }
   }
-  int8_t lo, hi;
-  limbs(val, lo, hi);
-  b_lo[tid] = bf16_of(lo);
-  b_hi[tid] = bf16_of(hi);
+  uint32_t l4[4], h4[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    int8_t a0, b0, a1, b1;
+    limbs(val[2 * v] & 0xFFFFu, a0, b0);
+    limbs(val[2 * v + 1] & 0xFFFFu, a1, b1);
+    l4[v] = f16_of(a0) | (static_cast<uint32_t>(f16_of(a1)) << 16);
+    h4[v] = f16_of(b0) | (static_cast<uint32_t>(f16_of(b1)) << 16);
+  }
+  *reinterpret_cast<uint4*>(b_lo + tid * 8) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+  *reinterpret_cast<uint4*>(b_hi + tid * 8) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
 }
 
 bool geom_ok(const ipc_geom* g) {
@@ -389,7 +387,7 @@ int prep_query_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, const ip
     set_error(std::string(who) + ": component stride shorter than Q * l");
     return IPC_EINVAL;
   }
-  const uintptr_t align = 8 * sizeof(T) - 1;  // one group's store: 16 bytes (bf16) or 8 (int8)
+  const uintptr_t align = 8 * sizeof(T) - 1;  // one group's store: 16 bytes (fp16) or 8 (int8)
   if (l % 8 == 0 && !(reinterpret_cast<uintptr_t>(b_lo) & align) && !(reinterpret_cast<uintptr_t>(b_hi) & align)) {
     const uint64_t threads = total / 8;
     prep_query_vec_kernel<T><<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
@@ -413,24 +411,10 @@ extern "C" int ipc_prep_query(const uint16_t* y, uint32_t Q, const ipc_geom* g, 
   return prep_query_strided(y, Q * l, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query");
 }
 
-extern "C" int ipc_prep_query_bf16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
-                                   uint16_t* b_hi, uint32_t n_pad, void* stream) {
+extern "C" int ipc_prep_query_f16(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint32_t party, uint16_t* b_lo,
+                                  uint16_t* b_hi, uint32_t n_pad, void* stream) {
   const uint64_t l = g ? static_cast<uint64_t>(g->rows) * g->cols * g->cell : 0;
-  return prep_query_strided(y, Q * l, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query_bf16");
-}
-
-extern "C" int ipc_split_limbs_bf16(const uint16_t* x, size_t count, uint16_t* lo, uint16_t* hi, void* stream) {
-  if (count == 0 || !x || !lo || !hi || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(lo) & 15) ||
-      (reinterpret_cast<uintptr_t>(hi) & 15)) {
-    set_error("ipc_split_limbs_bf16: count > 0, x, lo and hi 16-byte aligned");
-    return IPC_EINVAL;
-  }
-  const size_t threads = (count + 7) / 8;
-  const uint32_t bs = 256;
-  split_limbs_bf16_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(x, count, lo,
-                                                                                                      hi);
-  IPC_CUDA_TRY(cudaGetLastError());
-  return IPC_OK;
+  return prep_query_strided(y, Q * l, Q, g, party, b_lo, b_hi, n_pad, stream, "ipc_prep_query_f16");
 }
 
 namespace {
@@ -499,25 +483,31 @@ int prep_query_galois_strided(const uint16_t* y, uint64_t y_plane, uint32_t Q, c
     set_error("ipc_prep_query_galois: component stride shorter than Q * l");
     return IPC_EINVAL;
   }
-  const uint64_t total = static_cast<uint64_t>(n_pad) * l;
+  if ((reinterpret_cast<uintptr_t>(b_lo) & 15) || (reinterpret_cast<uintptr_t>(b_hi) & 15)) {
+    set_error("ipc_prep_query_galois: b_lo and b_hi must be 16-byte aligned");
+    return IPC_EINVAL;
+  }
+  const uint64_t threads = static_cast<uint64_t>(n_pad) * (l / 8);
   const uint32_t bs = 256;
-  prep_query_galois_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+  prep_query_galois_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
       y, y_plane, Q, *g, party, lagrange_at_zero(party), b_lo, b_hi, n_pad);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
-// Public operand of protocol 1: B[n][k] = bf16 of rot_rho(y[q])[k] for 0/1 values y [Q][l] (the
-// plain mask bits; K = l): the Galois preparation with lambda = 1 reads each element unchanged.
+// Public operand of protocol 1: B[n][k] = fp16 limbs of rot_rho(y[q])[k] for 0/1 values y [Q][l]
+// (the plain mask bits; K = l): the Galois preparation with lambda = 1 reads each element
+// unchanged.
 int prep_query_rotate_plain(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint16_t* b_lo, uint16_t* b_hi,
                             uint32_t n_pad, void* stream) {
-  if (!geom_ok(g) || g->cell % 2 != 0 || !y || !b_lo || !b_hi || Q == 0 || static_cast<uint64_t>(Q) * g->R > n_pad) {
-    set_error("plain-mask operand: invalid geometry (even cell) or n_pad < Q*R");
+  if (!geom_ok(g) || g->cell % 2 != 0 || !y || !b_lo || !b_hi || Q == 0 || static_cast<uint64_t>(Q) * g->R > n_pad ||
+      (reinterpret_cast<uintptr_t>(b_lo) & 15) || (reinterpret_cast<uintptr_t>(b_hi) & 15)) {
+    set_error("plain-mask operand: invalid geometry (even cell), n_pad < Q*R or unaligned outputs");
     return IPC_EINVAL;
   }
   const uint64_t l = static_cast<uint64_t>(g->rows) * g->cols * g->cell;
-  const uint64_t total = static_cast<uint64_t>(n_pad) * l;
+  const uint64_t threads = static_cast<uint64_t>(n_pad) * (l / 8);
   const uint32_t bs = 256;
-  prep_query_galois_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
+  prep_query_galois_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, as_stream(stream)>>>(
       y, static_cast<uint64_t>(Q) * l, Q, *g, 0, Gr{1, 0}, b_lo, b_hi, n_pad);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;

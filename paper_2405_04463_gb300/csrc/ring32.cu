@@ -2,8 +2,9 @@
 // NoLift also the code dot product, over Z_{2^32}.
 //
 // A0: client sharing of the masked bits and mask bits read in Z_{2^32}.
-// A1/A2: four balanced int8 limbs per element, x = x0 + 2^8 x1 + 2^16 x2 + 2^24 x3 (mod 2^32),
-//        each written as the bf16 bit pattern of the limb (exact).
+// A1: four balanced int8 limbs per element, x = x0 + 2^8 x1 + 2^16 x2 + 2^24 x3 (mod 2^32), in
+//     four resident int8 planes (the size of the u32 shares).
+// A2: the query operand's four limbs as fp16 bit patterns (exact).
 // A3 (gemm_tc32_kernel): the ring dot product on tcgen05 with fp32 TMEM accumulators, exact:
 //     z = sum_s 2^(8s) S_s (mod 2^32),  S_s = sum over a + b = s of sum_k x_a[k] y_b[k],
 //   ten limb products per k (1 + 2 + 3 + 4 for s = 0..3); products with a + b > 3 vanish mod
@@ -12,23 +13,16 @@
 //   gains at most (s + 1) 2^14 per k, so S_3 and S_2 are drained every 64 k, S_1 every 128 k,
 //   S_0 every 256 k. A drain adds (bits - bits(M)) << 8s to a 32-bit running sum per column;
 //   bits(M) << 8s vanishes mod 2^32 for s >= 2, and the S_1 and S_0 terms are subtracted once,
-//   up front.
-//
-// One CTA per tile of 128 database rows x 128 query columns (MMA 128 x 128 x 16), 10 warps:
-//   warp 0 lane 0  TMA producer: per k-block of 32 elements, eight tiles (database limbs 0-3,
-//                  query limbs 0-3; 128 x 32 bf16 each, 64-byte swizzle) into a 3-stage ring.
-//   warp 1 lane 0  MMA issuer: per k-block the S_3, S_2, S_1, S_0 products in that order,
-//                  committing S_s-full after the last k-block of its drain period and the stage
-//                  after the k-block's S_0 products. S_3's drain overlaps the k-block's other six
-//                  products; S_2's the S_1, S_0 products and the next k-block's S_3 products.
-//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 64 columns.
-// TMEM: S_s in columns [128 s, 128 s + 128), all 512 columns.
-// Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
-// status word, lets its copies and MMAs finish, frees its tensor memory and stores nothing.
+//   up front. The database limbs are widened from int8 to fp16 in shared memory, as in the
+//   16-bit kernel. Every wait is bounded (2 s, or sooner once another role has failed); a failed
+//   CTA raises the status word, lets its copies and MMAs finish, frees its tensor memory and
+//   stores nothing.
+#include <cuda_fp16.h>
+
 #include <mutex>
 #include <string>
 
-#include "tcgen05_pair.cuh"
+#include "tcgen05.cuh"
 
 namespace ipc {
 namespace {
@@ -45,9 +39,7 @@ __device__ __forceinline__ void limbs32(uint32_t x, int8_t (&o)[4]) {
   }
 }
 
-__device__ __forceinline__ uint16_t bf16_of8(int8_t v) {
-  return static_cast<uint16_t>(__float_as_uint(static_cast<float>(v)) >> 16);
-}
+__device__ __forceinline__ uint16_t f16_of8(int8_t v) { return __half_as_ushort(__short2half_rn(v)); }
 
 // A0 over Z_{2^32}: one thread per (row, 2 consecutive elements); one Philox call per vector
 // gives both elements' x_0, x_1 (words 2e, 2e + 1).
@@ -81,107 +73,117 @@ __global__ void encode_share32_kernel(const uint64_t* __restrict__ code_bits, co
   }
 }
 
-// A1 over Z_{2^32}: 4 elements per thread, one bf16 limb plane per limb.
-__global__ void split_limbs32_kernel(const uint32_t* __restrict__ x, size_t count, uint16_t* __restrict__ o0,
-                                     uint16_t* __restrict__ o1, uint16_t* __restrict__ o2,
-                                     uint16_t* __restrict__ o3) {
+// A1 over Z_{2^32}: 4 elements per thread, one int8 limb plane per limb.
+__global__ void split_limbs32_kernel(const uint32_t* __restrict__ x, size_t count, int8_t* __restrict__ o0,
+                                     int8_t* __restrict__ o1, int8_t* __restrict__ o2, int8_t* __restrict__ o3) {
   const size_t i4 = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) * 4;
   if (i4 >= count) return;
-  uint16_t* out[4] = {o0, o1, o2, o3};
+  int8_t* out[4] = {o0, o1, o2, o3};
   if (i4 + 4 <= count) {
     const uint4 v = *reinterpret_cast<const uint4*>(x + i4);
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    uint32_t packed[4][2] = {};
+    uint32_t packed[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       int8_t lb[4];
       limbs32(w[e], lb);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) packed[i][e >> 1] |= static_cast<uint32_t>(bf16_of8(lb[i])) << (16 * (e & 1));
+      for (int i = 0; i < 4; ++i) packed[i] |= static_cast<uint32_t>(static_cast<uint8_t>(lb[i])) << (8 * e);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2*>(out[i] + i4) = make_uint2(packed[i][0], packed[i][1]);
+    for (int i = 0; i < 4; ++i) *reinterpret_cast<uint32_t*>(out[i] + i4) = packed[i];
   } else {
     for (size_t e = i4; e < count; ++e) {
       int8_t lb[4];
       limbs32(x[e], lb);
-      for (int i = 0; i < 4; ++i) out[i][e] = bf16_of8(lb[i]);
+      for (int i = 0; i < 4; ++i) out[i][e] = lb[i];
     }
   }
 }
 
 // A2 over Z_{2^32}: party i's operand [rot(Y_i + Y_{i-1}) | rot(Y_i)] (K = 2l), or, for one
-// segment, rot(Y_i) alone (K = l); one thread per output element, four bf16 limb planes.
+// segment, rot(Y_i) alone (K = l); four fp16 limb planes. Eight consecutive k of one row n per
+// thread (l a multiple of 8, so a group stays in one half), one 16-byte store per plane.
 __global__ void prep_query32_kernel(const uint32_t* __restrict__ y, uint64_t plane, uint32_t Q, ipc_geom g,
                                     uint32_t party, uint32_t segments, uint16_t* __restrict__ o0,
                                     uint16_t* __restrict__ o1, uint16_t* __restrict__ o2, uint16_t* __restrict__ o3,
                                     uint32_t n_pad) {
-  const uint32_t l = g.rows * g.cols * g.cell, K = segments * l;
+  const uint32_t l = g.rows * g.cols * g.cell, K = segments * l, groups = K / 8;
   const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
-  const uint64_t total = static_cast<uint64_t>(n_pad) * K;
-  if (tid >= total) return;
-  const uint32_t n = static_cast<uint32_t>(tid / K);
-  const uint32_t k = static_cast<uint32_t>(tid % K);
-  uint32_t val = 0;
+  if (tid >= static_cast<uint64_t>(n_pad) * groups) return;
+  const uint32_t n = static_cast<uint32_t>(tid / groups);
+  const uint32_t k0 = static_cast<uint32_t>(tid % groups) * 8;
+  uint32_t val[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   if (n < Q * g.R) {
     const uint32_t q = n / g.R, rho = n % g.R;
     const int32_t shift = g.rot_lo + static_cast<int32_t>(rho);
-    const uint32_t kk = k < l ? k : k - l;
-    const uint32_t c = kk % g.cell, j = (kk / g.cell) % g.cols, r = kk / (g.cell * g.cols);
-    int32_t js = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
-    if (js < 0) js += g.cols;
-    const uint32_t src = (r * g.cols + static_cast<uint32_t>(js)) * g.cell + c;
+    const bool sum = segments == 2 && k0 < l;  // first half of K = 2l: y_i + y_{i-1}
+    const uint32_t kk = k0 < l ? k0 : k0 - l;
+    uint32_t c = kk % g.cell;
+    const uint32_t cidx = kk / g.cell;
+    uint32_t j = cidx % g.cols, r = cidx / g.cols;
+    int32_t jsi = (static_cast<int32_t>(j) - shift) % static_cast<int32_t>(g.cols);
+    uint32_t js = static_cast<uint32_t>(jsi < 0 ? jsi + static_cast<int32_t>(g.cols) : jsi);
     const uint32_t prev = (party + 2) % 3;
-    val = y[party * plane + static_cast<uint64_t>(q) * l + src];
-    if (segments == 2 && k < l) val += y[prev * plane + static_cast<uint64_t>(q) * l + src];  // y_i + y_{i-1}
+    const uint32_t* yi = y + party * plane + static_cast<uint64_t>(q) * l;
+    const uint32_t* yp = y + prev * plane + static_cast<uint64_t>(q) * l;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t src = (r * g.cols + js) * g.cell + c;
+      val[e] = sum ? yi[src] + yp[src] : yi[src];
+      if (++c == g.cell) {
+        c = 0;
+        if (++js == g.cols) js = 0;
+        if (++j == g.cols) {
+          j = 0;
+          ++r;
+        }
+      }
+    }
   }
-  int8_t lb[4];
-  limbs32(val, lb);
-  o0[tid] = bf16_of8(lb[0]);
-  o1[tid] = bf16_of8(lb[1]);
-  o2[tid] = bf16_of8(lb[2]);
-  o3[tid] = bf16_of8(lb[3]);
+  uint32_t w[4][4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    int8_t a[4], b[4];
+    limbs32(val[2 * v], a);
+    limbs32(val[2 * v + 1], b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i][v] = f16_of8(a[i]) | (static_cast<uint32_t>(f16_of8(b[i])) << 16);
+  }
+  uint16_t* out[4] = {o0, o1, o2, o3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) *reinterpret_cast<uint4*>(out[i] + tid * 8) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
 }
 
 // ----------------------------------- A3 -----------------------------------
-// PAIR = false: one CTA per 128-row x 128-column tile (MMA 128 x 128 x 16).
-// PAIR = true:  a cluster of two CTAs per 256-row x 128-column tile (cta_group::2, M = 256): CTA
-//   rank r owns rows 128 r .. 128 r + 127 and holds query columns 64 r .. 64 r + 63 of the tile in
-//   its shared memory, so each SM reads half the query tile per MMA. With N = 128 a single CTA's
-//   MMAs read 8 KiB of shared memory per 64 tensor cycles, the whole read rate; the pair reads
-//   6 KiB. The leader (rank 0) issues the MMAs and commits to both CTAs' barriers; both CTAs'
-//   producers count their copies on the leader's full barrier; the drain-empty barriers live in
-//   the leader and count both CTAs' drain warps.
+// One CTA per tile of 128 database rows x 128 query columns (MMA 128 x 128 x 16).
 constexpr int TM = 128, TN = 128, KB = 32, LIMBS = 4;
-constexpr int TILE_BYTES = TM * KB * 2;  // 8 KiB database tile
-constexpr int THREADS = 10 * 32, DRAIN_THREADS = 8 * 32;
+constexpr int W_TILE = TM * KB * 2;  // 8 KiB widened (fp16) database tile
+constexpr int RAW_TILE = TM * KB;    // 4 KiB raw (int8) database tile
+constexpr int B_TILE = TN * KB * 2;  // 8 KiB query tile
+constexpr int R_STAGES = 3, W_STAGES = 2;
+// R stage: query limbs 0-3, then raw database limbs 0-3; W stage: widened database limbs 0-3
+constexpr int R_STAGE = LIMBS * B_TILE + LIMBS * RAW_TILE;  // 48 KiB
+constexpr int W_STAGE = LIMBS * W_TILE;                      // 32 KiB
+constexpr int THREADS = 12 * 32, DRAIN_THREADS = 8 * 32;
+constexpr int WIDEN_WARP0 = 10, WIDEN_THREADS = 2 * 32;
 constexpr uint32_t KB_PER_CHUNK = 2;  // 64 k: the shortest drain period
 constexpr uint32_t TMEM_COLS = 4 * TN;
 constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
-
-template <bool PAIR>
-struct Cfg32 {
-  static constexpr int HN = PAIR ? TN / 2 : TN;                  // query columns held by this CTA
-  static constexpr int B_TILE = HN * KB * 2;                     // 4 or 8 KiB
-  static constexpr int STAGE_BYTES = LIMBS * TILE_BYTES + LIMBS * B_TILE;  // 48 or 64 KiB
-  static constexpr int STAGES = PAIR ? 4 : 3;
-  // full[S], empty[S], g_full[4], g_empty[4], done
-  static constexpr int NUM_BARS = 2 * STAGES + 9;
-  // pair: 16 KiB after the ring, so that every MMA operand read stays inside the allocation
-  static constexpr int SLACK = PAIR ? 16384 : 0;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + SLACK + 1024 + 8 * NUM_BARS;
-  // kind::f16: D f32, A and B bf16, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(TN >> 3) << 17) |
-                                    (static_cast<uint32_t>((PAIR ? 2 * TM : TM) >> 4) << 24);
-  static_assert(TN * TM * 4 <= STAGES * STAGE_BYTES, "the z tile is staged in the stage ring");
-};
+// r_full[R], r_empty[R], w_full[W], w_empty[W], g_full[4], g_empty[4], done
+constexpr int NUM_BARS = 2 * R_STAGES + 2 * W_STAGES + 9;
+constexpr int SMEM_BYTES = R_STAGES * R_STAGE + W_STAGES * W_STAGE + 1024 + 8 * NUM_BARS;
+static_assert(SMEM_BYTES <= 232448, "dynamic shared memory per block");
+static_assert(TN * TM * 4 <= R_STAGES * R_STAGE, "the z tile is staged in the R ring");
+// kind::f16: D f32, A and B f16, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (static_cast<uint32_t>(TN >> 3) << 17) | (static_cast<uint32_t>(TM >> 4) << 24);
 
 // Drain period of S_s in 64-k chunks.
 __host__ __device__ constexpr uint32_t period(int s) { return s == 0 ? 4u : (s == 1 ? 2u : 1u); }
 
 struct Maps32 {
-  CUtensorMap b[LIMBS];   // query limbs [n_pad][K]
-  CUtensorMap a0[LIMBS];  // database limbs of the first K segment [x_rows][l]
+  CUtensorMap b[LIMBS];   // query limbs [n_pad][K], fp16
+  CUtensorMap a0[LIMBS];  // database limbs of the first K segment [x_rows][l], int8
   CUtensorMap a1[LIMBS];  // and of the second
 };
 
@@ -199,57 +201,58 @@ struct Tc32Params {
   uint32_t* status;
 };
 
-template <bool PAIR>
+// Roles (12 warps):
+//   warp 0 lane 0  TMA producer: per k-block of 32 elements, the four fp16 query limb tiles
+//                  (128 x 32, 64-byte swizzle) and the four raw int8 database limb tiles (128 x 32)
+//                  into a 3-stage ring.
+//   warps 10-11    widening: per k-block the four raw database tiles become fp16 operand tiles in
+//                  a 2-stage ring of their own, so the copies can run a stage further ahead.
+//   warp 1 lane 0  MMA issuer: per k-block the S_3, S_2, S_1, S_0 products in that order,
+//                  committing S_s-full after the last k-block of its drain period and both stages
+//                  after the k-block's S_0 products. S_3's drain overlaps the k-block's other six
+//                  products; S_2's the S_1, S_0 products and the next k-block's S_3 products.
+//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 64 columns.
+// TMEM: S_s in columns [128 s, 128 s + 128), all 512 columns.
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_constant__ Maps32 m, const Tc32Params p) {
-  using C = Cfg32<PAIR>;
-  constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ uint32_t s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t tiles = smem_addr(smem);
-  const uint32_t bars = tiles + STAGES * STAGE_BYTES + C::SLACK;
-  const uint32_t full0 = bars, empty0 = bars + 8 * STAGES;
-  const uint32_t g_full = bars + 16 * STAGES, g_empty = g_full + 32, done_bar = g_full + 64;
+  const uint32_t rring = smem_addr(smem), wring = rring + R_STAGES * R_STAGE;
+  const uint32_t bars = wring + W_STAGES * W_STAGE;
+  const uint32_t r_full = bars, r_empty = bars + 8 * R_STAGES;
+  const uint32_t w_full = bars + 16 * R_STAGES, w_empty = w_full + 8 * W_STAGES;
+  const uint32_t g_full = w_empty + 8 * W_STAGES, g_empty = g_full + 32, done_bar = g_full + 64;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = PAIR ? cluster_rank() : 0u;
-  const bool leader = rank == 0;
-  const uint32_t q0 = (PAIR ? (blockIdx.x >> 1) : blockIdx.x) * TN;  // the tile's first query column
-  const uint32_t qh = q0 + rank * C::HN;                              // this CTA's query columns
-  const uint32_t d0 = PAIR ? blockIdx.y * (2 * TM) + rank * TM : blockIdx.y * TM;
+  const uint32_t q0 = blockIdx.x * TN, d0 = blockIdx.y * TM;
   const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;  // a multiple of 4: K is a multiple of 256
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+    for (int s = 0; s < R_STAGES; ++s) {
+      mbar_init(r_full + 8 * s, 1);
+      mbar_init(r_empty + 8 * s, 1);
+    }
+    for (int s = 0; s < W_STAGES; ++s) {
+      mbar_init(w_full + 8 * s, WIDEN_THREADS / 32);
+      mbar_init(w_empty + 8 * s, 1);
     }
     for (int g = 0; g < 4; ++g) {
       mbar_init(g_full + 8 * g, 1);
-      mbar_init(g_empty + 8 * g, (PAIR ? 2 : 1) * DRAIN_THREADS / 32);
+      mbar_init(g_empty + 8 * g, DRAIN_THREADS / 32);
     }
     mbar_init(done_bar, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    if constexpr (PAIR) {
-      // one warp of each CTA of the pair allocates, collectively, the same columns in both
-      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                   "r"(TMEM_COLS)
-                   : "memory");
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-    } else {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                   "r"(TMEM_COLS)
-                   : "memory");
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   fence_before();
   __syncthreads();
-  if constexpr (PAIR) cluster_sync();  // both CTAs' barriers exist before any remote arrive or TMA
   fence_after();
   const uint32_t tmem = s_tmem;
 
@@ -258,50 +261,38 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     if (lane == 0) {
       uint32_t issued = 0;
       for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
-        const uint32_t s = kb % STAGES;
-        if (!mbar_wait(empty0 + 8 * s, ((kb / STAGES) & 1u) ^ 1u, p.status, abort)) break;
-        const uint32_t full_own = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
+        const uint32_t s = kb % R_STAGES;
+        if (!mbar_wait(r_empty + 8 * s, ((kb / R_STAGES) & 1u) ^ 1u, p.status, abort)) break;
+        const uint32_t full = r_full + 8 * s, base = rring + s * R_STAGE;
         const bool first = kb < p.kb_half;
         const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
-        if constexpr (PAIR) {
-          if (leader) mbar_expect_tx(full_own, 2 * STAGE_BYTES);  // both CTAs' halves
-          const uint32_t full = peer_addr(full_own, 0);
+        mbar_expect_tx(full, R_STAGE);
 #pragma unroll
-          for (int a = 0; a < LIMBS; ++a)
-            tma_load_pair(base + a * TILE_BYTES, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full);
+        for (int b = 0; b < LIMBS; ++b)
+          tma_load(base + b * B_TILE, &m.b[b], static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
 #pragma unroll
-          for (int b = 0; b < LIMBS; ++b)
-            tma_load_pair(base + LIMBS * TILE_BYTES + b * C::B_TILE, &m.b[b], static_cast<int32_t>(kb * KB),
-                          static_cast<int32_t>(qh), full);
-        } else {
-          mbar_expect_tx(full_own, STAGE_BYTES);
-#pragma unroll
-          for (int a = 0; a < LIMBS; ++a)
-            tma_load(base + a * TILE_BYTES, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full_own);
-#pragma unroll
-          for (int b = 0; b < LIMBS; ++b)
-            tma_load(base + LIMBS * TILE_BYTES + b * C::B_TILE, &m.b[b], static_cast<int32_t>(kb * KB),
-                     static_cast<int32_t>(qh), full_own);
-        }
+        for (int a = 0; a < LIMBS; ++a)
+          tma_load(base + LIMBS * B_TILE + a * RAW_TILE, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0),
+                   full);
         issued = kb + 1;
       }
       if (*abort) {
-        // copies that may still be in flight land before the CTA goes on (bounded, no abort);
-        // a pair's copies are counted on the leader's barriers, so its own stage-empty phases
-        // stand in for them
-        for (uint32_t kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-          mbar_wait((PAIR ? empty0 : full0) + 8 * (kb % STAGES), (kb / STAGES) & 1u, p.status, nullptr);
+        // copies that may still be in flight land before the CTA goes on (bounded, no abort)
+        for (uint32_t kb = issued > R_STAGES ? issued - R_STAGES : 0; kb < issued; ++kb)
+          mbar_wait(r_full + 8 * (kb % R_STAGES), (kb / R_STAGES) & 1u, p.status, nullptr);
       }
     }
   } else if (warp == 1) {
-    // ------------------------- MMA issuer (the leader of a pair) -------------------------
-    if (leader && lane == 0) {
+    // -------------------------------- MMA issuer --------------------------------
+    if (lane == 0) {
       bool ok = true;
       for (uint32_t kb = 0; kb < p.kb_total && ok; ++kb) {
-        const uint32_t s = kb % STAGES, c = kb / KB_PER_CHUNK, j = kb % KB_PER_CHUNK;
-        if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1u, p.status, abort)) break;
+        const uint32_t s = kb % R_STAGES, w = kb % W_STAGES, c = kb / KB_PER_CHUNK, j = kb % KB_PER_CHUNK;
+        if (!mbar_wait(r_full + 8 * s, (kb / R_STAGES) & 1u, p.status, abort) ||
+            !mbar_wait(w_full + 8 * w, (kb / W_STAGES) & 1u, p.status, abort))
+          break;
         fence_after();
-        const uint32_t base = tiles + s * STAGE_BYTES;
+        const uint32_t qbase = rring + s * R_STAGE, dbase = wring + w * W_STAGE;
 #pragma unroll
         for (int g = 3; g >= 0; --g) {
           const uint32_t per = period(g);
@@ -316,48 +307,40 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
           const uint32_t t = tmem + TN * static_cast<uint32_t>(g);
 #pragma unroll
           for (uint32_t ks = 0; ks < KB / 16; ++ks) {
-            const uint32_t o = 32u * ks;  // 16 bf16 = 32 bytes along K inside the swizzled row
+            const uint32_t o = 32u * ks;  // 16 fp16 = 32 bytes along K inside the swizzled row
 #pragma unroll
-            for (int a = 0; a <= g; ++a) {
-              const uint64_t da = sdesc(base + a * TILE_BYTES + o);
-              const uint64_t db = sdesc(base + LIMBS * TILE_BYTES + (g - a) * C::B_TILE + o);
-              if constexpr (PAIR)
-                umma_pair_desc(t, da, db, C::IDESC);
-              else
-                umma(t, da, db, C::IDESC);
-            }
+            for (int a = 0; a <= g; ++a)
+              umma(t, sdesc(dbase + a * W_TILE + o), sdesc(qbase + (g - a) * B_TILE + o), IDESC);
           }
-          if (j == KB_PER_CHUNK - 1 && c % per == per - 1) {
-            if constexpr (PAIR)
-              umma_commit_pair(g_full + 8 * g);
-            else
-              umma_commit(g_full + 8 * g);
-          }
+          if (j == KB_PER_CHUNK - 1 && c % per == per - 1) umma_commit(g_full + 8 * g);
         }
-        if (ok) {  // stage free once these (and all earlier) MMAs are done
-          if constexpr (PAIR)
-            umma_commit_pair(empty0 + 8 * s);
-          else
-            umma_commit(empty0 + 8 * s);
+        if (ok) {  // both stages free once these (and all earlier) MMAs are done
+          umma_commit(r_empty + 8 * s);
+          umma_commit(w_empty + 8 * w);
         }
       }
       // every MMA issued above completes before the tensor memory is freed
-      if constexpr (PAIR)
-        umma_commit_pair(done_bar);
-      else
-        umma_commit(done_bar);
+      umma_commit(done_bar);
       mbar_wait(done_bar, 0, p.status, nullptr);
+    }
+  } else if (warp >= WIDEN_WARP0) {
+    // ---------------------------------- widening ---------------------------------
+    const uint32_t ct = threadIdx.x - WIDEN_WARP0 * 32;
+    for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
+      const uint32_t s = kb % R_STAGES, w = kb % W_STAGES;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_full + 8 * s, (kb / R_STAGES) & 1u, p.status, abort) &&
+                                       mbar_wait(w_empty + 8 * w, ((kb / W_STAGES) & 1u) ^ 1u, p.status, abort)))
+        break;
+      widen_tiles<LIMBS, WIDEN_THREADS>(rring + s * R_STAGE + LIMBS * B_TILE, RAW_TILE, wring + w * W_STAGE, W_TILE,
+                                        ct);
+      fence_proxy_async();  // the MMAs read these tiles through the async proxy
+      __syncwarp();
+      if (lane == 0) mbar_arrive(w_full + 8 * w);
     }
   } else {
     // ----------------------------------- drain ----------------------------------
     const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - 2) >> 2;
     const uint32_t tl = tmem + ((32u * q) << 16) + 64u * h;
-    auto release = [&](int g) {
-      if constexpr (PAIR)
-        arrive_leader(g_empty + 8 * g, leader);
-      else
-        mbar_arrive(g_empty + 8 * g);
-    };
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       tmem_fill32(tl + TN * g, MAGIC);
@@ -367,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     fence_before();
     __syncwarp();
     if (lane == 0)
-      for (int g = 0; g < 4; ++g) release(g);
+      for (int g = 0; g < 4; ++g) mbar_arrive(g_empty + 8 * g);
     // each S_1 drain adds bits(M) << 8 and each S_0 drain bits(M) once too often
     const uint32_t corr = 0u - (n_chunks / period(1)) * (MAGIC << 8) - (n_chunks / period(0)) * MAGIC;
     uint32_t acc[64];
@@ -396,13 +379,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
         tmem_wait_st();
         fence_before();
         __syncwarp();
-        if (lane == 0) release(g);
+        if (lane == 0) mbar_arrive(g_empty + 8 * g);
       }
     }
     // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) over Z_{2^32} (App. C) ----
-    // The sums go to shared memory (the stage ring is idle: the last S_0-full followed every
-    // MMA), then each (column, 4-row group) item adds the zero shares of its four rows, one
-    // Philox block per seed, and writes 16 bytes of z.
+    // The sums go to shared memory (the R ring is idle: the last S_0-full followed every MMA,
+    // and every copy was consumed), then each (column, 4-row group) item adds the zero shares of
+    // its four rows, one Philox block per seed, and writes 16 bytes of z.
     named_sync(1, DRAIN_THREADS);
     if (!*abort) {  // uniform: read after the barrier that every drainer reaches
       uint32_t* zs = reinterpret_cast<uint32_t*>(smem);  // [TN][TM]
@@ -431,50 +414,22 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
       }
     }
   }
-  // a pair's MMAs are complete (the leader's issuer waited for them) before either CTA frees
-  // tensor memory or leaves
   fence_before();
   __syncthreads();
-  if constexpr (PAIR) cluster_sync();
   if (warp == 0) {
     fence_after();
-    if constexpr (PAIR)
-      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    else
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-template <bool PAIR>
 int launch_tc32(const Maps32& m, const Tc32Params& p, uint32_t n_cols, size_t x_rows, cudaStream_t stream) {
-  using C = Cfg32<PAIR>;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(gemm_tc32_kernel<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
-  });
-  IPC_CUDA_TRY(attr);
-  const uint32_t rows_per = PAIR ? 2 * TM : TM;
-  const dim3 grid((PAIR ? 2 : 1) * ((n_cols + TN - 1) / TN), static_cast<unsigned>((x_rows + rows_per - 1) / rows_per));
-  if constexpr (PAIR) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = C::SMEM_BYTES;
-    cfg.stream = stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    IPC_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_tc32_kernel<true>, m, p));
-  } else {
-    gemm_tc32_kernel<false><<<grid, THREADS, C::SMEM_BYTES, stream>>>(m, p);
-  }
+  static PerDevice attr;
+  IPC_CUDA_TRY(attr.run(
+      [] { return cudaFuncSetAttribute(gemm_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES); }));
+  const dim3 grid((n_cols + TN - 1) / TN, static_cast<unsigned>((x_rows + TM - 1) / TM));
+  gemm_tc32_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(m, p);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
 }
@@ -483,11 +438,9 @@ int launch_tc32(const Maps32& m, const Tc32Params& p, uint32_t n_cols, size_t x_
 
 // segments: 2 for K = 2l over [x[0..3] | x[4..7]] (ABY3 replicated sharing, x[4..7] the
 // previous party's component), 1 for K = l over x[0..3] alone. K must be a multiple of 256.
-// pair: CTA pairs (256-row tiles) instead of one CTA per 128-row tile; the same z bit for bit.
-int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows, const uint16_t* const b[4],
+int ring_gemm_tc32(uint32_t segments, const int8_t* const x[8], size_t x_rows, const uint16_t* const b[4],
                    uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
-                   uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, cudaStream_t stream,
-                   bool pair) {
+                   uint64_t seed_prev, uint32_t vec, uint32_t* z, size_t ldz, uint64_t row0, cudaStream_t stream) {
   if (segments != 1 && segments != 2) {
     set_error("Z_2^32 ring GEMM: one or two K segments");
     return IPC_EINVAL;
@@ -505,13 +458,12 @@ int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows,
     set_error("Z_2^32 ring GEMM: too many rows for one launch");
     return IPC_EINVAL;
   }
-  const uint32_t hn = pair ? TN / 2 : TN;
   Maps32 m;
   int rc;
   for (int i = 0; i < LIMBS; ++i) {
-    if ((rc = make_map_bf16(&m.b[i], b[i], static_cast<uint64_t>(segments) * l, n_pad, hn)) ||
-        (rc = make_map_bf16(&m.a0[i], x[i], l, x_rows, TM)) ||
-        (rc = make_map_bf16(&m.a1[i], x[segments == 2 ? LIMBS + i : i], l, x_rows, TM)))
+    if ((rc = make_map_f16(&m.b[i], b[i], static_cast<uint64_t>(segments) * l, n_pad, TN)) ||
+        (rc = make_map_i8(&m.a0[i], x[i], l, x_rows, TM)) ||
+        (rc = make_map_i8(&m.a1[i], x[segments == 2 ? LIMBS + i : i], l, x_rows, TM)))
       return rc;
   }
   Tc32Params p;
@@ -527,7 +479,7 @@ int ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows,
   p.ldz = ldz;
   p.row0 = row0;
   p.status = status_ptr();
-  return pair ? launch_tc32<true>(m, p, n_cols, x_rows, stream) : launch_tc32<false>(m, p, n_cols, x_rows, stream);
+  return launch_tc32(m, p, n_cols, x_rows, stream);
 }
 
 int prep_query32(const uint32_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom* g, uint32_t party,
@@ -538,9 +490,14 @@ int prep_query32(const uint32_t* y, uint64_t y_plane, uint32_t Q, const ipc_geom
     set_error("Z_2^32 query operand: bad geometry, party, segments, pointers or n_pad < Q*R");
     return IPC_EINVAL;
   }
-  const uint64_t total = static_cast<uint64_t>(n_pad) * segments * l;
+  for (int i = 0; i < 4; ++i)
+    if (reinterpret_cast<uintptr_t>(b[i]) & 15u) {
+      set_error("Z_2^32 query operand: limb planes must be 16-byte aligned");
+      return IPC_EINVAL;
+    }
+  const uint64_t threads = static_cast<uint64_t>(n_pad) * segments * l / 8;
   const uint32_t bs = 256;
-  prep_query32_kernel<<<static_cast<unsigned>((total + bs - 1) / bs), bs, 0, stream>>>(
+  prep_query32_kernel<<<static_cast<unsigned>((threads + bs - 1) / bs), bs, 0, stream>>>(
       y, y_plane, Q, *g, party, segments, b[0], b[1], b[2], b[3], n_pad);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
@@ -566,18 +523,18 @@ extern "C" int ipc_encode_share32(const uint64_t* code_bits, const uint64_t* mas
   return IPC_OK;
 }
 
-extern "C" int ipc_split_limbs32_bf16(const uint32_t* x, size_t count, uint16_t* const limbs[4], void* stream) {
+extern "C" int ipc_split_limbs32(const uint32_t* x, size_t count, int8_t* const limbs[4], void* stream) {
   if (!x || !limbs || !limbs[0] || !limbs[1] || !limbs[2] || !limbs[3]) {
-    set_error("ipc_split_limbs32_bf16: null pointer");
+    set_error("ipc_split_limbs32: null pointer");
     return IPC_EINVAL;
   }
   if (!aligned16(x)) {
-    set_error("ipc_split_limbs32_bf16: x must be 16-byte aligned");
+    set_error("ipc_split_limbs32: x must be 16-byte aligned");
     return IPC_EINVAL;
   }
   for (int i = 0; i < 4; ++i)
-    if (reinterpret_cast<uintptr_t>(limbs[i]) & 7u) {
-      set_error("ipc_split_limbs32_bf16: limb planes must be 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(limbs[i]) & 3u) {
+      set_error("ipc_split_limbs32: limb planes must be 4-byte aligned");
       return IPC_EINVAL;
     }
   if (count == 0) return IPC_OK;
@@ -589,16 +546,16 @@ extern "C" int ipc_split_limbs32_bf16(const uint32_t* x, size_t count, uint16_t*
   return IPC_OK;
 }
 
-extern "C" int ipc_prep_query32_bf16(const uint32_t* y, uint32_t Q, const ipc_geom* g, uint32_t party,
-                                     uint32_t segments, uint16_t* const b[4], uint32_t n_pad, void* stream) {
+extern "C" int ipc_prep_query32_f16(const uint32_t* y, uint32_t Q, const ipc_geom* g, uint32_t party,
+                                    uint32_t segments, uint16_t* const b[4], uint32_t n_pad, void* stream) {
   const uint64_t l = g ? static_cast<uint64_t>(g->rows) * g->cols * g->cell : 0;
   return prep_query32(y, Q * l, Q, g, party, segments, b, n_pad, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8], size_t x_rows,
+extern "C" int ipc_ring_gemm_tc32(uint32_t segments, const int8_t* const x[8], size_t x_rows,
                                   const uint16_t* const b[4], uint32_t n_cols, uint32_t n_pad, uint32_t l,
                                   const uint32_t* col_tags, uint64_t seed_own, uint64_t seed_prev, uint32_t vec,
-                                  uint32_t* z, size_t ldz, uint64_t row0, uint32_t pair, void* stream) {
+                                  uint32_t* z, size_t ldz, uint64_t row0, void* stream) {
   if (!x || !b || !col_tags || !z) {
     set_error("ipc_ring_gemm_tc32: null pointer");
     return IPC_EINVAL;
@@ -613,6 +570,10 @@ extern "C" int ipc_ring_gemm_tc32(uint32_t segments, const uint16_t* const x[8],
     set_error("ipc_ring_gemm_tc32: x_rows above IPC_MAX_GEMM_ROWS");
     return IPC_EINVAL;
   }
+  if (l % 16 != 0) {
+    set_error("ipc_ring_gemm_tc32: l must be a multiple of 16");
+    return IPC_EINVAL;
+  }
   return ring_gemm_tc32(segments, x, x_rows, b, n_cols, n_pad, l, col_tags, seed_own, seed_prev, vec, z, ldz, row0,
-                        static_cast<cudaStream_t>(stream), pair != 0);
+                        static_cast<cudaStream_t>(stream));
 }

@@ -163,7 +163,7 @@ int pick_variant(const Server& S, uint32_t active_cols) {
   } while (0)
 
 uint8_t* bq_plane(const Server& S, int party, int vec, int limb) {
-  return S.bq + static_cast<size_t>((party * 2 + vec) * 2 + limb) * S.pool_pad * S.c->kq * S.c->esz;
+  return S.bq + static_cast<size_t>((party * 2 + vec) * 2 + limb) * S.pool_pad * S.c->kq * S.c->qsz;
 }
 
 uint16_t* z_plane(const Server& S, int vec, int party) {
@@ -182,8 +182,9 @@ int gemm(Server& S, int v, const Chunk& ch, int party, int vec, cudaStream_t st)
     const bool gal = c->cfg.path == IPC_PATH_TCG;
     const int other = gal ? party : prev;
     auto p16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
-    const uint16_t* xl[2] = {p16(ctx_plane(c, ch, party, vec, 0)), p16(ctx_plane(c, ch, other, vec, 0))};
-    const uint16_t* xh[2] = {p16(ctx_plane(c, ch, party, vec, 1)), p16(ctx_plane(c, ch, other, vec, 1))};
+    auto p8 = [](const uint8_t* p) { return reinterpret_cast<const int8_t*>(p); };
+    const int8_t* xl[2] = {p8(ctx_plane(c, ch, party, vec, 0)), p8(ctx_plane(c, ch, other, vec, 0))};
+    const int8_t* xh[2] = {p8(ctx_plane(c, ch, party, vec, 1)), p8(ctx_plane(c, ch, other, vec, 1))};
     return ring_gemm_tc_variant(V.tile_cols, gal ? 1 : 2, xl, xh, ch.rows, p16(bq_plane(S, party, vec, 0)),
                                 p16(bq_plane(S, party, vec, 1)), S.pool_pad, S.pool_pad, c->l, S.tags,
                                 c->cfg.seeds[party], c->cfg.seeds[prev], static_cast<uint32_t>(vec), zo, ldz, ch.row0,
@@ -270,7 +271,7 @@ int admit(Server& S, SReq* r) {
                               cudaMemcpyHostToDevice, c->sc));
   SRV_TRY(cudaMemcpyAsync(S.tags + 2ull * col0, r->tags.data(), r->tags.size() * sizeof(uint32_t),
                           cudaMemcpyHostToDevice, c->sc));
-  const size_t row_bytes = static_cast<size_t>(c->kq) * c->esz;
+  const size_t row_bytes = static_cast<size_t>(c->kq) * c->qsz;
   for (int i = 0; i < 3; ++i)
     for (int vec = 0; vec < 2; ++vec) {
       const uint16_t* y = S.ystage + (static_cast<size_t>(vec) * 3 * S.slots + r->slot0) * l;
@@ -279,7 +280,7 @@ int admit(Server& S, SReq* r) {
       if (c->cfg.path == IPC_PATH_TCG)
         SRV_RC(prep_query_galois_strided(y, static_cast<uint64_t>(S.slots) * l, r->Q, &c->cfg.geom, i,
                                          reinterpret_cast<uint16_t*>(lo), reinterpret_cast<uint16_t*>(hi), r->N, c->sc));
-      else if (c->esz == 2)
+      else if (c->qsz == 2)
         SRV_RC(prep_query_strided<uint16_t>(y, static_cast<uint64_t>(S.slots) * l, r->Q, &c->cfg.geom, i,
                                             reinterpret_cast<uint16_t*>(lo), reinterpret_cast<uint16_t*>(hi), r->N,
                                             c->sc, "serving admission"));
@@ -529,7 +530,7 @@ void free_server(Server* S) {
 // Per query slot: R columns of B planes (12 x 2l limbs), of z (6 x chunk rows) and of roots
 // (3 x ld_roots), the slot's query shares (6 x l) and bit components.
 size_t bytes_per_slot(const ipc_ctx* c, uint32_t R, size_t ld_roots) {
-  const size_t per_col = 12ull * c->kq * c->esz + 6ull * c->cfg.db_chunk_rows * 2 + 3ull * ld_roots * 4 + 8;
+  const size_t per_col = 12ull * c->kq * c->qsz + 6ull * c->cfg.db_chunk_rows * 2 + 3ull * ld_roots * 4 + 8;
   return R * per_col + 6ull * c->l * 2 + 3;
 }
 
@@ -630,7 +631,7 @@ extern "C" int ipc_serve_start(ipc_ctx* c, const ipc_serve_config* cfg) {
   S.slot_used.assign(slots, 0);
   S.variant_steps.assign(S.n_variants, 0);
   const size_t l = c->l;
-  bool ok = cudaMalloc(&S.bq, 12ull * S.pool_pad * c->kq * c->esz) == cudaSuccess &&
+  bool ok = cudaMalloc(&S.bq, 12ull * S.pool_pad * c->kq * c->qsz) == cudaSuccess &&
             cudaMalloc(&S.ystage, 6ull * slots * l * sizeof(uint16_t)) == cudaSuccess &&
             cudaMalloc(&S.tags, 2ull * S.pool_pad * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&S.roots, 3ull * S.pool_pad * S.ld_roots * sizeof(uint32_t)) == cudaSuccess &&
@@ -658,7 +659,7 @@ extern "C" int ipc_serve_start(ipc_ctx* c, const ipc_serve_config* cfg) {
   }
   // every pool byte defined (tiles of partly used columns compute on them); tags of unused
   // columns are request id 0
-  ok = cudaMemsetAsync(S.bq, 0, 12ull * S.pool_pad * c->kq * c->esz, c->sc) == cudaSuccess &&
+  ok = cudaMemsetAsync(S.bq, 0, 12ull * S.pool_pad * c->kq * c->qsz, c->sc) == cudaSuccess &&
        cudaMemsetAsync(S.tags, 0, 2ull * S.pool_pad * sizeof(uint32_t), c->sc) == cudaSuccess &&
        cudaMemsetAsync(S.z, 0, 6ull * S.pool_pad * c->cfg.db_chunk_rows * sizeof(uint16_t), c->sc) == cudaSuccess;
   for (int v = 0; v < S.n_variants && ok; ++v) ok = cudaMemsetAsync(S.count_dev[v], 0, 4, c->sc) == cudaSuccess;

@@ -1,6 +1,7 @@
 // Device helpers shared by the tcgen05 kernels: mbarriers with bounded waits, TMA tile loads,
 // shared-memory matrix descriptors (K-major, 64-byte swizzle), tcgen05.mma / commit / fences,
-// tensor-memory loads and stores, and the host-side tensor-map encoder.
+// tensor-memory loads and stores, the widening of int8 limb tiles to fp16 in shared memory, and
+// the host-side tensor-map encoders.
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -136,6 +137,70 @@ __device__ __forceinline__ uint32_t pack_c16(uint32_t x, uint32_t y) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// Orders this thread's generic-proxy shared-memory writes before later async-proxy reads
+// (tcgen05.mma operands), once the writer's mbarrier arrive has been observed.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+
+__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+// Two int8 limbs (bytes 2i, 2i+1 of the word, selected by SEL) as two fp16 values, exactly:
+// with the sign bit flipped a byte is u = v + 128 in [0, 255], the fp16 pattern 0x6400 | u is
+// 1024 + u (exponent 10, u in the low mantissa bits), and subtracting 1152 leaves v, an integer
+// far inside fp16's 11-bit significand, so the subtraction is exact.
+template <uint32_t SEL>
+__device__ __forceinline__ uint32_t widen2(uint32_t flipped) {
+  uint32_t h, d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(h) : "r"(flipped), "r"(0x64646464u), "n"(SEL));
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(h), "r"(0x64806480u));  // (1024 + u) - 1152
+  return d;
+}
+
+// Sixteen int8 limbs (one 16-byte raw chunk, K order) -> the two 16-byte fp16 chunks of the
+// same sixteen elements.
+__device__ __forceinline__ void widen16(uint4 raw, uint4& c0, uint4& c1) {
+  const uint32_t a = raw.x ^ 0x80808080u, b = raw.y ^ 0x80808080u, c = raw.z ^ 0x80808080u,
+                 d = raw.w ^ 0x80808080u;
+  c0 = make_uint4(widen2<0x4140>(a), widen2<0x4342>(a), widen2<0x4140>(b), widen2<0x4342>(b));
+  c1 = make_uint4(widen2<0x4140>(c), widen2<0x4342>(c), widen2<0x4140>(d), widen2<0x4342>(d));
+}
+
+// Widens `planes` raw database tiles of a stage to the MMA's operand layout. A raw tile is
+// [128 rows][32] int8, rows 32 bytes apart (TMA, no swizzle); its widened tile is [128][32]
+// fp16 in the 64-byte swizzled K-major layout that TMA would have written for an fp16 box:
+// row r at r * 64, its 16-byte chunk c (elements 8c..8c+7) at chunk position c ^ ((r >> 1) & 3).
+// `ct` in [0, nthreads) numbers the widening threads; each takes rows (ct >> 1) + 32 j, half
+// ct & 1 (16 elements), so its swizzle term (ct >> 2) & 3 is fixed.
+template <int PLANES, int NTHREADS>
+__device__ __forceinline__ void widen_tiles(uint32_t raw, uint32_t raw_stride, uint32_t dst, uint32_t dst_stride,
+                                            uint32_t ct) {
+  static_assert(NTHREADS == 64 || NTHREADS == 128, "two or four widening warps");
+  constexpr int JOBS = PLANES * 256 / NTHREADS;   // 16-element jobs per thread
+  constexpr int ROWS_STEP = NTHREADS / 2;           // rows between a thread's jobs in one plane
+  constexpr int PER_PLANE = 128 / ROWS_STEP;        // jobs per plane
+  const uint32_t h = ct & 1u, r0 = ct >> 1, sw = (ct >> 2) & 3u;
+  const uint32_t o0 = ((2u * h) ^ sw) * 16u, o1 = ((2u * h + 1u) ^ sw) * 16u;
+  uint4 v[JOBS];
+#pragma unroll
+  for (int j = 0; j < JOBS; ++j)
+    v[j] = lds128(raw + (j / PER_PLANE) * raw_stride + (r0 + ROWS_STEP * (j % PER_PLANE)) * 32u + 16u * h);
+#pragma unroll
+  for (int j = 0; j < JOBS; ++j) {
+    uint4 c0, c1;
+    widen16(v[j], c0, c1);
+    const uint32_t row = dst + (j / PER_PLANE) * dst_stride + (r0 + ROWS_STEP * (j % PER_PLANE)) * 64u;
+    sts128(row + o0, c0.x, c0.y, c0.z, c0.w);
+    sts128(row + o1, c1.x, c1.y, c1.z, c1.w);
+  }
+}
+
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -154,10 +219,10 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Bf16 tensor [rows][cols] (row stride cols * 2 bytes) as a TMA tensor map: box 32 elements (one
-// 64-byte swizzled row) x box_rows, 64-byte swizzle, zero fill outside the tensor (ragged row
-// tails and query rows past n_pad).
-inline int make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+// fp16 tensor [rows][cols] (row stride cols * 2 bytes) as a TMA tensor map: box 32 elements
+// (one 64-byte swizzled row) x box_rows, 64-byte swizzle, zero fill outside the tensor (query
+// rows past n_pad).
+inline int make_map_f16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -167,14 +232,67 @@ inline int make_map_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint
   cuuint64_t strides[1] = {cols * 2};
   cuuint32_t box[2] = {32, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled (bf16) failed with CUresult " + std::to_string(static_cast<int>(r)));
+    set_error("cuTensorMapEncodeTiled (fp16) failed with CUresult " + std::to_string(static_cast<int>(r)));
     return IPC_ECUDA;
   }
   return IPC_OK;
+}
+
+// int8 limb plane [rows][cols] (row stride cols bytes, a multiple of 16) as a TMA tensor map:
+// box 32 bytes x box_rows, no swizzle (rows 32 bytes apart in shared memory), zero fill past the
+// last row (ragged row tails).
+inline int make_map_i8(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return IPC_ECUDA;
+  }
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (int8) failed with CUresult " + std::to_string(static_cast<int>(r)));
+    return IPC_ECUDA;
+  }
+  return IPC_OK;
+}
+
+// Runs a set-up step (a kernel attribute) once per device: attributes belong to the device's
+// context, so a process that drives several devices needs it on each.
+class PerDevice {
+ public:
+  template <class F>
+  cudaError_t run(F&& f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu_);
+    if (dev >= 0 && dev < 64 && ((done_ >> dev) & 1u)) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done_ |= 1ull << dev;
+    return e;
+  }
+
+ private:
+  std::mutex mu_;
+  uint64_t done_ = 0;
+};
+
+// Number of SMs of the current device.
+inline int sm_count_current() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0)
+    return 1;
+  return n;
 }
 
 }  // namespace tc

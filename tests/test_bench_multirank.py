@@ -25,7 +25,7 @@ def _rank(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         import bench
-        ms = bench.max_over_ranks(10.0 + 5.0 * rank, device="cpu")
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank)
         rate = bench.whole_job_rate(1000.0, world, ms)
         out = io.StringIO()
         with redirect_stdout(out):   # the reference arm: ranks other than 0 leave without work
@@ -58,5 +58,5 @@ def test_two_gloo_ranks():
 def test_single_process_needs_no_group():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.max_over_ranks(3.5, device="cpu") == 3.5
+    assert bench.max_over_ranks(3.5) == 3.5
     assert bench.whole_job_rate(99.2e6, 1, 56.0) == pytest.approx(99.2e6 / 0.056)

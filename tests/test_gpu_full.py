@@ -160,11 +160,13 @@ def hdi_frac(dot, ml):
 
 
 def test_planted_workload_full_size():
-    """500,000 rows x 64 queries x 31 rotations (992 M comparisons), half the queries planted."""
-    _full_size("c3", keep=True)
+    """500,000 rows x 64 queries x 31 rotations (992 M comparisons), half the queries planted; in
+    the benchmark's configuration (messages not kept: double-buffered dot-product scratch)."""
+    _full_size("c3", keep=False)
 
 
 def test_largest_workload_full_size():
-    """600,000 rows (184 GB of resident bf16 limb planes) x 256 queries x 31 rotations (4.76 G
-    comparisons), 13 planted near-duplicates at 5-15% flipped bits."""
-    _full_size("c5", keep=False)
+    """600,000 rows (92 GB of resident int8 limb planes, the size of the u16 shares) x 256 queries
+    x 31 rotations (4.76 G comparisons), 13 planted near-duplicates at 5-15% flipped bits; the
+    messages are kept, so the planted columns' distances are checked row by row too."""
+    _full_size("c5", keep=True)

@@ -52,21 +52,22 @@ def test_split_limbs_exhaustive(torch):
     assert lo_.min() >= -128 and lo_.max() <= 127 and hi_.min() >= -128 and hi_.max() <= 127
 
 
-def test_split_limbs_bf16_exhaustive(torch):
-    """The bf16 limbs of the tensor-core path are the int8 limbs, exactly, for all 65536 values."""
+def test_prep_query_f16_is_the_int8_operand(small, torch):
+    """The tcgen05 path's query operand is the int8 operand of ipc_prep_query, each limb as the
+    fp16 pattern of its integer value, exactly (every row, padding rows included)."""
     ipc = lib()
-    x = torch.arange(65536, dtype=torch.int32).to(torch.int16).cuda()
-    lo8 = torch.empty(65536, dtype=torch.int8, device="cuda")
-    hi8 = torch.empty(65536, dtype=torch.int8, device="cuda")
-    ipc.ipc_split_limbs(x, 65536, lo8, hi8)
-    lo = torch.empty(65536, dtype=torch.int16, device="cuda")
-    hi = torch.empty(65536, dtype=torch.int16, device="cuda")
-    ipc.ipc_split_limbs_bf16(x, 65536, lo, hi)
-    lof = lo.view(torch.bfloat16).float().cpu().numpy()
-    hif = hi.view(torch.bfloat16).float().cpu().numpy()
-    assert (lof == lo8.cpu().numpy().astype(np.float32)).all()
-    assert (hif == hi8.cpu().numpy().astype(np.float32)).all()
-    assert ((256 * hif.astype(np.int64) + lof.astype(np.int64)) & 0xFFFF == np.arange(65536)).all()
+    g = ipc.iris_geom()
+    y = torch.from_numpy(small["qsc"].view(np.int16).copy()).cuda()
+    n_pad = 256
+    for party in range(3):
+        lo8 = torch.empty((n_pad, 2 * L), dtype=torch.int8, device="cuda")
+        hi8 = torch.empty((n_pad, 2 * L), dtype=torch.int8, device="cuda")
+        ipc.ipc_prep_query(y, 5, g, party, lo8, hi8, n_pad)
+        lo = torch.empty((n_pad, 2 * L), dtype=torch.int16, device="cuda")
+        hi = torch.empty((n_pad, 2 * L), dtype=torch.int16, device="cuda")
+        ipc.ipc_prep_query_f16(y, 5, g, party, lo, hi, n_pad)
+        assert (lo.view(torch.float16).float() == lo8.float()).all()
+        assert (hi.view(torch.float16).float() == hi8.float()).all()
 
 
 def test_encode_share_matches_oracle(small):
@@ -111,16 +112,16 @@ def test_prep_query_is_rotated_aby3_operand(small, torch):
         assert (rebuilt[Q * R:] == 0).all()
 
 
-def _planes(torch, shares, bf16=False):
-    """[3][n][l] uint16 numpy -> per component (lo, hi) device limb planes via the C ABI
-    (int8, or bf16 bit patterns for the tensor-core path)."""
+def _planes(torch, shares):
+    """[3][n][l] uint16 numpy -> per component (lo, hi) device int8 limb planes via the C ABI (the
+    resident database layout of every path)."""
     ipc = lib()
     out = []
     for j in range(3):
         x = torch.from_numpy(shares[j].view(np.int16).copy()).cuda()
-        lo = torch.empty(x.shape, dtype=torch.int16 if bf16 else torch.int8, device="cuda")
-        hi = torch.empty(x.shape, dtype=torch.int16 if bf16 else torch.int8, device="cuda")
-        (ipc.ipc_split_limbs_bf16 if bf16 else ipc.ipc_split_limbs)(x, x.numel(), lo, hi)
+        lo = torch.empty(x.shape, dtype=torch.int8, device="cuda")
+        hi = torch.empty(x.shape, dtype=torch.int8, device="cuda")
+        ipc.ipc_split_limbs(x, x.numel(), lo, hi)
         out.append((lo, hi))
     return out
 
@@ -137,14 +138,14 @@ def _gemm_all(torch, small, path):
     out = []
     tc = path == "tc"
     for vec, (db, qs) in enumerate(((small["dbc"], small["qsc"]), (small["dbm"], small["qsm"]))):
-        planes = _planes(torch, db, bf16=tc)
+        planes = _planes(torch, db)
         y = torch.from_numpy(qs.view(np.int16).copy()).cuda()
         z = torch.zeros((3, N, ldz), dtype=torch.int16, device="cuda")
         for i in range(3):
             prev = (i + 2) % 3
             blo = torch.empty((n_pad, 2 * L), dtype=torch.int16 if tc else torch.int8, device="cuda")
             bhi = torch.empty((n_pad, 2 * L), dtype=torch.int16 if tc else torch.int8, device="cuda")
-            (ipc.ipc_prep_query_bf16 if tc else ipc.ipc_prep_query)(y, Q, g, i, blo, bhi, n_pad)
+            (ipc.ipc_prep_query_f16 if tc else ipc.ipc_prep_query)(y, Q, g, i, blo, bhi, n_pad)
             xl, xh = [planes[i][0], planes[prev][0]], [planes[i][1], planes[prev][1]]
             if tc:
                 ipc.ipc_ring_gemm_tc(xl, xh, s, blo, bhi, N, n_pad, L, tags, w.prf_seeds[i], w.prf_seeds[prev], vec,
@@ -326,18 +327,15 @@ def test_gemm_exact_at_max_length_and_extreme_limbs(torch):
     y = torch.full((3, Q, Lm), 0x7F80, dtype=torch.int32).to(torch.int16).cuda()
     y[2] = 0  # party 0's operand is [y_0 + y_2 | y_0] = [0x7F80 | 0x7F80]: C reaches 2l * 2 * 128^2 = 2^30
     tags = torch.from_numpy(tags_for(1, Q, R).view(np.int32)).cuda()
-    lo16 = torch.empty((s, Lm), dtype=torch.int16, device="cuda")
-    hi16 = torch.empty((s, Lm), dtype=torch.int16, device="cuda")
-    ipc.ipc_split_limbs_bf16(x, x.numel(), lo16, hi16)
     res = {}
     for path in ("i8mma", "i8mix", "i32", "tc"):
         tc = path == "tc"
         blo = torch.empty((128, 2 * Lm), dtype=torch.int16 if tc else torch.int8, device="cuda")
         bhi = torch.empty((128, 2 * Lm), dtype=torch.int16 if tc else torch.int8, device="cuda")
-        (ipc.ipc_prep_query_bf16 if tc else ipc.ipc_prep_query)(y, Q, g, 0, blo, bhi, 128)
+        (ipc.ipc_prep_query_f16 if tc else ipc.ipc_prep_query)(y, Q, g, 0, blo, bhi, 128)
         z = torch.zeros((Q * R, 136), dtype=torch.int16, device="cuda")
         if tc:
-            ipc.ipc_ring_gemm_tc([lo16, lo16], [hi16, hi16], s, blo, bhi, Q * R, 128, Lm, tags, 0, 0, 0, z, 136, 0)
+            ipc.ipc_ring_gemm_tc([lo, lo], [hi, hi], s, blo, bhi, Q * R, 128, Lm, tags, 0, 0, 0, z, 136, 0)
         else:
             ipc.ipc_ring_gemm(path, [lo, lo], [hi, hi], s, blo, bhi, Q * R, 128, Lm, tags, 0, 0, 0, z, 136, 0)
         torch.cuda.synchronize()
@@ -426,9 +424,10 @@ def test_gemm_variants_and_tile_lists_match_int32(torch, variant):
             assert (z2[cols] == 77).all(), t
 
 
-def _bf16(torch, t):
-    """int8 limb tensor -> the bf16 bit patterns of the same integers (test-side conversion)."""
-    return t.float().to(torch.bfloat16).view(torch.int16).contiguous()
+def _f16(torch, t):
+    """int8 limb tensor -> the fp16 bit patterns of the same integers (test-side conversion of the
+    query operand)."""
+    return t.to(torch.float16).view(torch.int16).contiguous()
 
 
 @pytest.mark.parametrize("rows,N,row0", [(1000, 300, 8), (128, 256, 0), (4097, 31, 65536)])
@@ -446,42 +445,12 @@ def test_tc_gemm_matches_int32_on_random_limbs(torch, rows, N, row0):
     ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
     ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, ref, ldz, row0)
     z = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
-    p16 = [_bf16(torch, t) for t in planes]
-    ipc.ipc_ring_gemm_tc(p16[0:2], p16[2:4], rows, _bf16(torch, blo), _bf16(torch, bhi), N, n_pad, L, tags, 5, 6, 1,
-                         z, ldz, row0)
+    ipc.ipc_ring_gemm_tc(planes[0:2], planes[2:4], rows, _f16(torch, blo), _f16(torch, bhi), N, n_pad, L, tags, 5, 6,
+                         1, z, ldz, row0)
     torch.cuda.synchronize()
     ipc.ipc_status()
     assert (z.cpu()[:, :rows] == ref.cpu()[:, :rows]).all()
     assert (z.cpu()[:, rows:] == 77).all()
-
-
-@pytest.mark.parametrize("rows,N,row0", [(300, 155, 0), (1000, 700, 1024), (4096, 992, 65536)])
-def test_tc_pair_matches_single_cta_and_int32(torch, rows, N, row0):
-    """The CTA-pair kernel (cta_group::2, 256-row x 256-column tiles) equals the single-CTA
-    tcgen05 kernel and the int32 path: a row pair whose second CTA is past the last row, ragged
-    column pairs, a row offset past the first chunk."""
-    ipc = lib()
-    n_pad = (N + 127) // 128 * 128
-    g = torch.Generator(device="cpu").manual_seed(rows + 3 * N)
-    planes = [torch.randint(-128, 128, (rows, L), dtype=torch.int8, generator=g).cuda() for _ in range(4)]
-    blo = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
-    bhi = torch.randint(-128, 128, (n_pad, 2 * L), dtype=torch.int8, generator=g).cuda()
-    tags = torch.from_numpy(tags_for(9, (N + 30) // 31, 31).view(np.int32)).cuda()
-    ldz = (rows + 7) // 8 * 8
-    ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
-    ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 1, ref, ldz, row0)
-    p16 = [_bf16(torch, t) for t in planes]
-    b16 = [_bf16(torch, blo), _bf16(torch, bhi)]
-    single = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
-    ipc.ipc_ring_gemm_tc(p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 1, single, ldz, row0)
-    pair = torch.full((N, ldz), 77, dtype=torch.int16, device="cuda")
-    ipc.ipc_ring_gemm_tc_pair(p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 1, pair, ldz, row0)
-    torch.cuda.synchronize()
-    ipc.ipc_status()
-    pair, single, ref = pair.cpu(), single.cpu(), ref.cpu()
-    assert (pair[:, :rows] == ref[:, :rows]).all()
-    assert (pair == single).all()
-    assert (pair[:, rows:] == 77).all()
 
 
 @pytest.mark.parametrize("tile_cols", [256, 128])
@@ -498,8 +467,8 @@ def test_tc_tile_lists_match_int32(torch, tile_cols):
     ldz = 1000
     ref = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
     ipc.ipc_ring_gemm("i32", planes[0:2], planes[2:4], rows, blo, bhi, N, n_pad, L, tags, 5, 6, 0, ref, ldz, 16)
-    p16 = [_bf16(torch, t) for t in planes]
-    b16 = [_bf16(torch, blo), _bf16(torch, bhi)]
+    p16 = planes
+    b16 = [_f16(torch, blo), _f16(torch, bhi)]
     z = torch.zeros((N, ldz), dtype=torch.int16, device="cuda")
     ipc.ipc_ring_gemm_tc_tiles(tile_cols, p16[0:2], p16[2:4], rows, b16[0], b16[1], N, n_pad, L, tags, 5, 6, 0, z,
                                ldz, 16)
@@ -569,8 +538,8 @@ def test_prep_query_galois_is_lambda_times_rotated_share(small, small_galois, to
         lo = torch.empty((n_pad, L), dtype=torch.int16, device="cuda")
         hi = torch.empty((n_pad, L), dtype=torch.int16, device="cuda")
         ipc.ipc_prep_query_galois(y, Q, g, party, lo, hi, n_pad)
-        lof = lo.view(torch.bfloat16).float().cpu().numpy().astype(np.int64)
-        hif = hi.view(torch.bfloat16).float().cpu().numpy().astype(np.int64)
+        lof = lo.view(torch.float16).float().cpu().numpy().astype(np.int64)
+        hif = hi.view(torch.float16).float().cpu().numpy().astype(np.int64)
         rebuilt = (256 * hif + lof) & 0xFFFF
         l0, l1 = lam[party]
         for q in (0, 4):
@@ -593,7 +562,7 @@ def test_ring_gemm_galois_matches_oracle_shares(small, small_galois, torch):
     tags = torch.from_numpy(tags_for(REQ, Q, R).view(np.int32)).cuda()
     for vec, (db, qs, key) in enumerate(((small_galois["dbc"], small_galois["qsc"], "z_code"),
                                          (small_galois["dbm"], small_galois["qsm"], "z_mask"))):
-        planes = _planes(torch, db, bf16=True)
+        planes = _planes(torch, db)
         y = torch.from_numpy(qs.view(np.int16).copy()).cuda()
         z = torch.zeros((3, N, ldz), dtype=torch.int16, device="cuda")
         for i in range(3):
