@@ -17,17 +17,21 @@
 // The database stays resident as int8 limb planes (the size of its u16 shares): TMA brings each
 // k-block's raw int8 tiles into shared memory and two widening warps rewrite them as fp16 tiles
 // in the MMA's swizzled layout, next to the query tiles (already fp16, prepared per request).
+// Three rings decouple the steps, so that the widening never sits on the MMA's critical path:
+//   Q ring (QS stages)  query lo/hi tiles, TN x 32 fp16 each, 64-byte swizzle (TMA);
+//   R ring (RS stages)  raw database lo/hi tiles, 128 x 32 int8 each (TMA);
+//   W ring (WS stages)  widened database lo/hi tiles, 128 x 32 fp16 each (widening warps).
+// Each widening warp owns one limb plane: it issues that plane's raw copies itself, RS k-blocks
+// ahead, and widens them into the W ring up to WS - 1 k-blocks ahead of the MMAs; the two warps
+// never wait for each other.
 //
-// Pipeline (one CTA per tile of 128 database rows x TN query columns, 12 warps):
-//   warp 0 lane 0  TMA producer: per k-block of 32 elements, four tiles (raw database lo/hi
-//                  128 x 32 int8, query lo/hi TN x 32 fp16 with 64-byte swizzle) into a 4-stage
-//                  ring.
-//   warps 10-11    widening: per k-block, once the stage's copies have landed, the two raw
-//                  database tiles become 128 x 32 fp16 tiles in the same stage.
+// Roles (one CTA per tile of 128 database rows x TN query columns, 12 warps):
+//   warp 0 lane 0  query producer: per k-block of 32 elements, the two query tiles.
+//   warps 10-11    raw copies and widening of the lo (warp 10) and hi (warp 11) limb plane.
 //   warp 1 lane 0  MMA issuer: per chunk of four k-blocks, the C products (2 MMAs of 128xTNx16
 //                  per 16 k) with the L products (1 MMA per 16 k) one k-block behind, committing
-//                  C-full after the last C k-block, stage-empty after each L k-block, and L-full
-//                  after every second chunk.
+//                  C-full after the last C k-block, the k-block's Q and W stages after its L
+//                  products, and L-full after every second chunk.
 //   warps 2-9      drain: each thread owns one TMEM lane (database row) and TN/2 columns, their
 //                  running sums kept mod 2^16 two to a register; after C-full it reads C, adds
 //                  C << 8 to the sums and stores M back, and likewise for L after L-full. C is
@@ -46,7 +50,8 @@ using namespace tc;
 
 constexpr int TM = 128;          // database rows per tile (MMA M = TMEM lanes)
 constexpr int KB = 32;           // elements of K per stage: one 64-byte swizzled fp16 row
-constexpr int STAGES = 4;
+constexpr int QS = 4, WS = QS, RS = 4;  // stages of the query, widened and raw rings
+static_assert(WS == QS, "a k-block's Q and W stages are released by one commit");
 constexpr int KB_PER_CHUNK = 4;  // k-blocks per accumulator chunk (128 k)
 static_assert(KB_PER_CHUNK >= 2, "the L products lag the C products by one k-block");
 constexpr int A_BYTES = TM * KB * 2;  // 8 KiB widened (fp16) database tile
@@ -54,20 +59,21 @@ constexpr int A_RAW = TM * KB;        // 4 KiB raw (int8) database tile
 constexpr int THREADS = 12 * 32;
 constexpr int DRAIN_THREADS = 8 * 32;
 constexpr int WIDEN_WARP0 = 10, WIDEN_THREADS = 2 * 32;
-// full[S], empty[S], wide[S], c_full, c_empty, l_full, l_empty, done, epi_done
-constexpr int NUM_BARS = 3 * STAGES + 6;
+// q_full[QS], q_empty[QS] (also the W stages' release), w_full[WS], r_full[2][RS] (per plane),
+// c_full, c_empty, l_full, l_empty, done, epi_done
+constexpr int NUM_BARS = 2 * QS + WS + 2 * RS + 6;
 constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
 
-// Tile shape: TN query columns per tile (MMA N = 256 or 128). A stage holds, 1024-byte aligned:
-// widened database lo, hi (A_BYTES each), query lo, hi (B_BYTES each), raw database lo, hi.
+// Tile shape: TN query columns per tile (MMA N = 256 or 128). Shared memory, 1024-byte aligned:
+// the Q ring (first: the epilogue stages z there), the W ring, the R ring, the barriers.
 template <int TN>
 struct Shape {
   static_assert(TN == 256 || TN == 128, "tile width");
   static constexpr int B_BYTES = TN * KB * 2;
-  static constexpr int RAW_OFF = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGE_BYTES = RAW_OFF + 2 * A_RAW;  // 56 or 40 KiB
-  static_assert(STAGE_BYTES % 1024 == 0, "stage tiles stay 1024-byte aligned");
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NUM_BARS;
+  static constexpr int Q_STAGE = 2 * B_BYTES, W_STAGE = 2 * A_BYTES, R_STAGE = 2 * A_RAW;
+  static constexpr int W_OFF = QS * Q_STAGE, R_OFF = W_OFF + WS * W_STAGE, BAR_OFF = R_OFF + RS * R_STAGE;
+  static_assert(Q_STAGE % 1024 == 0 && W_STAGE % 1024 == 0 && R_STAGE % 1024 == 0, "aligned stages");
+  static constexpr int SMEM_BYTES = BAR_OFF + 1024 + 8 * NUM_BARS;
   static_assert(SMEM_BYTES <= 232448, "dynamic shared memory per block");
   static constexpr uint32_t TMEM_COLS = 2 * TN;  // L in [0, TN), C in [TN, 2 TN)
   static constexpr uint32_t TMEM_C = TN;
@@ -77,8 +83,8 @@ struct Shape {
   // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
   static constexpr uint32_t IDESC =
       (1u << 4) | (static_cast<uint32_t>(TN >> 3) << 17) | (static_cast<uint32_t>(TM >> 4) << 24);
-  // z of one tile, [TN][TM] uint16, staged in the (then idle) stage ring
-  static_assert(TN * TM * 2 <= STAGES * STAGE_BYTES, "z tile must fit the stage ring");
+  // z of one tile, [TN][TM] uint16, staged in the (then idle) Q ring
+  static_assert(TN * TM * 2 <= QS * Q_STAGE, "z tile must fit the Q ring");
 };
 
 struct TcParams {
@@ -101,7 +107,8 @@ struct TcParams {
 // Without a list (LIST false) the grid is (column tiles, row tiles), one tile per CTA. With a list,
 // gridDim.x persistent CTAs walk items w = blockIdx.x + i * gridDim.x: column tile
 // list[w % n_ct], row tile w / n_ct; k-block and chunk counters run on across items, and the
-// producer starts an item's copies once the previous item's epilogue has left the stage ring.
+// query producer starts an item's copies once the previous item's epilogue has left the Q ring
+// (the raw and widened rings run on into the next item meanwhile).
 template <int TN, bool LIST>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tb_lo, const __grid_constant__ CUtensorMap tb_hi,
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                    const __grid_constant__ CUtensorMap ta1_lo, const __grid_constant__ CUtensorMap ta1_hi,
                    const TcParams p) {
   using S = Shape<TN>;
-  constexpr int B_BYTES = S::B_BYTES, STAGE_BYTES = S::STAGE_BYTES;
+  constexpr int B_BYTES = S::B_BYTES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ uint32_t s_abort;
@@ -139,21 +146,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     d0 = (in_band / width) * TM;
   };
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t tiles = smem_addr(smem);
-  const uint32_t bars = tiles + STAGES * STAGE_BYTES;
-  const uint32_t full0 = bars, empty0 = bars + 8 * STAGES, wide0 = bars + 16 * STAGES;
-  const uint32_t c_full = bars + 24 * STAGES, c_empty = c_full + 8, l_full = c_full + 16, l_empty = c_full + 24,
+  const uint32_t qring = smem_addr(smem), wring = qring + S::W_OFF, rring = qring + S::R_OFF;
+  const uint32_t bars = qring + S::BAR_OFF;
+  const uint32_t q_full = bars, q_empty = q_full + 8 * QS, w_full = q_empty + 8 * QS, r_full = w_full + 8 * WS;
+  const uint32_t c_full = r_full + 16 * RS, c_empty = c_full + 8, l_full = c_full + 16, l_empty = c_full + 24,
                  done_bar = c_full + 32, epi_done = c_full + 40;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;  // even: l is a multiple of 128
+  const uint32_t total_kb = my_items * p.kb_total;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
-      mbar_init(wide0 + 8 * s, WIDEN_THREADS / 32);
+    for (int s = 0; s < QS; ++s) {
+      mbar_init(q_full + 8 * s, 1);
+      mbar_init(q_empty + 8 * s, 1);
     }
+    for (int s = 0; s < WS; ++s) mbar_init(w_full + 8 * s, WIDEN_THREADS / 32);
+    for (int s = 0; s < 2 * RS; ++s) mbar_init(r_full + 8 * s, 1);
     mbar_init(c_full, 1);
     mbar_init(c_empty, DRAIN_THREADS / 32);
     mbar_init(l_full, 1);
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = s_tmem;
 
   if (warp == 0) {
-    // ------------------------------- TMA producer -------------------------------
+    // ---------------------------- query TMA producer -----------------------------
     if (lane == 0) {
       uint32_t issued = 0;
       bool ok = true;
@@ -184,26 +193,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         coords(i, q0, d0);
         if (i > 0 && !mbar_wait(epi_done, (i - 1) & 1u, p.status, abort)) break;
         for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
-          const uint32_t G = i * p.kb_total + kb, s = G % STAGES;
-          if (!mbar_wait(empty0 + 8 * s, ((G / STAGES) & 1u) ^ 1u, p.status, abort)) {
+          const uint32_t G = i * p.kb_total + kb, s = G % QS;
+          if (!mbar_wait(q_empty + 8 * s, ((G / QS) & 1u) ^ 1u, p.status, abort)) {
             ok = false;
             break;
           }
-          const uint32_t full = full0 + 8 * s, base = tiles + s * STAGE_BYTES;
-          mbar_expect_tx(full, 2 * A_RAW + 2 * B_BYTES);
-          const bool first = kb < p.kb_half;
-          const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
-          tma_load(base + S::RAW_OFF, first ? &ta0_lo : &ta1_lo, kx, static_cast<int32_t>(d0), full);
-          tma_load(base + S::RAW_OFF + A_RAW, first ? &ta0_hi : &ta1_hi, kx, static_cast<int32_t>(d0), full);
-          tma_load(base + 2 * A_BYTES, &tb_lo, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
-          tma_load(base + 2 * A_BYTES + B_BYTES, &tb_hi, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+          const uint32_t full = q_full + 8 * s, base = qring + s * S::Q_STAGE;
+          mbar_expect_tx(full, 2 * B_BYTES);
+          tma_load(base, &tb_lo, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+          tma_load(base + B_BYTES, &tb_hi, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
           issued = G + 1;
         }
       }
       if (*abort) {
         // copies that may still be in flight land before the CTA leaves (bounded, no abort)
-        for (uint32_t G = issued > STAGES ? issued - STAGES : 0; G < issued; ++G)
-          mbar_wait(full0 + 8 * (G % STAGES), (G / STAGES) & 1u, p.status, nullptr);
+        for (uint32_t G = issued > QS ? issued - QS : 0; G < issued; ++G)
+          mbar_wait(q_full + 8 * (G % QS), (G / QS) & 1u, p.status, nullptr);
       }
     }
   } else if (warp == 1) {
@@ -213,22 +218,24 @@ __global__ void __launch_bounds__(THREADS, 1)
       // C products of k-block j, L products of k-block j - 1, so that the C drain of a chunk
       // overlaps its last two L k-blocks and the L drain the next chunk's first two C k-blocks:
       //   C0 C1 L0 C2 L1 C3 [C-full] L2 L3 [L-full]
-      auto issue_c = [&](uint32_t base) {
+      auto issue_c = [&](uint32_t qb, uint32_t wb) {
 #pragma unroll
         for (uint32_t ks = 0; ks < KB / 16; ++ks) {
           const uint32_t o = 32u * ks;  // 16 fp16 = 32 bytes along K inside the swizzled row
-          umma(tC, sdesc(base + o), sdesc(base + 2 * A_BYTES + B_BYTES + o), S::IDESC);  // lo * hi'
-          umma(tC, sdesc(base + A_BYTES + o), sdesc(base + 2 * A_BYTES + o), S::IDESC);  // hi * lo'
+          umma(tC, sdesc(wb + o), sdesc(qb + B_BYTES + o), S::IDESC);  // lo * hi'
+          umma(tC, sdesc(wb + A_BYTES + o), sdesc(qb + o), S::IDESC);  // hi * lo'
         }
       };
       auto issue_l = [&](uint32_t G) {
-        const uint32_t s = G % STAGES, base = tiles + s * STAGE_BYTES;
+        const uint32_t qs = G % QS, ws = G % WS, qb = qring + qs * S::Q_STAGE, wb = wring + ws * S::W_STAGE;
 #pragma unroll
         for (uint32_t ks = 0; ks < KB / 16; ++ks) {
           const uint32_t o = 32u * ks;
-          umma(tL, sdesc(base + o), sdesc(base + 2 * A_BYTES + o), S::IDESC);  // lo * lo'
+          umma(tL, sdesc(wb + o), sdesc(qb + o), S::IDESC);  // lo * lo'
         }
-        umma_commit(empty0 + 8 * s);  // stage free once these (and all earlier) MMAs are done
+        // the k-block's Q and W stages are free once these (and all earlier) MMAs are done: one
+        // commit (an mbarrier that the query producer and the widening warps both wait on)
+        umma_commit(q_empty + 8 * qs);
       };
       // C restarts every chunk (128 k), L every other chunk (256 k): L gains at most 2^14 per
       // k, C twice that, so both stay within 2^22 of the base between drains.
@@ -240,15 +247,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_after();
         bool ok = true;
         for (uint32_t kb = 0; kb < KB_PER_CHUNK; ++kb) {
-          const uint32_t G = G0 + kb, s = G % STAGES;
+          const uint32_t G = G0 + kb, qs = G % QS, ws = G % WS;
           // the query tiles landed (TMA) and the database tiles were widened
-          if (!mbar_wait(full0 + 8 * s, (G / STAGES) & 1u, p.status, abort) ||
-              !mbar_wait(wide0 + 8 * s, (G / STAGES) & 1u, p.status, abort)) {
+          if (!mbar_wait(q_full + 8 * qs, (G / QS) & 1u, p.status, abort) ||
+              !mbar_wait(w_full + 8 * ws, (G / WS) & 1u, p.status, abort)) {
             ok = false;
             break;
           }
           fence_after();
-          issue_c(tiles + s * STAGE_BYTES);
+          issue_c(qring + qs * S::Q_STAGE, wring + ws * S::W_STAGE);
           if (kb == KB_PER_CHUNK - 1) umma_commit(c_full);
           if (kb == 1 && l_opens) {
             if (!mbar_wait(l_empty, (c >> 1) & 1u, p.status, abort)) {
@@ -268,19 +275,48 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(done_bar, 0, p.status, nullptr);
     }
   } else if (warp >= WIDEN_WARP0) {
-    // ---------------------------------- widening ---------------------------------
-    // Per k-block, after the stage's copies have landed: the raw int8 database tiles become the
-    // fp16 operand tiles of the same stage. The stage's previous MMAs are complete by then (the
-    // producer waited for stage-empty before these copies).
-    const uint32_t ct = threadIdx.x - WIDEN_WARP0 * 32;
-    const uint32_t total = my_items * p.kb_total;
-    for (uint32_t G = 0; G < total; ++G) {
-      const uint32_t s = G % STAGES, base = tiles + s * STAGE_BYTES;
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(full0 + 8 * s, (G / STAGES) & 1u, p.status, abort))) break;
-      widen_tiles<2, WIDEN_THREADS>(base + S::RAW_OFF, A_RAW, base, A_BYTES, ct);
+    // ------------------------- raw copies and widening ---------------------------
+    // Lane 0 issues this warp's plane's raw copies: the first RS k-blocks up front, then
+    // k-block G + RS into raw stage G % RS once the warp has read k-block G from it.
+    const uint32_t pl = static_cast<uint32_t>(warp - WIDEN_WARP0);  // 0: lo limbs, 1: hi limbs
+    const uint32_t rf = r_full + 8 * RS * pl;
+    const CUtensorMap* map0 = pl ? &ta0_hi : &ta0_lo;
+    const CUtensorMap* map1 = pl ? &ta1_hi : &ta1_lo;
+    // the next raw copy (lane 0): k-block li_kb of item li, whose row offset li_d0 is looked up
+    // once per item, so that a copy costs no division
+    uint32_t issued = 0, li = 0, li_kb = 0, li_q0 = 0, li_d0 = 0;
+    coords(0, li_q0, li_d0);
+    auto load_raw = [&](uint32_t G) {
+      const uint32_t s = G % RS;
+      const bool first = li_kb < p.kb_half;
+      const int32_t kx = static_cast<int32_t>((first ? li_kb : li_kb - p.kb_half) * KB);
+      mbar_expect_tx(rf + 8 * s, A_RAW);
+      tma_load(rring + s * S::R_STAGE + pl * A_RAW, first ? map0 : map1, kx, static_cast<int32_t>(li_d0), rf + 8 * s);
+      issued = G + 1;
+      if (++li_kb == p.kb_total) {
+        li_kb = 0;
+        if (++li < my_items) coords(li, li_q0, li_d0);
+      }
+    };
+    if (lane == 0)
+      for (uint32_t G = 0; G < total_kb && G < RS; ++G) load_raw(G);
+    uint32_t G = 0;
+    for (; G < total_kb; ++G) {
+      const uint32_t rs = G % RS, ws = G % WS;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(rf + 8 * rs, (G / RS) & 1u, p.status, abort) &&
+                                       mbar_wait(q_empty + 8 * ws, ((G / WS) & 1u) ^ 1u, p.status, abort)))
+        break;
+      widen_tiles<1, 32>(rring + rs * S::R_STAGE + pl * A_RAW, 0, wring + ws * S::W_STAGE + pl * A_BYTES, 0, lane);
       fence_proxy_async();  // the MMAs read these tiles through the async proxy
-      __syncwarp();
-      if (lane == 0) mbar_arrive(wide0 + 8 * s);
+      __syncwarp();         // every lane has read raw stage rs
+      if (lane == 0) {
+        mbar_arrive(w_full + 8 * ws);
+        if (G + RS < total_kb) load_raw(G + RS);
+      }
+    }
+    if (lane == 0 && *abort) {
+      // raw copies that may still be in flight land before the CTA leaves (bounded, no abort)
+      for (uint32_t H = G; H < issued; ++H) mbar_wait(rf + 8 * (H % RS), (H / RS) & 1u, p.status, nullptr);
     }
   } else {
     // ----------------------------------- drain ----------------------------------
@@ -347,8 +383,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) mbar_arrive(l_empty);
       }
       // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) (App. C) ----
-      // The running sums go to shared memory (the stage ring is idle once every drainer has seen
-      // the item's last L-full and before the producer sees epi-done), then each (column, 8-row
+      // The running sums go to shared memory (the Q ring is idle once every drainer has seen the
+      // item's last L-full and before the query producer sees epi-done), then each (column, 8-row
       // group) item adds its zero shares, which one Philox block per seed gives for all 8 rows,
       // and writes 16 bytes of z.
       named_sync(1, DRAIN_THREADS);
@@ -390,7 +426,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(epi_done);  // this warp is done with the stage ring
+      if (lane == 0) mbar_arrive(epi_done);  // this warp is done with the Q ring
     }
   }
   fence_before();

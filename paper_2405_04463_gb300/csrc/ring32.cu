@@ -161,20 +161,22 @@ constexpr int TM = 128, TN = 128, KB = 32, LIMBS = 4;
 constexpr int W_TILE = TM * KB * 2;  // 8 KiB widened (fp16) database tile
 constexpr int RAW_TILE = TM * KB;    // 4 KiB raw (int8) database tile
 constexpr int B_TILE = TN * KB * 2;  // 8 KiB query tile
-constexpr int R_STAGES = 3, W_STAGES = 2;
-// R stage: query limbs 0-3, then raw database limbs 0-3; W stage: widened database limbs 0-3
-constexpr int R_STAGE = LIMBS * B_TILE + LIMBS * RAW_TILE;  // 48 KiB
-constexpr int W_STAGE = LIMBS * W_TILE;                      // 32 KiB
+constexpr int QS = 3, WS = 2, RS = 4;  // stages of the query, widened and raw rings
+constexpr int Q_STAGE = LIMBS * B_TILE;    // 32 KiB: query limbs 0-3
+constexpr int W_STAGE = LIMBS * W_TILE;    // 32 KiB: widened database limbs 0-3
+constexpr int R_STAGE = LIMBS * RAW_TILE;  // 16 KiB: raw database limbs 0-3
+constexpr int W_OFF = QS * Q_STAGE, R_OFF = W_OFF + WS * W_STAGE, BAR_OFF = R_OFF + RS * R_STAGE;
 constexpr int THREADS = 12 * 32, DRAIN_THREADS = 8 * 32;
 constexpr int WIDEN_WARP0 = 10, WIDEN_THREADS = 2 * 32;
 constexpr uint32_t KB_PER_CHUNK = 2;  // 64 k: the shortest drain period
 constexpr uint32_t TMEM_COLS = 4 * TN;
 constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
-// r_full[R], r_empty[R], w_full[W], w_empty[W], g_full[4], g_empty[4], done
-constexpr int NUM_BARS = 2 * R_STAGES + 2 * W_STAGES + 9;
-constexpr int SMEM_BYTES = R_STAGES * R_STAGE + W_STAGES * W_STAGE + 1024 + 8 * NUM_BARS;
+// q_full[QS], q_empty[QS], w_full[WS], w_empty[WS], r_full[RS], r_empty[RS], g_full[4],
+// g_empty[4], done
+constexpr int NUM_BARS = 2 * QS + 2 * WS + 2 * RS + 9;
+constexpr int SMEM_BYTES = BAR_OFF + 1024 + 8 * NUM_BARS;
 static_assert(SMEM_BYTES <= 232448, "dynamic shared memory per block");
-static_assert(TN * TM * 4 <= R_STAGES * R_STAGE, "the z tile is staged in the R ring");
+static_assert(TN * TM * 4 <= QS * Q_STAGE, "the z tile is staged in the Q ring");
 // kind::f16: D f32, A and B f16, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t IDESC = (1u << 4) | (static_cast<uint32_t>(TN >> 3) << 17) | (static_cast<uint32_t>(TM >> 4) << 24);
 
@@ -201,16 +203,16 @@ struct Tc32Params {
   uint32_t* status;
 };
 
-// Roles (12 warps):
-//   warp 0 lane 0  TMA producer: per k-block of 32 elements, the four fp16 query limb tiles
-//                  (128 x 32, 64-byte swizzle) and the four raw int8 database limb tiles (128 x 32)
-//                  into a 3-stage ring.
-//   warps 10-11    widening: per k-block the four raw database tiles become fp16 operand tiles in
-//                  a 2-stage ring of their own, so the copies can run a stage further ahead.
+// Roles (12 warps), with three rings as in the 16-bit kernel (query, raw database, widened
+// database), so that the widening runs ahead of the MMAs:
+//   warp 0 lane 0  query producer: per k-block of 32 elements, the four fp16 query limb tiles
+//                  (128 x 32, 64-byte swizzle).
+//   warps 10-11    raw copies and widening: the four raw int8 database limb tiles of a k-block
+//                  (copied RS k-blocks ahead) become fp16 operand tiles in the W ring.
 //   warp 1 lane 0  MMA issuer: per k-block the S_3, S_2, S_1, S_0 products in that order,
-//                  committing S_s-full after the last k-block of its drain period and both stages
-//                  after the k-block's S_0 products. S_3's drain overlaps the k-block's other six
-//                  products; S_2's the S_1, S_0 products and the next k-block's S_3 products.
+//                  committing S_s-full after the last k-block of its drain period and the Q and
+//                  W stages after the k-block's S_0 products. S_3's drain overlaps the k-block's
+//                  other six products; S_2's the S_1, S_0 products and the next k-block's S_3.
 //   warps 2-9      drain: each thread owns one TMEM lane (database row) and 64 columns.
 // TMEM: S_s in columns [128 s, 128 s + 128), all 512 columns.
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_constant__ Maps32 m, const Tc32Params p) {
@@ -218,24 +220,27 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
   __shared__ uint32_t s_tmem;
   __shared__ uint32_t s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t rring = smem_addr(smem), wring = rring + R_STAGES * R_STAGE;
-  const uint32_t bars = wring + W_STAGES * W_STAGE;
-  const uint32_t r_full = bars, r_empty = bars + 8 * R_STAGES;
-  const uint32_t w_full = bars + 16 * R_STAGES, w_empty = w_full + 8 * W_STAGES;
-  const uint32_t g_full = w_empty + 8 * W_STAGES, g_empty = g_full + 32, done_bar = g_full + 64;
+  const uint32_t qring = smem_addr(smem), wring = qring + W_OFF, rring = qring + R_OFF, bars = qring + BAR_OFF;
+  const uint32_t q_full = bars, q_empty = q_full + 8 * QS, w_full = q_empty + 8 * QS, w_empty = w_full + 8 * WS,
+                 r_full = w_empty + 8 * WS, r_empty = r_full + 8 * RS;
+  const uint32_t g_full = r_empty + 8 * RS, g_empty = g_full + 32, done_bar = g_full + 64;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t q0 = blockIdx.x * TN, d0 = blockIdx.y * TM;
   const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;  // a multiple of 4: K is a multiple of 256
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < R_STAGES; ++s) {
-      mbar_init(r_full + 8 * s, 1);
-      mbar_init(r_empty + 8 * s, 1);
+    for (int s = 0; s < QS; ++s) {
+      mbar_init(q_full + 8 * s, 1);
+      mbar_init(q_empty + 8 * s, 1);
     }
-    for (int s = 0; s < W_STAGES; ++s) {
+    for (int s = 0; s < WS; ++s) {
       mbar_init(w_full + 8 * s, WIDEN_THREADS / 32);
       mbar_init(w_empty + 8 * s, 1);
+    }
+    for (int s = 0; s < RS; ++s) {
+      mbar_init(r_full + 8 * s, 1);
+      mbar_init(r_empty + 8 * s, WIDEN_THREADS / 32);
     }
     for (int g = 0; g < 4; ++g) {
       mbar_init(g_full + 8 * g, 1);
@@ -257,29 +262,23 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
   const uint32_t tmem = s_tmem;
 
   if (warp == 0) {
-    // ------------------------------- TMA producer -------------------------------
+    // ---------------------------- query TMA producer -----------------------------
     if (lane == 0) {
       uint32_t issued = 0;
       for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
-        const uint32_t s = kb % R_STAGES;
-        if (!mbar_wait(r_empty + 8 * s, ((kb / R_STAGES) & 1u) ^ 1u, p.status, abort)) break;
-        const uint32_t full = r_full + 8 * s, base = rring + s * R_STAGE;
-        const bool first = kb < p.kb_half;
-        const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
-        mbar_expect_tx(full, R_STAGE);
+        const uint32_t s = kb % QS;
+        if (!mbar_wait(q_empty + 8 * s, ((kb / QS) & 1u) ^ 1u, p.status, abort)) break;
+        const uint32_t full = q_full + 8 * s, base = qring + s * Q_STAGE;
+        mbar_expect_tx(full, Q_STAGE);
 #pragma unroll
         for (int b = 0; b < LIMBS; ++b)
           tma_load(base + b * B_TILE, &m.b[b], static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
-#pragma unroll
-        for (int a = 0; a < LIMBS; ++a)
-          tma_load(base + LIMBS * B_TILE + a * RAW_TILE, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0),
-                   full);
         issued = kb + 1;
       }
       if (*abort) {
         // copies that may still be in flight land before the CTA goes on (bounded, no abort)
-        for (uint32_t kb = issued > R_STAGES ? issued - R_STAGES : 0; kb < issued; ++kb)
-          mbar_wait(r_full + 8 * (kb % R_STAGES), (kb / R_STAGES) & 1u, p.status, nullptr);
+        for (uint32_t kb = issued > QS ? issued - QS : 0; kb < issued; ++kb)
+          mbar_wait(q_full + 8 * (kb % QS), (kb / QS) & 1u, p.status, nullptr);
       }
     }
   } else if (warp == 1) {
@@ -287,12 +286,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     if (lane == 0) {
       bool ok = true;
       for (uint32_t kb = 0; kb < p.kb_total && ok; ++kb) {
-        const uint32_t s = kb % R_STAGES, w = kb % W_STAGES, c = kb / KB_PER_CHUNK, j = kb % KB_PER_CHUNK;
-        if (!mbar_wait(r_full + 8 * s, (kb / R_STAGES) & 1u, p.status, abort) ||
-            !mbar_wait(w_full + 8 * w, (kb / W_STAGES) & 1u, p.status, abort))
+        const uint32_t qs = kb % QS, ws = kb % WS, c = kb / KB_PER_CHUNK, j = kb % KB_PER_CHUNK;
+        if (!mbar_wait(q_full + 8 * qs, (kb / QS) & 1u, p.status, abort) ||
+            !mbar_wait(w_full + 8 * ws, (kb / WS) & 1u, p.status, abort))
           break;
         fence_after();
-        const uint32_t qbase = rring + s * R_STAGE, dbase = wring + w * W_STAGE;
+        const uint32_t qbase = qring + qs * Q_STAGE, dbase = wring + ws * W_STAGE;
 #pragma unroll
         for (int g = 3; g >= 0; --g) {
           const uint32_t per = period(g);
@@ -315,8 +314,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
           if (j == KB_PER_CHUNK - 1 && c % per == per - 1) umma_commit(g_full + 8 * g);
         }
         if (ok) {  // both stages free once these (and all earlier) MMAs are done
-          umma_commit(r_empty + 8 * s);
-          umma_commit(w_empty + 8 * w);
+          umma_commit(q_empty + 8 * qs);
+          umma_commit(w_empty + 8 * ws);
         }
       }
       // every MMA issued above completes before the tensor memory is freed
@@ -324,18 +323,43 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
       mbar_wait(done_bar, 0, p.status, nullptr);
     }
   } else if (warp >= WIDEN_WARP0) {
-    // ---------------------------------- widening ---------------------------------
+    // ------------------------- raw copies and widening ---------------------------
     const uint32_t ct = threadIdx.x - WIDEN_WARP0 * 32;
-    for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
-      const uint32_t s = kb % R_STAGES, w = kb % W_STAGES;
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_full + 8 * s, (kb / R_STAGES) & 1u, p.status, abort) &&
-                                       mbar_wait(w_empty + 8 * w, ((kb / W_STAGES) & 1u) ^ 1u, p.status, abort)))
+    uint32_t issued = 0;
+    auto load_raw = [&](uint32_t kb) {
+      const uint32_t s = kb % RS, full = r_full + 8 * s, base = rring + s * R_STAGE;
+      const bool first = kb < p.kb_half;
+      const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
+      mbar_expect_tx(full, R_STAGE);
+#pragma unroll
+      for (int a = 0; a < LIMBS; ++a)
+        tma_load(base + a * RAW_TILE, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full);
+      issued = kb + 1;
+    };
+    if (ct == 0)
+      for (uint32_t kb = 0; kb < p.kb_total && kb < RS; ++kb) load_raw(kb);
+    uint32_t kb = 0;
+    for (; kb < p.kb_total; ++kb) {
+      const uint32_t rs = kb % RS, ws = kb % WS;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_full + 8 * rs, (kb / RS) & 1u, p.status, abort) &&
+                                       mbar_wait(w_empty + 8 * ws, ((kb / WS) & 1u) ^ 1u, p.status, abort)))
         break;
-      widen_tiles<LIMBS, WIDEN_THREADS>(rring + s * R_STAGE + LIMBS * B_TILE, RAW_TILE, wring + w * W_STAGE, W_TILE,
-                                        ct);
+      widen_tiles<LIMBS, WIDEN_THREADS>(rring + rs * R_STAGE, RAW_TILE, wring + ws * W_STAGE, W_TILE, ct);
       fence_proxy_async();  // the MMAs read these tiles through the async proxy
       __syncwarp();
-      if (lane == 0) mbar_arrive(w_full + 8 * w);
+      if (lane == 0) {
+        mbar_arrive(w_full + 8 * ws);
+        mbar_arrive(r_empty + 8 * rs);  // this warp has read raw stage rs
+      }
+      if (warp == WIDEN_WARP0 && kb + RS < p.kb_total) {
+        // refill once both warps have read the stage (a bounded wait, warp-uniform like the others)
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_empty + 8 * rs, (kb / RS) & 1u, p.status, abort))) break;
+        if (lane == 0) load_raw(kb + RS);
+      }
+    }
+    if (ct == 0 && *abort) {
+      // raw copies that may still be in flight land before the CTA leaves (bounded, no abort)
+      for (uint32_t h = kb; h < issued; ++h) mbar_wait(r_full + 8 * (h % RS), (h / RS) & 1u, p.status, nullptr);
     }
   } else {
     // ----------------------------------- drain ----------------------------------
@@ -383,7 +407,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
       }
     }
     // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) over Z_{2^32} (App. C) ----
-    // The sums go to shared memory (the R ring is idle: the last S_0-full followed every MMA,
+    // The sums go to shared memory (the Q ring is idle: the last S_0-full followed every MMA,
     // and every copy was consumed), then each (column, 4-row group) item adds the zero shares of
     // its four rows, one Philox block per seed, and writes 16 bytes of z.
     named_sync(1, DRAIN_THREADS);

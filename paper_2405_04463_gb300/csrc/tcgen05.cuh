@@ -176,12 +176,12 @@ __device__ __forceinline__ void widen16(uint4 raw, uint4& c0, uint4& c1) {
 // [128 rows][32] int8, rows 32 bytes apart (TMA, no swizzle); its widened tile is [128][32]
 // fp16 in the 64-byte swizzled K-major layout that TMA would have written for an fp16 box:
 // row r at r * 64, its 16-byte chunk c (elements 8c..8c+7) at chunk position c ^ ((r >> 1) & 3).
-// `ct` in [0, nthreads) numbers the widening threads; each takes rows (ct >> 1) + 32 j, half
-// ct & 1 (16 elements), so its swizzle term (ct >> 2) & 3 is fixed.
+// `ct` in [0, NTHREADS) numbers the widening threads; each takes rows (ct >> 1) + (NTHREADS / 2) j,
+// half ct & 1 (16 elements), so its swizzle term (ct >> 2) & 3 is fixed.
 template <int PLANES, int NTHREADS>
 __device__ __forceinline__ void widen_tiles(uint32_t raw, uint32_t raw_stride, uint32_t dst, uint32_t dst_stride,
                                             uint32_t ct) {
-  static_assert(NTHREADS == 64 || NTHREADS == 128, "two or four widening warps");
+  static_assert(NTHREADS == 32 || NTHREADS == 64 || NTHREADS == 128, "one, two or four widening warps");
   constexpr int JOBS = PLANES * 256 / NTHREADS;   // 16-element jobs per thread
   constexpr int ROWS_STEP = NTHREADS / 2;           // rows between a thread's jobs in one plane
   constexpr int PER_PLANE = 128 / ROWS_STEP;        // jobs per plane
