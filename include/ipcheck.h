@@ -514,6 +514,15 @@ int fetch_transcript_hash(ipc_ctx* ctx, uint64_t req_id, uint64_t* hash_out, int
 int fetch_distances(ipc_ctx* ctx, uint64_t req_id, uint32_t q, uint32_t rho, size_t row_begin, size_t row_end,
                     int16_t* dot, uint16_t* ml);
 
+/* Fault injection for tests (no counterpart in the paper): the next request submitted on this
+ * context simulates party `party` (0..2) dropping out. Before that party computes its messages,
+ * its stream waits for a device flag that nothing ever sets; the wait gives up after limit_us
+ * (1..1,000,000) of global time and raises the device status word, as every bounded wait in the
+ * pipeline does, instead of hanging. A fetch with a shorter timeout returns IPC_ETIMEOUT and
+ * keeps the request; the next fetch after the limit returns IPC_EDEVICE once (the word is then
+ * cleared), and later fetches return the request's results, which are unaffected. */
+int ipc_debug_stall_party(ipc_ctx* ctx, uint32_t party, uint32_t limit_us);
+
 /* Resource management (no counterpart in the paper): releases a request that will not be
  * fetched, returning its slot to the context; waits for its device work first. */
 int ipc_release(ipc_ctx* ctx, uint64_t req_id);

@@ -118,6 +118,7 @@ _SIGS = {
     "fetch_transcript_hash": [_vp, _u64, ctypes.POINTER(_u64), _int],
     "ipc_selftest_bounded_wait": [_u32, _vp],
     "ipc_release": [_vp, _u64],
+    "ipc_debug_stall_party": [_vp, _u32, _u32],
     "ipc_db_rows": [_vp],
     "ipc_destroy": [_vp],
     "ipc_last_error": [_vp],
@@ -377,6 +378,10 @@ def fetch_bit_shares(ctx, req_id, shares_out, n_queries, timeout_ms=-1):
 
 def fetch_distances(ctx, req_id, q, rho, row_begin, row_end, dot, ml):
     _check(lib.fetch_distances(ctx, req_id, q, rho, row_begin, row_end, ptr(dot), ptr(ml)), ctx)
+
+
+def ipc_debug_stall_party(ctx, party, limit_us):
+    _check(lib.ipc_debug_stall_party(ctx, party, limit_us), ctx)
 
 
 def ipc_release(ctx, req_id):

@@ -234,6 +234,7 @@ extern "C" void ipc_destroy(ipc_ctx* c) {
   for (auto& ch : c->chunks) cudaFree(ch.planes);
   cudaFree(c->zbuf);
   cudaFree(c->stage);
+  cudaFree(c->stall_flag);
   for (int i = 0; i < 3; ++i)
     if (c->sp[i]) cudaStreamDestroy(c->sp[i]);
   if (c->sc) cudaStreamDestroy(c->sc);
@@ -440,6 +441,11 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   auto f16p = [](uint8_t* p) { return reinterpret_cast<uint16_t*>(p); };
   for (int i = 0; i < 3; ++i) {
     SUB_TRY(cudaStreamWaitEvent(c->sp[i], c->ev_setup, 0));
+    if (c->stall_party == i) {
+      // injected failure: this party's work waits for a message that never comes (bounded)
+      SUB_RC(stall_launch(c->stall_flag, c->stall_us, c->sp[i]));
+      c->stall_party = -1;
+    }
     for (int vec = 0; vec < 2; ++vec) {
       const uint16_t* y = reinterpret_cast<const uint16_t*>(qvec(vec));
       if (wide(c, vec)) {
@@ -701,6 +707,19 @@ extern "C" int fetch_transcript_hash(ipc_ctx* c, uint64_t req_id, uint64_t* hash
   for (uint32_t p = 0; p < 3; ++p)
     for (uint32_t q = 0; q < r.Q; ++q) h ^= msg_hash(2, p, q, 0, sl.shares_host[static_cast<size_t>(p) * r.Q + q]);
   *hash_out = h;
+  return IPC_OK;
+}
+
+extern "C" int ipc_debug_stall_party(ipc_ctx* c, uint32_t party, uint32_t limit_us) {
+  if (!c || party > 2 || limit_us == 0 || limit_us > 1000000)
+    return fail(c, IPC_EINVAL, "ipc_debug_stall_party: party 0..2 and limit_us in 1..1000000");
+  CTX_TRY(c, cudaSetDevice(c->cfg.device));
+  if (!c->stall_flag) {
+    CTX_TRY(c, cudaMalloc(&c->stall_flag, sizeof(uint32_t)));
+    CTX_TRY(c, cudaMemset(c->stall_flag, 0, sizeof(uint32_t)));  // nothing ever sets it
+  }
+  c->stall_party = static_cast<int>(party);
+  c->stall_us = limit_us;
   return IPC_OK;
 }
 

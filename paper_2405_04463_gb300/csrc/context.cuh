@@ -56,6 +56,7 @@ int ctx_fail(ipc_ctx* c, int code, const std::string& msg);
 int ctx_cfail(ipc_ctx* c, cudaError_t e, const char* what);
 uint8_t* ctx_plane(const ipc_ctx* c, const Chunk& ch, int comp, int vec, int limb);
 int ctx_check_device_status(ipc_ctx* c);
+int stall_launch(const uint32_t* flag, uint32_t limit_us, cudaStream_t st);
 int prep_query_rotate_plain(const uint16_t* y, uint32_t Q, const ipc_geom* g, uint16_t* b_lo, uint16_t* b_hi,
                             uint32_t n_pad, void* stream);
 int compare_launch_tiles(const uint16_t* const z_code[3], const uint16_t* const z_mask[3], size_t ldz,
@@ -112,4 +113,8 @@ struct ipc_ctx {
   std::mutex id_mu;            // next_id, when the serving loop runs
   ipc::Server* srv = nullptr;  // the serving loop, while one runs
   std::string err;
+  // test aid: the next request's party stall_party first waits for a flag that nothing sets
+  int stall_party = -1;
+  uint32_t stall_us = 0;
+  uint32_t* stall_flag = nullptr;
 };

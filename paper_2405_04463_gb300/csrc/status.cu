@@ -53,6 +53,18 @@ __global__ void bounded_wait_kernel(const volatile uint32_t* flag, uint64_t limi
 }  // namespace
 }  // namespace ipc
 
+namespace ipc {
+// Enqueues, without synchronising, a wait on `flag` (which nothing sets) that gives up after
+// limit_us and raises the status word: a stalled party, injected on the host.
+int stall_launch(const uint32_t* flag, uint32_t limit_us, cudaStream_t st) {
+  uint32_t* status = status_ptr();
+  if (!status) return cuda_fail(cudaErrorMemoryAllocation, "status word");
+  bounded_wait_kernel<<<1, 32, 0, st>>>(flag, 1000ull * limit_us, status);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
+}
+}  // namespace ipc
+
 extern "C" int ipc_selftest_bounded_wait(uint32_t limit_us, void* stream) {
   if (limit_us == 0 || limit_us > 1000000) {
     ipc::set_error("ipc_selftest_bounded_wait: limit_us must be in 1..1000000");
