@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
-    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc32) or compare")
+    ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc32), "
+                    "compare, or overlap (Galois GEMM and comparison alone and on two streams)")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--serving", action="store_true",
@@ -115,6 +116,63 @@ def run_compare_kernel(args, w):
     print(json.dumps(out))
 
 
+def run_overlap(args, w):
+    """Can the comparison phase hide behind the dot-product GEMMs on the same GPU? The Galois-ring
+    GEMM of one party and vector (K = l) over a chunk of --rows rows and the MPCLift comparison of
+    the same chunk are timed alone, then launched together on two streams, interleaved. Overlap
+    would show as together < GEMM + comparison; it is what a fused GEMM + comparison kernel
+    (Sec. 6.4's dots-then-comparisons split on one device) would have to exploit."""
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    l, N, rows = w.l, w.Q * w.R, args.rows
+    n_pad = (N + 127) // 128 * 128
+    f16 = lambda t: t.to(torch.float16).view(torch.int16).contiguous()
+    xl = torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda")
+    xh = torch.randint(-128, 128, (rows, l), dtype=torch.int8, device="cuda")
+    bl = f16(torch.randint(-128, 128, (n_pad, l), dtype=torch.int8, device="cuda"))
+    bh = f16(torch.randint(-128, 128, (n_pad, l), dtype=torch.int8, device="cuda"))
+    tags = torch.zeros((N, 2), dtype=torch.int32, device="cuda")
+    z = torch.empty((N, rows), dtype=torch.int16, device="cuda")
+    g = torch.Generator(device="cpu").manual_seed(7)
+    zc = [torch.randint(-32768, 32768, (N, rows), dtype=torch.int16, generator=g).cuda() for _ in range(3)]
+    zm = [torch.randint(0, 12801, (N, rows), dtype=torch.int16, generator=g).cuda() for _ in range(3)]
+    nb = (rows + 1023) // 1024
+    roots = torch.zeros((3, N, nb), dtype=torch.int32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def gemm(st):
+        ipc.ipc_ring_gemm_tc_galois(256, xl, xh, rows, bl, bh, N, n_pad, l, tags, 1, 2, 0, z, rows, 0, stream=st)
+
+    def cmp(st):
+        ipc.ipc_compare(zc, zm, rows, N, rows, 0, tags, w.prf_seeds, w.thr_a, 5, roots, nb, stream=st)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t)
+
+    reps = max(args.reps, 6)
+    for _ in range(2):
+        gemm(s1)
+        cmp(s2)
+    t_gemm = timed(lambda: [gemm(s1) for _ in range(reps)]) / reps
+    t_cmp = timed(lambda: [cmp(s2) for _ in range(reps)]) / reps
+
+    def both():
+        for _ in range(reps):
+            gemm(s1)
+            cmp(s2)
+    t_both = timed(both) / reps
+    ipc.ipc_status()
+    print(json.dumps({"kernel": "overlap", "rows": rows, "cols": N, "gemm_ms": t_gemm, "compare_ms": t_cmp,
+                      "together_ms": t_both, "sum_ms": t_gemm + t_cmp,
+                      "hidden_fraction_of_compare": (t_gemm + t_cmp - t_both) / t_cmp,
+                      "note": "per pair of launches, host wall clock around reps launches on two streams"}))
+
+
 def run_kernel(args, w):
     """One ring-GEMM launch shape of the workload (all its query columns x --rows rows), random
     operands, timed alone with CUDA events; used for ncu captures on a small case."""
@@ -123,6 +181,8 @@ def run_kernel(args, w):
     import paper_2405_04463_gb300 as ipc
     if args.kernel == "compare":
         return run_compare_kernel(args, w)
+    if args.kernel == "overlap":
+        return run_overlap(args, w)
     l, N = w.l, w.Q * w.R
     n_pad = (N + 127) // 128 * 128
     rows = args.rows
