@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                    add2(acc.w, fo.w, fp.w));
         uint16_t* dst = p.z + static_cast<uint64_t>(col) * p.ldz + r0;
         if (r0 + 8 <= p.x_rows) {
-          *reinterpret_cast<uint4*>(dst) = v;
+          __stcs(reinterpret_cast<uint4*>(dst), v);  // streamed: z is read by a later kernel, not from L2
         } else {
           const uint32_t w[4] = {v.x, v.y, v.z, v.w};
           for (uint32_t e = 0; e < p.x_rows - r0; ++e) dst[e] = static_cast<uint16_t>(w[e >> 1] >> (16 * (e & 1)));

@@ -21,6 +21,7 @@
 
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "tcgen05.cuh"
 
@@ -156,37 +157,56 @@ __global__ void prep_query32_kernel(const uint32_t* __restrict__ y, uint64_t pla
 }
 
 // ----------------------------------- A3 -----------------------------------
-// One CTA per tile of 128 database rows x 128 query columns (MMA 128 x 128 x 16).
-constexpr int TM = 128, TN = 128, KB = 32, LIMBS = 4;
+// One CTA per tile of 128 database rows x 256 query columns (MMA 128 x 256 x 16). Four 256-column
+// accumulators would need 1,024 TMEM columns (an SM has 512), so the tile runs in two passes of
+// two accumulators each, over the same rings:
+//   pass A (stages 0 .. KBT-1, one k-block each): S_3 and S_2, seven limb products over limbs
+//     0-3. Only U = (S_2 + 2^8 S_3) mod 2^16 matters (it enters z shifted by 16), so its running
+//     sums are kept mod 2^16, two columns to a register; at the end of the pass they go to z as
+//     U << 16 (global memory, read back by the epilogue).
+//   pass B (stages KBT .. KBT + KBT/2 - 1, two k-blocks each): S_1 and S_0, three limb products
+//     over limbs 0-1, whose sums are kept mod 2^32.
+// A stage holds four tiles of each operand: limbs 0-3 of one k-block (pass A) or limbs 0-1 of
+// two k-blocks (pass B), so the rings run on from one pass into the other.
+constexpr int TM = 128, TN = 256, KB = 32, SLOTS = 4;
 constexpr int W_TILE = TM * KB * 2;  // 8 KiB widened (fp16) database tile
 constexpr int RAW_TILE = TM * KB;    // 4 KiB raw (int8) database tile
-constexpr int B_TILE = TN * KB * 2;  // 8 KiB query tile
-constexpr int QS = 3, WS = 2, RS = 4;  // stages of the query, widened and raw rings
-constexpr int Q_STAGE = LIMBS * B_TILE;    // 32 KiB: query limbs 0-3
-constexpr int W_STAGE = LIMBS * W_TILE;    // 32 KiB: widened database limbs 0-3
-constexpr int R_STAGE = LIMBS * RAW_TILE;  // 16 KiB: raw database limbs 0-3
+constexpr int B_TILE = TN * KB * 2;  // 16 KiB query tile
+constexpr int QS = 2, WS = 2, RS = 2;  // stages of the query, widened and raw rings
+constexpr int Q_STAGE = SLOTS * B_TILE;    // 64 KiB
+constexpr int W_STAGE = SLOTS * W_TILE;    // 32 KiB
+constexpr int R_STAGE = SLOTS * RAW_TILE;  // 16 KiB
 constexpr int W_OFF = QS * Q_STAGE, R_OFF = W_OFF + WS * W_STAGE, BAR_OFF = R_OFF + RS * R_STAGE;
 constexpr int THREADS = 12 * 32, DRAIN_THREADS = 8 * 32;
-constexpr int WIDEN_WARP0 = 10, WIDEN_THREADS = 2 * 32;
-constexpr uint32_t KB_PER_CHUNK = 2;  // 64 k: the shortest drain period
-constexpr uint32_t TMEM_COLS = 4 * TN;
+constexpr int WIDEN_WARP0 = 2, WIDEN_THREADS = 2 * 32, DRAIN_WARP0 = 4;
+constexpr uint32_t TMEM_COLS = 2 * TN;  // region 0 (S_2, then S_0) and region 1 (S_3, then S_1)
 constexpr uint32_t MAGIC = 0x4B400000u;  // fp32 bits of 1.5 * 2^23
-// q_full[QS], q_empty[QS], w_full[WS], w_empty[WS], r_full[RS], r_empty[RS], g_full[4],
-// g_empty[4], done
-constexpr int NUM_BARS = 2 * QS + 2 * WS + 2 * RS + 9;
+// q_full[QS], q_empty[QS], w_full[WS], w_empty[WS], r_full[RS], r_empty[RS], a_full[2],
+// a_empty[2], done
+constexpr int NUM_BARS = 2 * QS + 2 * WS + 2 * RS + 5;
 constexpr int SMEM_BYTES = BAR_OFF + 1024 + 8 * NUM_BARS;
 static_assert(SMEM_BYTES <= 232448, "dynamic shared memory per block");
 static_assert(TN * TM * 4 <= QS * Q_STAGE, "the z tile is staged in the Q ring");
 // kind::f16: D f32, A and B f16, both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t IDESC = (1u << 4) | (static_cast<uint32_t>(TN >> 3) << 17) | (static_cast<uint32_t>(TM >> 4) << 24);
 
-// Drain period of S_s in 64-k chunks.
-__host__ __device__ constexpr uint32_t period(int s) { return s == 0 ? 4u : (s == 1 ? 2u : 1u); }
+// Drain periods, in stages: pass A drains both regions every 2 stages (64 k: S_3 gains at most
+// 4 * 2^14 per k); pass B drains S_1 every 2 stages (128 k) and S_0 every 4 (256 k).
+// Operand tile t of stage G: its limb and k-block.
+__device__ __forceinline__ void stage_slot(uint32_t G, uint32_t kbt, uint32_t t, uint32_t& limb, uint32_t& kb) {
+  if (G < kbt) {
+    limb = t;
+    kb = G;
+  } else {
+    limb = t & 1u;
+    kb = 2u * (G - kbt) + (t >> 1);
+  }
+}
 
 struct Maps32 {
-  CUtensorMap b[LIMBS];   // query limbs [n_pad][K], fp16
-  CUtensorMap a0[LIMBS];  // database limbs of the first K segment [x_rows][l], int8
-  CUtensorMap a1[LIMBS];  // and of the second
+  CUtensorMap b[4];   // query limbs [n_pad][K], fp16
+  CUtensorMap a0[4];  // database limbs of the first K segment [x_rows][l], int8
+  CUtensorMap a1[4];  // and of the second
 };
 
 struct Tc32Params {
@@ -205,16 +225,17 @@ struct Tc32Params {
 
 // Roles (12 warps), with three rings as in the 16-bit kernel (query, raw database, widened
 // database), so that the widening runs ahead of the MMAs:
-//   warp 0 lane 0  query producer: per k-block of 32 elements, the four fp16 query limb tiles
-//                  (128 x 32, 64-byte swizzle).
-//   warps 10-11    raw copies and widening: the four raw int8 database limb tiles of a k-block
-//                  (copied RS k-blocks ahead) become fp16 operand tiles in the W ring.
-//   warp 1 lane 0  MMA issuer: per k-block the S_3, S_2, S_1, S_0 products in that order,
-//                  committing S_s-full after the last k-block of its drain period and the Q and
-//                  W stages after the k-block's S_0 products. S_3's drain overlaps the k-block's
-//                  other six products; S_2's the S_1, S_0 products and the next k-block's S_3.
-//   warps 2-9      drain: each thread owns one TMEM lane (database row) and 64 columns.
-// TMEM: S_s in columns [128 s, 128 s + 128), all 512 columns.
+//   warp 0 lane 0  query producer: per stage, four fp16 query tiles (256 x 32, 64-byte swizzle).
+//   warps 2-3      raw copies and widening: a stage's four raw int8 database tiles (copied RS
+//                  stages ahead) become fp16 operand tiles in the W ring.
+//   warp 1 lane 0  MMA issuer: per stage, region 1's products (S_3, or S_1), then region 0's
+//                  (S_2, or S_0), committing a region's full barrier after the last stage of its
+//                  drain period, then the stage's Q and W slots. Region 1 drains while region
+//                  0's products of the same stage run.
+//   warps 4-11     drain: each thread owns one TMEM lane (database row) and 128 columns.
+// Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
+// status word, lets its copies and MMAs finish and frees its tensor memory (its z tile is then
+// undefined).
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_constant__ Maps32 m, const Tc32Params p) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
@@ -223,11 +244,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
   const uint32_t qring = smem_addr(smem), wring = qring + W_OFF, rring = qring + R_OFF, bars = qring + BAR_OFF;
   const uint32_t q_full = bars, q_empty = q_full + 8 * QS, w_full = q_empty + 8 * QS, w_empty = w_full + 8 * WS,
                  r_full = w_empty + 8 * WS, r_empty = r_full + 8 * RS;
-  const uint32_t g_full = r_empty + 8 * RS, g_empty = g_full + 32, done_bar = g_full + 64;
+  const uint32_t a_full = r_empty + 8 * RS, a_empty = a_full + 16, done_bar = a_full + 32;
   volatile uint32_t* abort = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t q0 = blockIdx.x * TN, d0 = blockIdx.y * TM;
-  const uint32_t n_chunks = p.kb_total / KB_PER_CHUNK;  // a multiple of 4: K is a multiple of 256
+  const uint32_t kbt = p.kb_total;           // a multiple of 8: K is a multiple of 256
+  const uint32_t n_stages = kbt + kbt / 2;   // pass A, then pass B
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < QS; ++s) {
@@ -242,9 +264,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
       mbar_init(r_full + 8 * s, 1);
       mbar_init(r_empty + 8 * s, WIDEN_THREADS / 32);
     }
-    for (int g = 0; g < 4; ++g) {
-      mbar_init(g_full + 8 * g, 1);
-      mbar_init(g_empty + 8 * g, DRAIN_THREADS / 32);
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(a_full + 8 * g, 1);
+      mbar_init(a_empty + 8 * g, DRAIN_THREADS / 32);
     }
     mbar_init(done_bar, 1);
     s_abort = 0;
@@ -265,159 +287,262 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     // ---------------------------- query TMA producer -----------------------------
     if (lane == 0) {
       uint32_t issued = 0;
-      for (uint32_t kb = 0; kb < p.kb_total; ++kb) {
-        const uint32_t s = kb % QS;
-        if (!mbar_wait(q_empty + 8 * s, ((kb / QS) & 1u) ^ 1u, p.status, abort)) break;
+      for (uint32_t G = 0; G < n_stages; ++G) {
+        const uint32_t s = G % QS;
+        if (!mbar_wait(q_empty + 8 * s, ((G / QS) & 1u) ^ 1u, p.status, abort)) break;
         const uint32_t full = q_full + 8 * s, base = qring + s * Q_STAGE;
         mbar_expect_tx(full, Q_STAGE);
 #pragma unroll
-        for (int b = 0; b < LIMBS; ++b)
-          tma_load(base + b * B_TILE, &m.b[b], static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
-        issued = kb + 1;
+        for (uint32_t t = 0; t < SLOTS; ++t) {
+          uint32_t limb, kb;
+          stage_slot(G, kbt, t, limb, kb);
+          tma_load(base + t * B_TILE, &m.b[limb], static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+        }
+        issued = G + 1;
       }
       if (*abort) {
         // copies that may still be in flight land before the CTA goes on (bounded, no abort)
-        for (uint32_t kb = issued > QS ? issued - QS : 0; kb < issued; ++kb)
-          mbar_wait(q_full + 8 * (kb % QS), (kb / QS) & 1u, p.status, nullptr);
+        for (uint32_t G = issued > QS ? issued - QS : 0; G < issued; ++G)
+          mbar_wait(q_full + 8 * (G % QS), (G / QS) & 1u, p.status, nullptr);
       }
     }
   } else if (warp == 1) {
     // -------------------------------- MMA issuer --------------------------------
     if (lane == 0) {
+      const uint32_t t0 = tmem, t1 = tmem + TN;
+      uint32_t started0 = 0, started1 = 0;  // drain periods started per region
       bool ok = true;
-      for (uint32_t kb = 0; kb < p.kb_total && ok; ++kb) {
-        const uint32_t qs = kb % QS, ws = kb % WS, c = kb / KB_PER_CHUNK, j = kb % KB_PER_CHUNK;
-        if (!mbar_wait(q_full + 8 * qs, (kb / QS) & 1u, p.status, abort) ||
-            !mbar_wait(w_full + 8 * ws, (kb / WS) & 1u, p.status, abort))
+      for (uint32_t G = 0; G < n_stages && ok; ++G) {
+        const uint32_t s = G % QS;  // QS == WS
+        if (!mbar_wait(q_full + 8 * s, (G / QS) & 1u, p.status, abort) ||
+            !mbar_wait(w_full + 8 * s, (G / WS) & 1u, p.status, abort))
           break;
         fence_after();
-        const uint32_t qbase = qring + qs * Q_STAGE, dbase = wring + ws * W_STAGE;
-#pragma unroll
-        for (int g = 3; g >= 0; --g) {
-          const uint32_t per = period(g);
-          if (j == 0 && c % per == 0) {
-            // first k-block of a drain period of S_g: its previous period has been drained
-            if (!mbar_wait(g_empty + 8 * g, (c / per) & 1u, p.status, abort)) {
-              ok = false;
-              break;
-            }
-            fence_after();
-          }
-          const uint32_t t = tmem + TN * static_cast<uint32_t>(g);
+        const bool pass_a = G < kbt;
+        const uint32_t j = pass_a ? G : G - kbt;
+        const bool open1 = (j & 1u) == 0, close1 = (j & 1u) == 1;
+        const bool open0 = pass_a ? (j & 1u) == 0 : (j & 3u) == 0;
+        const bool close0 = pass_a ? (j & 1u) == 1 : (j & 3u) == 3;
+        const uint32_t qb = qring + s * Q_STAGE, wb = wring + s * W_STAGE;
+        if (open1) {
+          if (!mbar_wait(a_empty + 8, started1 & 1u, p.status, abort)) break;
+          ++started1;
+          fence_after();
+        }
+        if (pass_a) {
 #pragma unroll
           for (uint32_t ks = 0; ks < KB / 16; ++ks) {
             const uint32_t o = 32u * ks;  // 16 fp16 = 32 bytes along K inside the swizzled row
 #pragma unroll
-            for (int a = 0; a <= g; ++a)
-              umma(t, sdesc(dbase + a * W_TILE + o), sdesc(qbase + (g - a) * B_TILE + o), IDESC);
+            for (uint32_t a = 0; a < 4; ++a)  // S_3: x_a y_(3-a)
+              umma(t1, sdesc(wb + a * W_TILE + o), sdesc(qb + (3 - a) * B_TILE + o), IDESC);
           }
-          if (j == KB_PER_CHUNK - 1 && c % per == per - 1) umma_commit(g_full + 8 * g);
+        } else {
+#pragma unroll
+          for (uint32_t sub = 0; sub < 2; ++sub)
+#pragma unroll
+            for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+              const uint32_t o = 32u * ks, w = wb + 2 * sub * W_TILE + o, q = qb + 2 * sub * B_TILE + o;
+              umma(t1, sdesc(w), sdesc(q + B_TILE), IDESC);  // S_1: x_0 y_1
+              umma(t1, sdesc(w + W_TILE), sdesc(q), IDESC);  //      x_1 y_0
+            }
         }
-        if (ok) {  // both stages free once these (and all earlier) MMAs are done
-          umma_commit(q_empty + 8 * qs);
-          umma_commit(w_empty + 8 * ws);
+        if (close1) umma_commit(a_full + 8);
+        if (open0) {
+          if (!mbar_wait(a_empty, started0 & 1u, p.status, abort)) {
+            ok = false;
+            break;
+          }
+          ++started0;
+          fence_after();
         }
+        if (pass_a) {
+#pragma unroll
+          for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+            const uint32_t o = 32u * ks;
+#pragma unroll
+            for (uint32_t a = 0; a < 3; ++a)  // S_2: x_a y_(2-a)
+              umma(t0, sdesc(wb + a * W_TILE + o), sdesc(qb + (2 - a) * B_TILE + o), IDESC);
+          }
+        } else {
+#pragma unroll
+          for (uint32_t sub = 0; sub < 2; ++sub)
+#pragma unroll
+            for (uint32_t ks = 0; ks < KB / 16; ++ks) {
+              const uint32_t o = 32u * ks;  // S_0: x_0 y_0
+              umma(t0, sdesc(wb + 2 * sub * W_TILE + o), sdesc(qb + 2 * sub * B_TILE + o), IDESC);
+            }
+        }
+        if (close0) umma_commit(a_full);
+        // both slots free once these (and all earlier) MMAs are done
+        umma_commit(q_empty + 8 * s);
+        umma_commit(w_empty + 8 * s);
       }
       // every MMA issued above completes before the tensor memory is freed
       umma_commit(done_bar);
       mbar_wait(done_bar, 0, p.status, nullptr);
     }
-  } else if (warp >= WIDEN_WARP0) {
+  } else if (warp < DRAIN_WARP0) {
     // ------------------------- raw copies and widening ---------------------------
     const uint32_t ct = threadIdx.x - WIDEN_WARP0 * 32;
     uint32_t issued = 0;
-    auto load_raw = [&](uint32_t kb) {
-      const uint32_t s = kb % RS, full = r_full + 8 * s, base = rring + s * R_STAGE;
-      const bool first = kb < p.kb_half;
-      const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
+    auto load_raw = [&](uint32_t G) {
+      const uint32_t s = G % RS, full = r_full + 8 * s, base = rring + s * R_STAGE;
       mbar_expect_tx(full, R_STAGE);
 #pragma unroll
-      for (int a = 0; a < LIMBS; ++a)
-        tma_load(base + a * RAW_TILE, first ? &m.a0[a] : &m.a1[a], kx, static_cast<int32_t>(d0), full);
-      issued = kb + 1;
+      for (uint32_t t = 0; t < SLOTS; ++t) {
+        uint32_t limb, kb;
+        stage_slot(G, kbt, t, limb, kb);
+        const bool first = kb < p.kb_half;
+        const int32_t kx = static_cast<int32_t>((first ? kb : kb - p.kb_half) * KB);
+        tma_load(base + t * RAW_TILE, first ? &m.a0[limb] : &m.a1[limb], kx, static_cast<int32_t>(d0), full);
+      }
+      issued = G + 1;
     };
     if (ct == 0)
-      for (uint32_t kb = 0; kb < p.kb_total && kb < RS; ++kb) load_raw(kb);
-    uint32_t kb = 0;
-    for (; kb < p.kb_total; ++kb) {
-      const uint32_t rs = kb % RS, ws = kb % WS;
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_full + 8 * rs, (kb / RS) & 1u, p.status, abort) &&
-                                       mbar_wait(w_empty + 8 * ws, ((kb / WS) & 1u) ^ 1u, p.status, abort)))
+      for (uint32_t G = 0; G < n_stages && G < RS; ++G) load_raw(G);
+    uint32_t G = 0;
+    for (; G < n_stages; ++G) {
+      const uint32_t rs = G % RS, ws = G % WS;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_full + 8 * rs, (G / RS) & 1u, p.status, abort) &&
+                                       mbar_wait(w_empty + 8 * ws, ((G / WS) & 1u) ^ 1u, p.status, abort)))
         break;
-      widen_tiles<LIMBS, WIDEN_THREADS>(rring + rs * R_STAGE, RAW_TILE, wring + ws * W_STAGE, W_TILE, ct);
+      widen_tiles<SLOTS, WIDEN_THREADS>(rring + rs * R_STAGE, RAW_TILE, wring + ws * W_STAGE, W_TILE, ct);
       fence_proxy_async();  // the MMAs read these tiles through the async proxy
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(w_full + 8 * ws);
         mbar_arrive(r_empty + 8 * rs);  // this warp has read raw stage rs
       }
-      if (warp == WIDEN_WARP0 && kb + RS < p.kb_total) {
+      if (warp == WIDEN_WARP0 && G + RS < n_stages) {
         // refill once both warps have read the stage (a bounded wait, warp-uniform like the others)
-        if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_empty + 8 * rs, (kb / RS) & 1u, p.status, abort))) break;
-        if (lane == 0) load_raw(kb + RS);
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(r_empty + 8 * rs, (G / RS) & 1u, p.status, abort))) break;
+        if (lane == 0) load_raw(G + RS);
       }
     }
     if (ct == 0 && *abort) {
       // raw copies that may still be in flight land before the CTA leaves (bounded, no abort)
-      for (uint32_t h = kb; h < issued; ++h) mbar_wait(r_full + 8 * (h % RS), (h / RS) & 1u, p.status, nullptr);
+      for (uint32_t h = G; h < issued; ++h) mbar_wait(r_full + 8 * (h % RS), (h / RS) & 1u, p.status, nullptr);
     }
   } else {
     // ----------------------------------- drain ----------------------------------
-    const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - 2) >> 2;
-    const uint32_t tl = tmem + ((32u * q) << 16) + 64u * h;
+    const uint32_t q = static_cast<uint32_t>(warp) & 3u, h = static_cast<uint32_t>(warp - DRAIN_WARP0) >> 2;
+    const uint32_t tl = tmem + ((32u * q) << 16) + 128u * h;  // region 0; region 1 at + TN
+    const uint32_t row = d0 + 32 * q + lane;
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      tmem_fill32(tl + TN * g, MAGIC);
-      tmem_fill32(tl + TN * g + 32, MAGIC);
+    for (uint32_t g = 0; g < 4; ++g) {
+      tmem_fill32(tl + 32 * g, MAGIC);
+      tmem_fill32(tl + TN + 32 * g, MAGIC);
     }
     tmem_wait_st();
     fence_before();
     __syncwarp();
-    if (lane == 0)
-      for (int g = 0; g < 4; ++g) mbar_arrive(g_empty + 8 * g);
-    // each S_1 drain adds bits(M) << 8 and each S_0 drain bits(M) once too often
-    const uint32_t corr = 0u - (n_chunks / period(1)) * (MAGIC << 8) - (n_chunks / period(0)) * MAGIC;
-    uint32_t acc[64];
+    if (lane == 0) {
+      mbar_arrive(a_empty);
+      mbar_arrive(a_empty + 8);
+    }
+    uint32_t done0 = 0, done1 = 0;  // drains per region
+    // one drain of a region: wait for its full barrier, hand each 32-column group's fp32 bit
+    // patterns to f, re-base the accumulator, release the region
+    // (W columns at a time: 32 in pass A, 16 in pass B, whose 32-bit sums take 128 registers)
+    auto drain = [&](uint32_t region, uint32_t& done, auto&& f, auto width) -> bool {
+      constexpr uint32_t W = decltype(width)::value;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(a_full + 8 * region, done & 1u, p.status, abort))) return false;
+      ++done;
+      fence_after();
 #pragma unroll
-    for (int k = 0; k < 64; ++k) acc[k] = corr;
+      for (uint32_t g = 0; g < 128 / W; ++g) {
+        uint32_t r[W];
+        if constexpr (W == 32) {
+          tmem_ld32(tl + TN * region + W * g, r);
+        } else {
+          tmem_ld16(tl + TN * region + W * g, r);
+        }
+        tmem_wait_ld();
+        f(g, r);
+        if constexpr (W == 32) {
+          tmem_fill32(tl + TN * region + W * g, MAGIC);
+        } else {
+          tmem_fill16(tl + TN * region + W * g, MAGIC);
+        }
+      }
+      tmem_wait_st();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(a_empty + 8 * region);
+      return true;
+    };
     bool ok = true;
-    for (uint32_t c = 0; c < n_chunks && ok; ++c) {
+    {
+      // pass A: u[k] holds U mod 2^16 of columns 2k (low half) and 2k + 1 (high half); bits(M)
+      // is 0 mod 2^16, so the raw bits of a drained S_2 add as they are, S_3's shifted by 8
+      uint32_t u[64];
 #pragma unroll
-      for (int g = 3; g >= 0; --g) {
-        const uint32_t per = period(g);
-        if (c % per != per - 1) continue;
-        if (!__all_sync(0xFFFFFFFFu, mbar_wait(g_full + 8 * g, (c / per) & 1u, p.status, abort))) {
-          ok = false;
-          break;
+      for (int k = 0; k < 64; ++k) u[k] = 0;
+      for (uint32_t d = 0; d < kbt / 2 && ok; ++d) {
+        ok = drain(
+            1, done1,
+            [&](uint32_t g, const uint32_t (&r)[32]) {
+#pragma unroll
+              for (int k = 0; k < 16; ++k) u[16 * g + k] = add16x2(u[16 * g + k], pack_c16(r[2 * k], r[2 * k + 1]));
+            },
+            std::integral_constant<uint32_t, 32>{});
+        if (ok)
+          ok = drain(
+              0, done0,
+              [&](uint32_t g, const uint32_t (&r)[32]) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                  u[16 * g + k] = add16x2(u[16 * g + k], pack_lo16(r[2 * k], r[2 * k + 1]));
+              },
+              std::integral_constant<uint32_t, 32>{});
+      }
+      // U << 16 goes to z, where the epilogue adds pass B's sums and the zero shares to it
+      if (ok && row < p.x_rows) {
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+          const uint32_t c = q0 + 128 * h + 2 * k;
+          if (c < p.n_cols) p.z[static_cast<uint64_t>(c) * p.ldz + row] = u[k] << 16;
+          if (c + 1 < p.n_cols) p.z[static_cast<uint64_t>(c + 1) * p.ldz + row] = u[k] & 0xFFFF0000u;
         }
-        fence_after();
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          uint32_t r[32];
-          tmem_ld32(tl + TN * g + 32 * hh, r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int k = 0; k < 32; ++k) acc[32 * hh + k] += r[k] << (8 * g);
-          tmem_fill32(tl + TN * g + 32 * hh, MAGIC);
-        }
-        tmem_wait_st();
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(g_empty + 8 * g);
       }
     }
-    // ---- epilogue: z + r_i, r_i = F(seed_own) - F(seed_prev) over Z_{2^32} (App. C) ----
+    // pass B: 32-bit sums; each S_1 drain adds bits(M) << 8 and each S_0 drain bits(M) once too
+    // often, subtracted up front
+    const uint32_t corr = 0u - (kbt / 4) * (MAGIC << 8) - (kbt / 8) * MAGIC;
+    uint32_t acc[128];
+#pragma unroll
+    for (int k = 0; k < 128; ++k) acc[k] = corr;
+    for (uint32_t j = 0; j < kbt / 2 && ok; ++j) {
+      if ((j & 1u) == 1)
+        ok = drain(
+            1, done1,
+            [&](uint32_t g, const uint32_t (&r)[16]) {
+#pragma unroll
+              for (int k = 0; k < 16; ++k) acc[16 * g + k] += r[k] << 8;
+            },
+            std::integral_constant<uint32_t, 16>{});
+      if (ok && (j & 3u) == 3)
+        ok = drain(
+            0, done0,
+            [&](uint32_t g, const uint32_t (&r)[16]) {
+#pragma unroll
+              for (int k = 0; k < 16; ++k) acc[16 * g + k] += r[k];
+            },
+            std::integral_constant<uint32_t, 16>{});
+    }
+    // ---- epilogue: z = U << 16 + pass B + r_i, r_i = F(seed_own) - F(seed_prev) (App. C) ----
     // The sums go to shared memory (the Q ring is idle: the last S_0-full followed every MMA,
-    // and every copy was consumed), then each (column, 4-row group) item adds the zero shares of
-    // its four rows, one Philox block per seed, and writes 16 bytes of z.
+    // and every copy was consumed), then each (column, 4-row group) item adds U << 16 (from z)
+    // and the zero shares of its four rows, one Philox block per seed, and writes 16 bytes of z.
     named_sync(1, DRAIN_THREADS);
     if (!*abort) {  // uniform: read after the barrier that every drainer reaches
       uint32_t* zs = reinterpret_cast<uint32_t*>(smem);  // [TN][TM]
-      const uint32_t row = 32 * q + lane;
+      const uint32_t trow = 32 * q + lane;
 #pragma unroll
-      for (int k = 0; k < 64; ++k) zs[(64 * h + k) * TM + row] = acc[k];
+      for (int k = 0; k < 128; ++k) zs[(128 * h + k) * TM + trow] = acc[k];
       named_sync(1, DRAIN_THREADS);
-      const uint32_t dt = threadIdx.x - 64;
+      const uint32_t dt = threadIdx.x - DRAIN_WARP0 * 32;
       const uint32_t grp0 = static_cast<uint32_t>((p.row0 + d0) >> 2);
       const uint32_t ctr3 = (IPC_D_ZA32 << 24) | p.vec;
       for (uint32_t it = dt; it < TN * (TM / 4); it += DRAIN_THREADS) {
@@ -427,13 +552,15 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
         const uint4 fo = philox(grp0 + g4, tag, req, ctr3, p.seed_own);
         const uint4 fp = philox(grp0 + g4, tag, req, ctr3, p.seed_prev);
         const uint4 a = *reinterpret_cast<const uint4*>(zs + cc * TM + 4 * g4);
-        const uint4 v = make_uint4(a.x + fo.x - fp.x, a.y + fo.y - fp.y, a.z + fo.z - fp.z, a.w + fo.w - fp.w);
         uint32_t* dst = p.z + static_cast<uint64_t>(col) * p.ldz + r0;
         if (r0 + 4 <= p.x_rows) {
-          *reinterpret_cast<uint4*>(dst) = v;
+          const uint4 u = *reinterpret_cast<const uint4*>(dst);
+          const uint4 v = make_uint4(a.x + u.x + fo.x - fp.x, a.y + u.y + fo.y - fp.y, a.z + u.z + fo.z - fp.z,
+                                     a.w + u.w + fo.w - fp.w);
+          __stcs(reinterpret_cast<uint4*>(dst), v);  // streamed: z is read by a later kernel, not from L2
         } else {
-          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-          for (uint32_t e = 0; e < p.x_rows - r0; ++e) dst[e] = w[e];
+          const uint32_t av[4] = {a.x, a.y, a.z, a.w}, f[4] = {fo.x - fp.x, fo.y - fp.y, fo.z - fp.z, fo.w - fp.w};
+          for (uint32_t e = 0; e < p.x_rows - r0; ++e) dst[e] = av[e] + dst[e] + f[e];
         }
       }
     }
@@ -469,11 +596,11 @@ int ring_gemm_tc32(uint32_t segments, const int8_t* const x[8], size_t x_rows, c
     set_error("Z_2^32 ring GEMM: one or two K segments");
     return IPC_EINVAL;
   }
-  if ((segments * l) % (4 * KB_PER_CHUNK * KB) != 0) {
+  if ((segments * l) % (8 * KB) != 0) {
     set_error("Z_2^32 ring GEMM: K must be a multiple of 256");
     return IPC_EINVAL;
   }
-  if (n_pad % TN != 0 || n_cols > n_pad || ldz % 4 != 0 || ldz < x_rows || !aligned16(z)) {
+  if (n_pad % 128 != 0 || n_cols > n_pad || ldz % 4 != 0 || ldz < x_rows || !aligned16(z)) {
     set_error("Z_2^32 ring GEMM: n_pad % 128, n_cols <= n_pad, ldz % 4, ldz >= x_rows and a 16-byte aligned z");
     return IPC_EINVAL;
   }
@@ -484,10 +611,10 @@ int ring_gemm_tc32(uint32_t segments, const int8_t* const x[8], size_t x_rows, c
   }
   Maps32 m;
   int rc;
-  for (int i = 0; i < LIMBS; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if ((rc = make_map_f16(&m.b[i], b[i], static_cast<uint64_t>(segments) * l, n_pad, TN)) ||
         (rc = make_map_i8(&m.a0[i], x[i], l, x_rows, TM)) ||
-        (rc = make_map_i8(&m.a1[i], x[segments == 2 ? LIMBS + i : i], l, x_rows, TM)))
+        (rc = make_map_i8(&m.a1[i], x[segments == 2 ? 4 + i : i], l, x_rows, TM)))
       return rc;
   }
   Tc32Params p;

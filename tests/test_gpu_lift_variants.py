@@ -123,10 +123,11 @@ def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5)):
     return u32(z), ref.astype(np.uint32), tags
 
 
-@pytest.mark.parametrize("rows,N,segments,row0", [(300, 200, 2, 0), (1000, 93, 2, 1024), (130, 128, 1, 0)])
+@pytest.mark.parametrize("rows,N,segments,row0", [(300, 200, 2, 0), (1000, 93, 2, 1024), (130, 128, 1, 0),
+                                                    (260, 300, 2, 0)])
 def test_gemm_tc32_exact_on_random_limbs(torch, rows, N, segments, row0):
     """Equal seeds make the zero share vanish: z is the exact ring product; ragged row and column
-    tiles, one and two K segments."""
+    tiles (one and two 256-column tiles), one and two K segments."""
     z, ref, _ = _gemm_case(torch, rows, N, segments, row0)
     assert (z[:, :rows] == ref).all()
     assert (z[:, rows:] == 77).all()
