@@ -8,15 +8,16 @@
 // A3 (gemm_tc32_kernel): the ring dot product on tcgen05 with fp32 TMEM accumulators, exact:
 //     z = sum_s 2^(8s) S_s (mod 2^32),  S_s = sum over a + b = s of sum_k x_a[k] y_b[k],
 //   ten limb products per k (1 + 2 + 3 + 4 for s = 0..3); products with a + b > 3 vanish mod
-//   2^32. S_s has its own accumulator, started at M = 1.5 * 2^23 and drained while every partial
-//   sum stays within M +- 2^22 (so every fp32 addition is exact, as in the 16-bit kernel): S_s
-//   gains at most (s + 1) 2^14 per k, so S_3 and S_2 are drained every 64 k, S_1 every 128 k,
-//   S_0 every 256 k. A drain adds (bits - bits(M)) << 8s to a 32-bit running sum per column;
-//   bits(M) << 8s vanishes mod 2^32 for s >= 2, and the S_1 and S_0 terms are subtracted once,
-//   up front. The database limbs are widened from int8 to fp16 in shared memory, as in the
-//   16-bit kernel. Every wait is bounded (2 s, or sooner once another role has failed); a failed
-//   CTA raises the status word, lets its copies and MMAs finish, frees its tensor memory and
-//   stores nothing.
+//   2^32. Each S_s is accumulated in a TMEM accumulator started at M = 1.5 * 2^23 and drained
+//   while every partial sum stays within M +- 2^22 (so every fp32 addition is exact, as in the
+//   16-bit kernel): S_s gains at most (s + 1) 2^14 per k, so S_3 and S_2 are drained every 64 k,
+//   S_1 every 128 k, S_0 every 256 k. Two passes per tile (S_3 and S_2, then S_1 and S_0) share
+//   the 512 TMEM columns; a drain adds the raw bits, shifted by 8s, to running sums: mod 2^16
+//   for (S_2 + 2^8 S_3), whose bits(M) terms vanish, and mod 2^32 for S_0 + 2^8 S_1, whose
+//   bits(M) terms are subtracted once, up front. The database limbs are widened from int8 to
+//   fp16 in shared memory, as in the 16-bit kernel. Every wait is bounded (2 s, or sooner once
+//   another role has failed); a failed CTA raises the status word, lets its copies and MMAs
+//   finish and frees its tensor memory.
 #include <cuda_fp16.h>
 
 #include <mutex>
