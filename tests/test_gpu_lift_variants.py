@@ -92,7 +92,7 @@ def test_prep_query32_is_rotated_aby3_operand(torch):
             assert (got[Q * R:] == 0).all()
 
 
-def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5)):
+def _gemm_case(torch, rows, N, segments, row0, extreme=False, seeds=(5, 5), L=L):
     ipc = lib()
     n_pad = (N + 127) // 128 * 128
     K = segments * L
@@ -131,6 +131,17 @@ def test_gemm_tc32_exact_on_random_limbs(torch, rows, N, segments, row0):
     z, ref, _ = _gemm_case(torch, rows, N, segments, row0)
     assert (z[:, :rows] == ref).all()
     assert (z[:, rows:] == 77).all()
+
+
+@pytest.mark.parametrize("l,segments", [(256, 1), (128, 2), (768, 1)])
+def test_gemm_tc32_exact_at_short_k(torch, l, segments):
+    """The shortest K, 256 (eight k-blocks: pass A four drain periods, pass B four stages with a
+    single S_0 drain), over one segment and over two segments of 128 (the second segment
+    starting at a pass-B stage), and K = 768 (three S_0 periods)."""
+    z, ref, _ = _gemm_case(torch, 200, 280, segments, 0, L=l)
+    assert (z[:, :200] == ref).all()
+    ze, refe, _ = _gemm_case(torch, 128, 128, segments, 0, extreme=True, L=l)
+    assert (ze[:, :128] == refe).all()
 
 
 def test_gemm_tc32_exact_at_extreme_limbs(torch):
