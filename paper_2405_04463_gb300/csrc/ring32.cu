@@ -445,26 +445,48 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc32_kernel(const __grid_cons
     uint32_t done0 = 0, done1 = 0;  // drains per region
     // one drain of a region: wait for its full barrier, hand each 32-column group's fp32 bit
     // patterns to f, re-base the accumulator, release the region
-    // (W columns at a time: 32 in pass A, 16 in pass B, whose 32-bit sums take 128 registers)
+    // (W columns a load: 32 in pass A, two loads before each wait; 16 in pass B, one load a wait,
+    // whose 32-bit sums take 128 registers)
     auto drain = [&](uint32_t region, uint32_t& done, auto&& f, auto width) -> bool {
       constexpr uint32_t W = decltype(width)::value;
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(a_full + 8 * region, done & 1u, p.status, abort))) return false;
       ++done;
       fence_after();
-#pragma unroll
-      for (uint32_t g = 0; g < 128 / W; ++g) {
-        uint32_t r[W];
+      auto ld_ = [&](uint32_t g, uint32_t (&r)[W]) {
         if constexpr (W == 32) {
           tmem_ld32(tl + TN * region + W * g, r);
         } else {
           tmem_ld16(tl + TN * region + W * g, r);
         }
-        tmem_wait_ld();
-        f(g, r);
+      };
+      auto fill_ = [&](uint32_t g) {
         if constexpr (W == 32) {
           tmem_fill32(tl + TN * region + W * g, MAGIC);
         } else {
           tmem_fill16(tl + TN * region + W * g, MAGIC);
+        }
+      };
+      if constexpr (W == 32) {
+        // two loads in flight before each wait (pass A: 64 packed sums leave room for them)
+#pragma unroll
+        for (uint32_t g = 0; g < 128 / W; g += 2) {
+          uint32_t r[W], r2[W];
+          ld_(g, r);
+          ld_(g + 1, r2);
+          tmem_wait_ld();
+          f(g, r);
+          f(g + 1, r2);
+          fill_(g);
+          fill_(g + 1);
+        }
+      } else {
+#pragma unroll
+        for (uint32_t g = 0; g < 128 / W; ++g) {
+          uint32_t r[W];
+          ld_(g, r);
+          tmem_wait_ld();
+          f(g, r);
+          fill_(g);
         }
       }
       tmem_wait_st();
