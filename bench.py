@@ -18,6 +18,7 @@ CPU oracle (the 3-party simulation of Alg. 3) on bounded samples of the same wor
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -50,8 +51,10 @@ def parse():
     ap.add_argument("--no-i32", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=2048)
     ap.add_argument("--kernel", default=None, help="time one kernel alone: a ring-GEMM path (i8mix | i8mma | i32 | tc | tc32), "
-                    "compare, or overlap (Galois GEMM and comparison alone and on two streams)")
+                    "compare, overlap (Galois GEMM and comparison alone and on two streams), or fused "
+                    "(the fused chunk step against the unfused one)")
     ap.add_argument("--rows", type=int, default=16384, help="database rows of the --kernel case")
+    ap.add_argument("--fused-path", default="tcg", choices=["tc", "tcg"], help="sharing of --kernel fused")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--serving", action="store_true",
                     help="serving run: Poisson arrivals of 1..256-query batches at 3 rates (workload c4)")
@@ -173,6 +176,52 @@ def run_overlap(args, w):
                       "note": "per pair of launches, host wall clock around reps launches on two streams"}))
 
 
+def run_fused(args, w):
+    """The chunk step of a context, fused (one gemm_cmp_kernel launch per chunk: the six ring GEMMs
+    tile by tile and each tile's comparison phase, then the block join) and unfused (six GEMM
+    launches on the party streams and one comparison launch), on the workload's first --rows
+    database rows (one resident chunk for --rows <= 65,536), Galois-ring Shamir dots (--path tcg,
+    the default) or replicated sharing (tc). Steps timed with CUDA events on the control stream."""
+    import torch
+
+    import paper_2405_04463_gb300 as ipc
+    from paper_2405_04463_gb300.workload import galois, load_workload, make_ctx, query_shares_gpu
+
+    wr = dataclasses.replace(w, s=args.rows)
+    gal = galois(args.fused_path)
+    qc, qm = query_shares_gpu(wr, galois_shares=gal)
+    out = {"kernel": "fused", "path": args.fused_path, "rows": args.rows, "cols": wr.Q * wr.R}
+    bits = {}
+    for fused in (False, True):
+        ctx = make_ctx(wr, path=args.fused_path, max_queries=wr.Q, max_requests=SLOTS, fused=fused)
+        try:
+            load_workload(ctx, wr, chunk=16384, galois_shares=gal)
+            stream = torch.cuda.ExternalStream(ipc.ipc_ctx_stream(ctx))
+            b = np.zeros(wr.Q, np.uint8)
+
+            def steps(k):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                rids = [ipc.submit_queries(ctx, [qc[j] for j in range(3)], [qm[j] for j in range(3)], wr.Q, 1)
+                        for _ in range(k)]
+                e1.record(stream)
+                for r in rids:
+                    ipc.fetch_match_bits(ctx, r, b, wr.Q, -1)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1) / k
+
+            steps(1)
+            ms = steps(max(1, min(args.reps, SLOTS)))
+        finally:
+            ipc.ipc_destroy(ctx)
+        key = "fused" if fused else "unfused"
+        out[key] = {"ms_per_step": ms, "comparisons_per_s": wr.comparisons / (ms * 1e-3)}
+        bits[key] = b.copy()
+    out["bits_equal"] = bool((bits["fused"] == bits["unfused"]).all())
+    print(json.dumps(out))
+
+
 def run_kernel(args, w):
     """One ring-GEMM launch shape of the workload (all its query columns x --rows rows), random
     operands, timed alone with CUDA events; used for ncu captures on a small case."""
@@ -183,6 +232,8 @@ def run_kernel(args, w):
         return run_compare_kernel(args, w)
     if args.kernel == "overlap":
         return run_overlap(args, w)
+    if args.kernel == "fused":
+        return run_fused(args, w)
     l, N = w.l, w.Q * w.R
     n_pad = (N + 127) // 128 * 128
     rows = args.rows
@@ -492,9 +543,10 @@ def run_ours(args, w):
     ctxs.clear()
     torch.cuda.empty_cache()
 
-    def other(path, plain=False, lift=None):
+    def other(path, plain=False, lift=None, fused=False):
         gal = galois(path)
-        ctx = make_ctx(w, path=path, max_queries=w.Q, plain_mask=plain, lift=lift or "mpc", max_requests=SLOTS)
+        ctx = make_ctx(w, path=path, max_queries=w.Q, plain_mask=plain, lift=lift or "mpc", max_requests=SLOTS,
+                       fused=fused)
         try:
             load_workload(ctx, w, chunk=32768, galois_shares=gal, plain_mask=plain, lift=lift)
             run_steps(ctx, 1, False, gal, plain, lift)
@@ -508,6 +560,9 @@ def run_ours(args, w):
                 "bits_equal_to_headline_path": bool((b == bits).all())}
 
     out_gal = other("tcg")
+    # the fused chunk step (six ring GEMMs and the comparison phase in one launch per chunk)
+    out_fused_gal = other("tcg", fused=True)
+    out_fused = other("tc", fused=True)
     out_plain = other("tc", plain=True)
     out_plain_gal = other("tcg", plain=True)
     out_const = other("tc", lift="const")
@@ -644,6 +699,12 @@ def run_ours(args, w):
         "galois_shamir_path": dict(out_gal, note="the paper's deployed sharing of the dot products "
                                                  "(Sec. 4.3.2): one length-l GEMM per party and vector "
                                                  "instead of 2l, same tcgen05 kernel, same comparison phase"),
+        "fused_step": {
+            "galois_shamir": dict(out_fused_gal, unfused_ms_per_step=out_gal.get("ms_per_step")),
+            "replicated": dict(out_fused, unfused_ms_per_step=ms_main),
+            "note": "Sec. 6.4's dots and comparisons of a chunk in one launch: the six ring GEMMs tile by tile "
+                    "(gemm_cmp_kernel), each tile's comparison phase run by its drain warps after the sixth "
+                    "GEMM, z read back from L2; then the block join of the part roots"},
         "plain_mask_path": dict(out_plain, galois_shamir=out_plain_gal,
                                 note="protocol 1 (Sec. 4, Alg. 2): public masks, ml one plaintext GEMM "
                                      "(K = l) instead of three shared ones, 16-bit comparison (29 ANDs)"),

@@ -444,6 +444,13 @@ typedef struct {
   uint32_t max_requests;    /* request slots: requests submitted and not yet fetched or released,
                                at most 64; 0 = 4. Each slot holds every per-request buffer for
                                max_queries queries, allocated by the first submit_queries. */
+  uint32_t fused;           /* nonzero: each resident chunk of a request runs as one fused launch,
+                               the six ring GEMMs (A3) tile by tile with each tile's comparison
+                               phase (A4-A8) after its sixth GEMM, in place of six GEMM launches on
+                               the party streams and one comparison launch (Sec. 6.4 runs the dots
+                               and then the comparisons of the same rows). IPC_PATH_TC or
+                               IPC_PATH_TCG with shared masks and MPCLift; submit_queries only (not
+                               serving or ipc_check_persons). Same shares, bits and messages. */
 } ipc_config;
 
 /* Creates a context on cfg->device: the three MPC parties of Alg. 3 (Sec. 2, App. C: 3-party

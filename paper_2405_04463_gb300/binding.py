@@ -48,7 +48,7 @@ class ipc_config(ctypes.Structure):
                 ("db_chunk_rows", ctypes.c_uint32), ("max_queries", ctypes.c_uint32),
                 ("seeds", ctypes.c_uint64 * 3), ("keep_distances", ctypes.c_uint32), ("device", ctypes.c_int32),
                 ("plain_mask", ctypes.c_uint32), ("lift", ctypes.c_uint32), ("thr_b", ctypes.c_uint32),
-                ("max_requests", ctypes.c_uint32)]
+                ("max_requests", ctypes.c_uint32), ("fused", ctypes.c_uint32)]
 
 
 LIFTS = {"mpc": 0, "const": 1, "none": 2}
@@ -326,7 +326,7 @@ def ipc_selftest_bounded_wait(limit_us, stream=None):
 def make_config(geom: ipc_geom | None = None, thr_a: int = 16384, path="i8mma", db_chunk_rows: int = 0,
                 max_queries: int = 0, seeds=(0x51EED0, 0x51EED1, 0x51EED2), keep_distances: bool = False,
                 device: int = 0, plain_mask: bool = False, lift="mpc", thr_b: int = 0,
-                max_requests: int = 0) -> ipc_config:
+                max_requests: int = 0, fused: bool = False) -> ipc_config:
     c = ipc_config()
     c.geom = geom if geom is not None else iris_geom()
     c.thr_a = thr_a
@@ -341,6 +341,7 @@ def make_config(geom: ipc_geom | None = None, thr_a: int = 16384, path="i8mma", 
     c.lift = LIFTS.get(lift, lift)
     c.thr_b = thr_b
     c.max_requests = max_requests
+    c.fused = 1 if fused else 0
     return c
 
 

@@ -86,11 +86,25 @@ int ensure_zbuf(ipc_ctx* c, uint32_t n_pad) {
   return IPC_OK;
 }
 
+// The fused step's part roots of one chunk: 3 components x n_pad columns x chunk_rows / 128 parts.
+int ensure_parts(ipc_ctx* c, uint32_t n_pad) {
+  if (!c->cfg.fused || c->parts_cols >= n_pad) return IPC_OK;
+  const size_t bytes = 3ull * n_pad * (c->cfg.db_chunk_rows / 128) * sizeof(uint32_t);
+  if (cudaMalloc(&c->parts, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, IPC_ENOMEM, "cannot allocate the fused step's part roots for " + std::to_string(n_pad) + " columns");
+  }
+  c->parts_cols = n_pad;
+  return IPC_OK;
+}
+
 // Creates the request slots and the dot-product scratch for max_queries queries (once).
 int ensure_slots(ipc_ctx* c) {
   if (!c->slots.empty()) return IPC_OK;
   const uint32_t Qm = c->cfg.max_queries, n_pad = round_up(Qm * c->cfg.geom.R, 128);
   int rc = ensure_zbuf(c, n_pad);
+  if (rc) return rc;
+  rc = ensure_parts(c, n_pad);
   if (rc) return rc;
   const size_t qes = c->cfg.lift ? 4 : 2;  // bytes per staged query element
   std::vector<Slot> slots(c->cfg.max_requests);
@@ -192,6 +206,8 @@ extern "C" int ipc_create(const ipc_config* cfg, ipc_ctx** out) {
     return fail(nullptr, IPC_EINVAL, "ipc_create: thr_b is 2^16 unless lift is IPC_LIFT_NONE (then 1..2^16)");
   if (cfg->db_chunk_rows % 1024 != 0) return fail(nullptr, IPC_EINVAL, "ipc_create: db_chunk_rows % 1024 != 0");
   if (cfg->max_requests > 64) return fail(nullptr, IPC_EINVAL, "ipc_create: max_requests is at most 64");
+  if (cfg->fused && ((cfg->path != IPC_PATH_TC && cfg->path != IPC_PATH_TCG) || cfg->plain_mask || cfg->lift))
+    return fail(nullptr, IPC_EINVAL, "ipc_create: the fused step needs the tc or tcg path with shared masks and MPCLift");
   ipc_ctx* c = new ipc_ctx();
   c->cfg = *cfg;
   if (c->cfg.db_chunk_rows == 0) c->cfg.db_chunk_rows = 65536;
@@ -233,6 +249,7 @@ extern "C" void ipc_destroy(ipc_ctx* c) {
   for (auto& s : c->slots) free_slot(s);
   for (auto& ch : c->chunks) cudaFree(ch.planes);
   cudaFree(c->zbuf);
+  cudaFree(c->parts);
   cudaFree(c->stage);
   cudaFree(c->stall_flag);
   for (int i = 0; i < 3; ++i)
@@ -468,6 +485,14 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
   }
   auto i8p = [](const uint8_t* p) { return reinterpret_cast<const int8_t*>(p); };
   auto cf16 = [](const uint8_t* p) { return reinterpret_cast<const uint16_t*>(p); };
+  const bool fused = c->cfg.fused != 0;
+  if (fused) {
+    // one kernel per chunk on the control stream runs every party's GEMMs and the comparison phase
+    for (int i = 0; i < 3; ++i) {
+      SUB_TRY(cudaEventRecord(c->ev_gemm[i][0], c->sp[i]));
+      SUB_TRY(cudaStreamWaitEvent(c->sc, c->ev_gemm[i][0], 0));
+    }
+  }
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const Chunk& ch = c->chunks[ci];
     if (ch.rows == 0) continue;
@@ -487,6 +512,29 @@ extern "C" int submit_queries(ipc_ctx* c, const uint16_t* const code[3], const u
         zm[i] = zslot(c, set, 1, i);
         ldz = c->cfg.db_chunk_rows;
       }
+    }
+    if (fused) {
+      // Sec. 6.4's two phases of a chunk in one launch: the six ring GEMMs tile by tile, each
+      // tile's comparison after its sixth pass; then the block roots from the part roots
+      const int8_t* xl[6];
+      const int8_t* xh[6];
+      const uint16_t* bl[6];
+      const uint16_t* bh[6];
+      uint16_t* zo[6];
+      for (int j = 0; j < 3; ++j)
+        for (int vec = 0; vec < 2; ++vec) {
+          xl[2 * j + vec] = i8p(plane(c, ch, j, vec, 0));
+          xh[2 * j + vec] = i8p(plane(c, ch, j, vec, 1));
+          bl[2 * j + vec] = cf16(bq(j, vec, 0));
+          bh[2 * j + vec] = cf16(bq(j, vec, 1));
+          zo[2 * j + vec] = reinterpret_cast<uint16_t*>(vec == 0 ? zc[j] : zm[j]);
+        }
+      const size_t ld_parts = c->cfg.db_chunk_rows / 128;
+      SUB_RC(ring_gemm_compare_tc(c->cfg.path == IPC_PATH_TCG ? 1u : 2u, xl, xh, ch.rows, bl, bh, N, n_pad, l, sl.tags,
+                                  c->cfg.seeds, c->cfg.thr_a, zo, ldz, ch.row0, c->parts, ld_parts, c->sc));
+      SUB_RC(or_join_parts_launch(c->parts, ld_parts, N, ch.rows, ch.row0, sl.tags, c->cfg.seeds, sl.roots,
+                                  r.ld_roots, c->sc));
+      continue;
     }
     for (int i = 0; i < 3; ++i) {
       const int prev = (i + 2) % 3;

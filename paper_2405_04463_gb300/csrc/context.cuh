@@ -76,6 +76,14 @@ int compare_launch_liftfree(const uint16_t* const zc16[3], const uint32_t* const
                             const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a, uint32_t thr_b,
                             uint32_t p, uint32_t* roots, size_t ld_roots, uint8_t* msb_out, size_t ld_msb,
                             cudaStream_t st);
+int ring_gemm_compare_tc(uint32_t segments, const int8_t* const x_lo[6], const int8_t* const x_hi[6], size_t x_rows,
+                         const uint16_t* const b_lo[6], const uint16_t* const b_hi[6], uint32_t n_cols, uint32_t n_pad,
+                         uint32_t l, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
+                         uint16_t* const z[6], size_t ldz, uint64_t row0, uint32_t* part_roots, size_t ld_parts,
+                         cudaStream_t stream);
+int or_join_parts_launch(const uint32_t* parts, size_t ld_parts, uint32_t n_cols, size_t n_rows, uint64_t row0,
+                         const uint32_t* col_tags, const uint64_t seeds[3], uint32_t* roots, size_t ld_roots,
+                         cudaStream_t st);
 int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const int8_t* const x_lo[2],
                          const int8_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo, const uint16_t* b_hi,
                          uint32_t n_cols, uint32_t n_pad, uint32_t l, const uint32_t* col_tags, uint64_t seed_own,
@@ -105,6 +113,8 @@ struct ipc_ctx {
   size_t rows = 0;
   uint8_t* zbuf = nullptr;  // [2 sets][vec][party][zbuf_cols][chunk_rows] of zsz-byte elements
   size_t zbuf_cols = 0;
+  uint32_t* parts = nullptr;  // fused step: [3][parts_cols][chunk_rows / 128] part roots of one chunk
+  size_t parts_cols = 0;
   uint8_t* stage = nullptr;  // load staging [chunk_rows][l] u16 (u32 with a lifting variant)
   std::map<uint64_t, ipc::Request> reqs;
   std::vector<ipc::Slot> slots;  // request slots, created by the first submit_queries

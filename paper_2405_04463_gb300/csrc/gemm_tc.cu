@@ -41,6 +41,7 @@
 // Tile widths TN = 256 (the fixed-shape launch) and 128; see gemm_tc_kernel for the list mode.
 // Every wait is bounded (2 s, or sooner once another role has failed); a failed CTA raises the
 // status word, lets its copies and MMAs finish, frees its tensor memory and stores nothing.
+#include "compare.cuh"
 #include "tcgen05.cuh"
 
 namespace ipc {
@@ -104,17 +105,82 @@ struct TcParams {
   uint32_t* status;
 };
 
+// Fused form (gemm_cmp_kernel, Sec. 6.4's dots followed by the comparisons of the same rows): the
+// six ring GEMMs of one chunk -- pass ps = 0..5 is party ps / 2, vector ps % 2 -- run tile after
+// tile in one persistent launch, each a complete item of the pipeline above with its own query
+// and database tensor maps, zero shares and z output. z stays in L2 (plain stores), and after a
+// tile's sixth pass the drain warps run the comparison phase (A4-A8) on the tile: one (column,
+// 128-row part) unit per drain thread, through the same part routine and gate numbering as the
+// stand-alone comparison kernel, its scratch in the Q ring (idle until the drain releases it).
+// The part roots are joined into 1,024-row block roots by or_join_parts afterwards.
+constexpr uint32_t NPASS = 6;
+struct FuseMaps {
+  CUtensorMap q[NPASS][2];  // query operand of pass ps (party ps / 2, vector ps % 2): lo, hi limbs
+  CUtensorMap x[NPASS][2];  // database planes of component c, vector v at 2 c + v: lo, hi limbs
+};
+struct FuseParams {
+  uint32_t n_ct;           // column tiles of the launch
+  uint16_t* z[NPASS];      // z of pass ps, [n_cols][ldz]
+  uint64_t seeds[3];       // seeds[j] shared by parties j and j + 1
+  uint32_t thr_a;
+  uint32_t* part_roots;    // [3][n_cols][ld_parts]: OR root of (column, row tile) of the chunk
+  uint64_t ld_parts;
+};
+// The six tensor maps of a one-pass launch (kernel parameters).
+struct MapRefs {
+  const CUtensorMap *b_lo, *b_hi, *a0_lo, *a0_hi, *a1_lo, *a1_hi;
+};
+constexpr uint32_t FUSE_LOG2_BLOCK = 5;  // 1,024-row OR blocks: 8 row tiles of 128 rows
+
 // Without a list (LIST false) the grid is (column tiles, row tiles), one tile per CTA. With a list,
 // gridDim.x persistent CTAs walk items w = blockIdx.x + i * gridDim.x: column tile
 // list[w % n_ct], row tile w / n_ct; k-block and chunk counters run on across items, and the
 // query producer starts an item's copies once the previous item's epilogue has left the Q ring
 // (the raw and widened rings run on into the next item meanwhile).
-template <int TN, bool LIST>
-__global__ void __launch_bounds__(THREADS, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tb_lo, const __grid_constant__ CUtensorMap tb_hi,
-                   const __grid_constant__ CUtensorMap ta0_lo, const __grid_constant__ CUtensorMap ta0_hi,
-                   const __grid_constant__ CUtensorMap ta1_lo, const __grid_constant__ CUtensorMap ta1_hi,
-                   const TcParams p) {
+// bar.sync over n threads that also returns, to every one of them, whether any had pred set.
+__device__ __forceinline__ bool named_sync_or(uint32_t id, uint32_t n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(pred ? 1u : 0u), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// The comparison phase of one (column n, row tile rt) part in the fused form: z of the chunk's six
+// passes from global memory, the part's OR root to fp.part_roots. Not inlined, so that its
+// registers do not weigh on the drain loop around it.
+__device__ __noinline__ void fused_part_compare(const TcParams& p, const FuseParams& fp, uint32_t n, uint32_t rt,
+                                                uint32_t* scratch, uint32_t tid) {
+  cmp::CmpParams P{};
+  for (int j = 0; j < 3; ++j) {
+    P.zc[j] = fp.z[2 * j];
+    P.zm[j] = fp.z[2 * j + 1];
+    P.seeds.s[j] = fp.seeds[j];
+  }
+  P.ldz = p.ldz;
+  P.n_cols = p.n_cols;
+  P.n_rows = p.x_rows;
+  P.row0 = p.row0;
+  P.col_tags = p.col_tags;
+  P.thr_a = fp.thr_a;
+  P.p = FUSE_LOG2_BLOCK;
+  cmp::B3 root;
+  uint32_t nw;
+  cmp::part_root<cmp::MODE_LIFT, DRAIN_THREADS>(P, n, rt >> 3, rt & 7u, 3u, scratch, tid, root, nw);
+  const uint64_t plane = static_cast<uint64_t>(p.n_cols) * fp.ld_parts;
+  const uint64_t at = static_cast<uint64_t>(n) * fp.ld_parts + rt;
+  fp.part_roots[at] = root.c0;
+  fp.part_roots[plane + at] = root.c1;
+  fp.part_roots[2 * plane + at] = root.c2;
+}
+
+template <int TN, bool LIST, bool FUSE>
+__device__ __forceinline__ void gemm_tc_body(const MapRefs& mr, const FuseMaps* fm, const TcParams& p,
+                                             const FuseParams& fp) {
+  static_assert(!(LIST && FUSE), "the fused form walks the fixed shape");
+  constexpr bool PERSIST = LIST || FUSE;
   using S = Shape<TN>;
   constexpr int B_BYTES = S::B_BYTES;
   extern __shared__ uint8_t smem_raw[];
@@ -127,6 +193,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     my_items = n_items > blockIdx.x ? (n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     if (my_items == 0) return;  // uniform for the CTA, before any barrier or allocation
   }
+  if (FUSE) {
+    // items: the six passes of each of this CTA's tiles, tile after tile
+    n_ct = fp.n_ct;
+    const uint32_t n_tiles = n_ct * p.n_row_tiles;
+    const uint32_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (my_tiles == 0) return;
+    my_items = my_tiles * NPASS;
+  }
   // Tiles are taken in linear order (blocks are dispatched in blockIdx order; a persistent CTA
   // takes items blockIdx.x + i gridDim.x). The order walks bands of up to kBand column tiles,
   // all row tiles of a band before the next, so that the tiles in flight at once (one CTA per
@@ -135,9 +209,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   // query columns the whole query operand is several times the L2).
   constexpr uint32_t kBand = 8;
   auto coords = [&](uint32_t i, uint32_t& q0, uint32_t& d0) {
-    const uint32_t n_cols_t = LIST ? n_ct : gridDim.x;
-    const uint32_t n_rt = LIST ? p.n_row_tiles : gridDim.y;
-    const uint32_t lin = LIST ? blockIdx.x + i * gridDim.x : blockIdx.x + gridDim.x * blockIdx.y;
+    const uint32_t n_cols_t = PERSIST ? n_ct : gridDim.x;
+    const uint32_t n_rt = PERSIST ? p.n_row_tiles : gridDim.y;
+    const uint32_t lin = FUSE   ? blockIdx.x + (i / NPASS) * gridDim.x
+                         : LIST ? blockIdx.x + i * gridDim.x
+                                : blockIdx.x + gridDim.x * blockIdx.y;
     const uint32_t band = lin / (kBand * n_rt), c0 = band * kBand;
     const uint32_t width = n_cols_t - c0 < kBand ? n_cols_t - c0 : kBand;
     const uint32_t in_band = lin - band * kBand * n_rt;
@@ -199,9 +275,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           const uint32_t full = q_full + 8 * s, base = qring + s * S::Q_STAGE;
+          const CUtensorMap* mlo = FUSE ? &fm->q[i % NPASS][0] : mr.b_lo;
+          const CUtensorMap* mhi = FUSE ? &fm->q[i % NPASS][1] : mr.b_hi;
           mbar_expect_tx(full, 2 * B_BYTES);
-          tma_load(base, &tb_lo, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
-          tma_load(base + B_BYTES, &tb_hi, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+          tma_load(base, mlo, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
+          tma_load(base + B_BYTES, mhi, static_cast<int32_t>(kb * KB), static_cast<int32_t>(q0), full);
           issued = G + 1;
         }
       }
@@ -280,12 +358,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     // k-block G + RS into raw stage G % RS once the warp has read k-block G from it.
     const uint32_t pl = static_cast<uint32_t>(warp - WIDEN_WARP0);  // 0: lo limbs, 1: hi limbs
     const uint32_t rf = r_full + 8 * RS * pl;
-    const CUtensorMap* map0 = pl ? &ta0_hi : &ta0_lo;
-    const CUtensorMap* map1 = pl ? &ta1_hi : &ta1_lo;
-    // the next raw copy (lane 0): k-block li_kb of item li, whose row offset li_d0 is looked up
-    // once per item, so that a copy costs no division
+    // the database planes of item i's two K segments: components ps / 2 and ps / 2 - 1 of the
+    // pass's vector in the fused form
+    auto seg_maps = [&](uint32_t i, const CUtensorMap*& m0, const CUtensorMap*& m1) {
+      if (FUSE) {
+        const uint32_t ps = i % NPASS, party = ps >> 1, vec = ps & 1u;
+        m0 = &fm->x[2 * party + vec][pl];
+        m1 = &fm->x[2 * ((party + 2) % 3) + vec][pl];
+      } else {
+        m0 = pl ? mr.a0_hi : mr.a0_lo;
+        m1 = pl ? mr.a1_hi : mr.a1_lo;
+      }
+    };
+    const CUtensorMap *map0, *map1;
+    // the next raw copy (lane 0): k-block li_kb of item li, whose row offset li_d0 and tensor
+    // maps are looked up once per item, so that a copy costs no division
     uint32_t issued = 0, li = 0, li_kb = 0, li_q0 = 0, li_d0 = 0;
     coords(0, li_q0, li_d0);
+    seg_maps(0, map0, map1);
     auto load_raw = [&](uint32_t G) {
       const uint32_t s = G % RS;
       const bool first = li_kb < p.kb_half;
@@ -295,7 +385,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       issued = G + 1;
       if (++li_kb == p.kb_total) {
         li_kb = 0;
-        if (++li < my_items) coords(li, li_q0, li_d0);
+        if (++li < my_items) {
+          coords(li, li_q0, li_d0);
+          seg_maps(li, map0, map1);
+        }
       }
     };
     if (lane == 0)
@@ -387,10 +480,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       // item's last L-full and before the query producer sees epi-done), then each (column, 8-row
       // group) item adds its zero shares, which one Philox block per seed gives for all 8 rows,
       // and writes 16 bytes of z.
-      named_sync(1, DRAIN_THREADS);
-      if (*abort) break;  // uniform: read after the barrier that every drainer reaches
+      // every drainer takes the same decision: the barrier returns whether any of them saw the
+      // abort flag
+      if (named_sync_or(1, DRAIN_THREADS, *abort != 0)) break;
       uint32_t q0, d0;
       coords(i, q0, d0);
+      const uint32_t ps = FUSE ? i % NPASS : 0u, party = ps >> 1;
+      const uint64_t seed_own = FUSE ? fp.seeds[party] : p.seed_own;
+      const uint64_t seed_prev = FUSE ? fp.seeds[(party + 2) % 3] : p.seed_prev;
+      const uint32_t vec = FUSE ? (ps & 1u) : p.vec;
+      uint16_t* const zout = FUSE ? fp.z[ps] : p.z;
       uint16_t* zs = reinterpret_cast<uint16_t*>(smem);  // [TN][TM]
       const uint32_t row = 32 * q + lane;
 #pragma unroll
@@ -401,13 +500,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       named_sync(1, DRAIN_THREADS);
       const uint32_t dt = threadIdx.x - 64;
       const uint32_t grp0 = static_cast<uint32_t>((p.row0 + d0) >> 3);
-      const uint32_t ctr3 = (IPC_D_ZA << 24) | p.vec;
+      const uint32_t ctr3 = (IPC_D_ZA << 24) | vec;
       for (uint32_t it = dt; it < TN * (TM / 8); it += DRAIN_THREADS) {
         const uint32_t cc = it / (TM / 8), g = it % (TM / 8), col = q0 + cc, r0 = d0 + 8 * g;
         if (col >= p.n_cols || r0 >= p.x_rows) continue;
         const uint32_t req = p.col_tags[2 * col], tag = p.col_tags[2 * col + 1];
-        const uint4 fo = philox(grp0 + g, tag, req, ctr3, p.seed_own);
-        const uint4 fp = philox(grp0 + g, tag, req, ctr3, p.seed_prev);
+        const uint4 fo = philox(grp0 + g, tag, req, ctr3, seed_own);
+        const uint4 fq = philox(grp0 + g, tag, req, ctr3, seed_prev);
         const uint4 acc = *reinterpret_cast<const uint4*>(zs + cc * TM + 8 * g);
         // per 16-bit half: z = acc + (F_own - F_prev)  (mod 2^16)
         auto add2 = [](uint32_t a, uint32_t o, uint32_t f) {
@@ -415,15 +514,25 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t hi = ((a >> 16) + (o >> 16) - (f >> 16)) << 16;
           return lo | hi;
         };
-        const uint4 v = make_uint4(add2(acc.x, fo.x, fp.x), add2(acc.y, fo.y, fp.y), add2(acc.z, fo.z, fp.z),
-                                   add2(acc.w, fo.w, fp.w));
-        uint16_t* dst = p.z + static_cast<uint64_t>(col) * p.ldz + r0;
+        const uint4 v = make_uint4(add2(acc.x, fo.x, fq.x), add2(acc.y, fo.y, fq.y), add2(acc.z, fo.z, fq.z),
+                                   add2(acc.w, fo.w, fq.w));
+        uint16_t* dst = zout + static_cast<uint64_t>(col) * p.ldz + r0;
         if (r0 + 8 <= p.x_rows) {
-          __stcs(reinterpret_cast<uint4*>(dst), v);  // streamed: z is read by a later kernel, not from L2
+          if (FUSE)
+            *reinterpret_cast<uint4*>(dst) = v;  // kept in L2: this CTA reads it back after the tile's last pass
+          else
+            __stcs(reinterpret_cast<uint4*>(dst), v);  // streamed: z is read by a later kernel, not from L2
         } else {
           const uint32_t w[4] = {v.x, v.y, v.z, v.w};
           for (uint32_t e = 0; e < p.x_rows - r0; ++e) dst[e] = static_cast<uint16_t>(w[e >> 1] >> (16 * (e & 1)));
         }
+      }
+      if (FUSE && ps == NPASS - 1) {
+        // ---- A4-A8 on the tile: its six z tiles are in global memory (L2), written by this
+        // CTA's drainers; the barrier orders those stores before the reads below ----
+        named_sync(1, DRAIN_THREADS);
+        const uint32_t n = q0 + dt;
+        if (n < p.n_cols) fused_part_compare(p, fp, n, d0 / TM, reinterpret_cast<uint32_t*>(smem), dt);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(epi_done);  // this warp is done with the Q ring
@@ -435,6 +544,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
   }
+}
+
+template <int TN, bool LIST>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tb_lo, const __grid_constant__ CUtensorMap tb_hi,
+                   const __grid_constant__ CUtensorMap ta0_lo, const __grid_constant__ CUtensorMap ta0_hi,
+                   const __grid_constant__ CUtensorMap ta1_lo, const __grid_constant__ CUtensorMap ta1_hi,
+                   const TcParams p) {
+  gemm_tc_body<TN, LIST, false>(MapRefs{&tb_lo, &tb_hi, &ta0_lo, &ta0_hi, &ta1_lo, &ta1_hi}, nullptr, p,
+                                FuseParams{});
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_cmp_kernel(const __grid_constant__ FuseMaps fm, const __grid_constant__ TcParams p,
+                    const __grid_constant__ FuseParams fp) {
+  gemm_tc_body<256, false, true>(MapRefs{}, &fm, p, fp);
 }
 
 template <int TN, bool LIST>
@@ -502,6 +627,70 @@ int ring_gemm_tc_variant(uint32_t tile_cols, uint32_t segments, const int8_t* co
   }
   const dim3 grid((n_cols + tile_cols - 1) / tile_cols, p.n_row_tiles);
   return tile_cols == 256 ? launch_tc<256, false>(m, p, grid, stream) : launch_tc<128, false>(m, p, grid, stream);
+}
+
+// The fused chunk step: the six ring GEMMs of a chunk (replicated sharing, segments = 2: party i
+// reads components i and i - 1 of each vector; Galois-ring Shamir shares, segments = 1: party i
+// reads its own share) and the comparison phase of every tile, in one persistent launch of one CTA
+// per SM. x_lo / x_hi[2 c + v]: database limb planes of component c, vector v (0 code, 1 mask),
+// [x_rows][l] int8; b_lo / b_hi[2 i + v]: party i's query operand of vector v, [n_pad][segments l]
+// fp16 patterns; z[2 i + v]: party i's z of vector v, [n_cols][ldz]. part_roots: [3][n_cols][ld_parts]
+// words, ld_parts >= ceil(x_rows / 128); the chunk must start on a 1,024-row block (row0 % 1024 == 0).
+int ring_gemm_compare_tc(uint32_t segments, const int8_t* const x_lo[6], const int8_t* const x_hi[6], size_t x_rows,
+                         const uint16_t* const b_lo[6], const uint16_t* const b_hi[6], uint32_t n_cols, uint32_t n_pad,
+                         uint32_t l, const uint32_t* col_tags, const uint64_t seeds[3], uint32_t thr_a,
+                         uint16_t* const z[6], size_t ldz, uint64_t row0, uint32_t* part_roots, size_t ld_parts,
+                         cudaStream_t stream) {
+  if (segments != 1 && segments != 2) {
+    set_error("fused GEMM + comparison: one or two K segments");
+    return IPC_EINVAL;
+  }
+  if ((segments * l) % (2 * KB_PER_CHUNK * KB) != 0) {
+    set_error("fused GEMM + comparison: K must be a multiple of 256");
+    return IPC_EINVAL;
+  }
+  const uint32_t n_rt = static_cast<uint32_t>((x_rows + TM - 1) / TM);
+  if (row0 % (32u << FUSE_LOG2_BLOCK) != 0 || ld_parts < n_rt || ldz % 8 != 0 || ldz < x_rows || n_cols == 0 ||
+      x_rows == 0 || n_pad < n_cols) {
+    set_error("fused GEMM + comparison: need row0 % 1024 == 0, ld_parts >= ceil(rows / 128), ldz % 8 == 0, "
+              "ldz >= rows, 1 <= n_cols <= n_pad, rows >= 1");
+    return IPC_EINVAL;
+  }
+  FuseMaps fm;  // passed by value as kernel parameters (3 KiB)
+  int rc;
+  for (uint32_t s = 0; s < NPASS; ++s) {
+    if ((rc = make_map_f16(&fm.q[s][0], b_lo[s], static_cast<uint64_t>(segments) * l, n_pad, 256)) ||
+        (rc = make_map_f16(&fm.q[s][1], b_hi[s], static_cast<uint64_t>(segments) * l, n_pad, 256)) ||
+        (rc = make_map_i8(&fm.x[s][0], x_lo[s], l, x_rows, TM)) || (rc = make_map_i8(&fm.x[s][1], x_hi[s], l, x_rows, TM)))
+      return rc;
+  }
+  TcParams p{};
+  p.n_cols = n_cols;
+  p.x_rows = static_cast<uint32_t>(x_rows);
+  p.kb_total = segments * l / KB;
+  p.kb_half = l / KB;
+  p.n_row_tiles = n_rt;
+  p.col_tags = col_tags;
+  p.ldz = ldz;
+  p.row0 = row0;
+  p.status = status_ptr();
+  FuseParams fp{};
+  fp.n_ct = (n_cols + 255) / 256;
+  for (uint32_t s = 0; s < NPASS; ++s) fp.z[s] = z[s];
+  for (int j = 0; j < 3; ++j) fp.seeds[j] = seeds[j];
+  fp.thr_a = thr_a;
+  fp.part_roots = part_roots;
+  fp.ld_parts = ld_parts;
+  static PerDevice attr;
+  IPC_CUDA_TRY(attr.run([] {
+    return cudaFuncSetAttribute(gemm_cmp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<256>::SMEM_BYTES);
+  }));
+  const uint32_t n_tiles = fp.n_ct * n_rt;
+  const uint32_t sms = static_cast<uint32_t>(sm_count_current());
+  const dim3 grid(n_tiles < sms ? n_tiles : sms);
+  gemm_cmp_kernel<<<grid, THREADS, Shape<256>::SMEM_BYTES, stream>>>(fm, p, fp);
+  IPC_CUDA_TRY(cudaGetLastError());
+  return IPC_OK;
 }
 
 int ring_gemm_tc(const int8_t* const x_lo[2], const int8_t* const x_hi[2], size_t x_rows, const uint16_t* b_lo,

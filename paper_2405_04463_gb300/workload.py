@@ -126,12 +126,12 @@ def query_shares_gpu(w: synth.Workload, qc=None, qm=None, galois_shares=False):
 
 
 def make_ctx(w: synth.Workload, path="i8mma", keep=False, chunk_rows=0, max_queries=0, plain_mask=False,
-             lift="mpc", thr_b=0, max_requests=0):
+             lift="mpc", thr_b=0, max_requests=0, fused=False):
     ipc = lib()
     g = ipc.ipc_geom(w.rows, w.cols, w.cell, w.rot_lo, w.R)
     cfg = ipc.make_config(g, thr_a=w.thr_a, path=path, db_chunk_rows=chunk_rows, max_queries=max_queries or w.Q,
                           seeds=w.prf_seeds, keep_distances=keep, plain_mask=plain_mask, lift=lift, thr_b=thr_b,
-                          max_requests=max_requests)
+                          max_requests=max_requests, fused=fused)
     ctx = ipc.ipc_create(cfg)
     ipc.ipc_set_input_stream(ctx)   # device inputs come from torch's current stream
     return ctx
