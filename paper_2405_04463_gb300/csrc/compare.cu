@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "compare.cuh"
+#include "tcgen05.cuh"  // PerDevice
 
 namespace ipc {
 namespace {
@@ -180,19 +181,18 @@ int launch_compare(CmpParams& P, int mode, cudaStream_t st) {
   P.n_blocks = static_cast<uint32_t>((P.n_rows + (32ull << P.p) - 1) >> (5 + P.p));
   const uint64_t threads = (static_cast<uint64_t>(P.n_cols) * P.n_blocks) << (P.p < LOG2_SPLIT ? P.p : LOG2_SPLIT);
   const size_t smem = sizeof(uint32_t) * S_WORDS * CT;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [smem] {
-    attr = cudaFuncSetAttribute(compare_kernel<MODE_LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(compare_kernel<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem));
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(compare_kernel<MODE_LIFTFREE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem));
-  });
-  IPC_CUDA_TRY(attr);
+  static tc::PerDevice attr;  // a kernel attribute belongs to one device's context
+  IPC_CUDA_TRY(attr.run([smem] {
+    cudaError_t e = cudaFuncSetAttribute(compare_kernel<MODE_LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(compare_kernel<MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(compare_kernel<MODE_LIFTFREE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+    return e;
+  }));
   const unsigned grid = static_cast<unsigned>((threads + CT - 1) / CT);
   if (mode == MODE_PLAIN)
     compare_kernel<MODE_PLAIN><<<grid, CT, smem, st>>>(P);

@@ -24,6 +24,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "tcgen05.cuh"  // PerDevice, sm_count_current
 
 namespace ipc {
 namespace {
@@ -477,26 +478,13 @@ int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, u
 
 namespace {
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
 template <int MODE, int BQ, bool LIST>
 int launch_variant(const CUtensorMap* m, const Params& p, dim3 grid, cudaStream_t stream) {
-  static std::once_flag once;
-  static cudaError_t err = cudaSuccess;
-  std::call_once(once, [] {
-    err = cudaFuncSetAttribute(gemm_i8_kernel<MODE, BQ, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kSmemBytes<BQ>);
-  });
-  IPC_CUDA_TRY(err);
+  static tc::PerDevice attr;  // a kernel attribute belongs to one device's context
+  IPC_CUDA_TRY(attr.run([] {
+    return cudaFuncSetAttribute(gemm_i8_kernel<MODE, BQ, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemBytes<BQ>);
+  }));
   gemm_i8_kernel<MODE, BQ, LIST><<<grid, kThreads<MODE>, kSmemBytes<BQ>, stream>>>(m[0], m[1], m[2], m[3], m[4], m[5], p);
   IPC_CUDA_TRY(cudaGetLastError());
   return IPC_OK;
@@ -544,7 +532,7 @@ int ring_gemm_i8_variant(int variant, const int8_t* const x_lo[2], const int8_t*
   // Without a tile list every tile gets its own CTA (a 2-D grid, measured faster for a fixed
   // shape); with a list whose length is known only on the device, one persistent CTA per SM walks it.
   if (col_tiles) {
-    const dim3 grid(static_cast<unsigned>(sm_count()));
+    const dim3 grid(static_cast<unsigned>(tc::sm_count_current()));
     switch (variant) {
       case 0: return launch_variant<1, 128, true>(m, p, grid, stream);
       case 1: return launch_variant<0, 128, true>(m, p, grid, stream);
