@@ -51,3 +51,15 @@ def test_error_paths_need_no_gpu(libipc):
     with pytest.raises(ipc.IpcError):
         ipc.ipc_ring_gemm("i8mma", [16, 16], [16, 16], 10, 16, 16, 4, 128, 100, 16, 0, 0, 0, 16, 16, 0, stream=0)
     assert "l must be" in ipc.ipc_last_error()
+
+
+def test_fused_setting_is_validated_without_gpu(libipc):
+    """ipc_config.fused reaches the library at its declared place in the struct: a fused context
+    on a path without the fused kernel, or with public masks or a lifting variant, is refused by
+    the argument checks, before any device call."""
+    import paper_2405_04463_gb300 as ipc
+    g = ipc.ipc_geom(16, 200, 4, -15, 31)
+    for kw in (dict(path="i8mma"), dict(path="i32"), dict(path="tc", plain_mask=True), dict(path="tc", lift="const")):
+        with pytest.raises(ipc.IpcError) as e:
+            ipc.ipc_create(ipc.make_config(g, fused=True, **kw))
+        assert e.value.rc == ipc.IPC_EINVAL and "fused" in str(e.value), kw
