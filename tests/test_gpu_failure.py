@@ -116,17 +116,25 @@ def test_fetch_with_zero_timeout_on_a_running_request(torch, small):
         ipc.ipc_destroy(ctx)
 
 
-def test_dropped_party_times_out_instead_of_hanging(torch, small):
+@pytest.mark.parametrize("fused", [False, True])
+def test_dropped_party_times_out_instead_of_hanging(torch, small, fused):
     """A party that never delivers its messages (its stream waits for a flag that nothing sets,
     injected on the host): fetches with a shorter timeout return IPC_ETIMEOUT, the wait gives up
     after its limit and the request reports IPC_EDEVICE once; its results are intact and the next
-    request is served normally."""
+    request is served normally. The same with the fused chunk step, whose launch waits for every
+    party's query preparation."""
     ipc = lib()
     w = small["w"]
-    ctx = make_ctx(w, path="tc")
+    ctx = make_ctx(w, path="tc", fused=fused)
     try:
         load_workload(ctx, w, chunk=300)
         code, mask = query_shares_gpu(w, small["qc"], small["qm"])
+        # one ordinary request first: in a fresh process it also loads the library's kernels, which
+        # would otherwise make the stalled request's submit outlast the stall
+        bits = np.zeros(w.Q, np.uint8)
+        ipc.fetch_match_bits(ctx, ipc.submit_queries(ctx, [code[j] for j in range(3)], [mask[j] for j in range(3)],
+                                                     w.Q, 1), bits, w.Q, 60000)
+        assert (bits == small["match"]).all()
         torch.cuda.synchronize()
         ipc.ipc_status()
         ipc.ipc_debug_stall_party(ctx, 1, 300000)   # party 1 is "gone" for 0.3 s
@@ -144,7 +152,7 @@ def test_dropped_party_times_out_instead_of_hanging(torch, small):
         assert (sh == _oracle_shares(small, rid)).all()
         ipc.ipc_release(ctx, rid)
         rid2 = ipc.submit_queries(ctx, [code[j] for j in range(3)], [mask[j] for j in range(3)], w.Q, 1)
-        bits = np.zeros(w.Q, np.uint8)
+        bits[:] = 0
         ipc.fetch_match_bits(ctx, rid2, bits, w.Q, 60000)
         assert (bits == small["match"]).all()
         with pytest.raises(ipc.IpcError):
