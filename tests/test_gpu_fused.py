@@ -106,6 +106,23 @@ def test_fused_persistent_tiles(torch, path):
     assert (bits == match).all() and match.sum() == 1
 
 
+@pytest.mark.parametrize("path", ["tc", "tcg"])
+def test_fused_degenerate_queries(torch, path):
+    """A one-row database (one row tile with one valid row: a part of one word of one row), one
+    rotation, an all-masked query (ml = 0: never a match) and a query equal to the row (a match):
+    shares equal to the oracle's, bits [0, 1]."""
+    ipc = lib()
+    w = synth.Workload("fusedd", s=1, Q=2, rot_lo=0, R=1, seed=78)
+    dc, dm = w.db_bits()
+    qc = np.stack([dc[0], dc[0]])
+    qm = np.stack([np.zeros_like(dm[0]), dm[0]])
+    ((rid, sh, bits, th),) = run_ctx(w, path, True, qc, qm, keep=True)
+    ref = oracle_shares(w, path, rid, dc, dm, qc, qm, want_z=True)
+    assert (sh == ref["bits"]).all()
+    assert th == oracle.transcript_hash(ref["z_code"], ref["z_mask"], ref["bits"])
+    assert bits.tolist() == [0, 1]
+
+
 def test_fused_rejects_other_settings(torch):
     ipc = lib()
     w = synth.Workload("fusedx", s=300, Q=1, planted=0, seed=1)
